@@ -1,0 +1,239 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws scenes and writes them as surface-parameter arrays; it
+holds none of the voting arithmetic.  Both the CUDA path and the CPU oracle read
+the arrays it returns.  Every generator is ``numpy.random.default_rng(seed)``
+(PCG64); the standard workloads use seed ``2107118100 + i`` for workload ``i``.
+
+Surface parameters are FP64, structure-of-arrays ``params[P, n]``:
+
+* ``LINE2D``      (Sec. 3, Eq. 2; line fitting of Sec. 4.1):  P = 2, rows (x, y) of the
+  image points; voting space (m, b) with the dual line b = y - x m.
+* ``PLANE3D_SPH`` (Sec. 4.1, hyperplanes in d-space, in spherical form): P = 3,
+  rows (qx, qy, qz); voting space (theta, phi, d) with d = q . n(theta, phi).
+* ``POSE3DOF``    (camera posing with known gravity, focal length and height; the
+  3DoF reduction of the 5DoF surfaces of Sec. 4.2.1): P = 4, rows (w1, w2, a, b);
+  voting space (yaw, x, y) with x = w1 - (a cos yaw - b sin yaw) and
+  y = w2 - (a sin yaw + b cos yaw); (a, b) = r (cos beta, sin beta), r the
+  horizontal distance implied by the elevation, beta the bearing azimuth.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF = 1, 2, 3, 4
+FAMILY_NAMES = {LINE2D: "LINE2D", PLANE3D_SPH: "PLANE3D_SPH", POSE3DOF: "POSE3DOF", POSE6DOF: "POSE6DOF"}
+FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1)}
+SEED_BASE = 2107118100
+
+
+@dataclass
+class Problem:
+    family: int
+    eps: np.ndarray          # [d]
+    bounds: np.ndarray       # [2d]: lo0, hi0, lo1, hi1, ...
+    params: np.ndarray       # [P, n] float64 (SoA)
+    truth: np.ndarray        # [d] planted solution in voting coordinates
+    inliers: np.ndarray      # indices of planted inliers
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.params.shape[1])
+
+    @property
+    def d(self) -> int:
+        return FAMILY_DK[self.family][0]
+
+    @property
+    def k(self) -> int:
+        return FAMILY_DK[self.family][1]
+
+
+# ---------------------------------------------------------------------------
+# 2D line fitting
+# ---------------------------------------------------------------------------
+
+def line2d(n: int = 10_000, inlier_frac: float = 0.10, eps: float = 0.01, noise: float = 0.002,
+           seed: int = SEED_BASE + 0, quantize: int | None = None) -> Problem:
+    """Points in [0,1]^2: ``inlier_frac`` of them within uniform +-noise
+    (perpendicular) of a random line y = m x + b (m ~ U[-1,1], b ~ U[0,1]), the
+    rest uniform.  Voting domain m in [-1, 1], b in [-1, 2].
+
+    ``quantize=q`` rounds coordinates to multiples of 2^-q (dyadic inputs)."""
+    rng = np.random.default_rng(seed)
+    m = rng.uniform(-1.0, 1.0)
+    b = rng.uniform(0.0, 1.0)
+    n_in = int(round(n * inlier_frac))
+    pts = np.empty((n, 2))
+    got = 0
+    while got < n_in:
+        x0 = rng.uniform(0.0, 1.0, size=2 * (n_in - got) + 8)
+        u = rng.uniform(-noise, noise, size=x0.size)
+        nrm = 1.0 / math.sqrt(1.0 + m * m)
+        px = x0 - u * m * nrm
+        py = m * x0 + b + u * nrm
+        ok = (px >= 0) & (px <= 1) & (py >= 0) & (py <= 1)
+        take = np.stack([px[ok], py[ok]], axis=1)[: n_in - got]
+        pts[got:got + len(take)] = take
+        got += len(take)
+    pts[n_in:] = rng.uniform(0.0, 1.0, size=(n - n_in, 2))
+    perm = rng.permutation(n)
+    pts = pts[perm]
+    inliers = np.nonzero(perm < n_in)[0]
+    if quantize is not None:
+        pts = np.round(pts * 2.0 ** quantize) / 2.0 ** quantize
+    return Problem(LINE2D, np.array([eps, eps]), np.array([-1.0, 1.0, -1.0, 2.0]),
+                   np.ascontiguousarray(pts.T), np.array([m, b]), inliers, "line2d",
+                   dict(inlier_frac=inlier_frac, noise=noise))
+
+
+# ---------------------------------------------------------------------------
+# 3D plane fitting, (theta, phi, d) parameter space
+# ---------------------------------------------------------------------------
+
+def plane3d(n: int = 1_000_000, inlier_frac: float = 0.02, eps: float = 0.005, sigma: float = 0.001,
+            seed: int = SEED_BASE + 1) -> Problem:
+    """Points in the unit cube: ``inlier_frac`` on a random plane (normal uniform on
+    the sphere, through a U[0,1]^3 point) plus N(0, sigma) along the normal, the
+    rest uniform.  Voting domain theta in [0, pi], phi in [0, 2 pi],
+    d in [-sqrt 3, sqrt 3]; eps_d = eps, eps_theta = eps_phi = eps / sqrt 3."""
+    rng = np.random.default_rng(seed)
+    while True:
+        v = rng.normal(size=3)
+        nrm = v / np.linalg.norm(v)
+        p0 = rng.uniform(0.0, 1.0, size=3)
+        dd = float(nrm @ p0)
+        corners = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], float)
+        s = corners @ nrm - dd
+        if s.min() < -0.05 and s.max() > 0.05:
+            break
+    theta = math.acos(max(-1.0, min(1.0, nrm[2])))
+    phi = math.atan2(nrm[1], nrm[0]) % (2 * math.pi)
+    n_in = int(round(n * inlier_frac))
+    pts = np.empty((n, 3))
+    got = 0
+    while got < n_in:
+        q = rng.uniform(0.0, 1.0, size=(2 * (n_in - got) + 8, 3))
+        q = q - np.outer(q @ nrm - dd, nrm)
+        ok = np.all((q >= 0) & (q <= 1), axis=1)
+        q = q[ok][: n_in - got]
+        q = q + np.outer(rng.normal(0.0, sigma, size=len(q)), nrm)
+        pts[got:got + len(q)] = q
+        got += len(q)
+    pts[n_in:] = rng.uniform(0.0, 1.0, size=(n - n_in, 3))
+    perm = rng.permutation(n)
+    pts = pts[perm]
+    inliers = np.nonzero(perm < n_in)[0]
+    r3 = math.sqrt(3.0)
+    e_ang = eps / r3
+    return Problem(PLANE3D_SPH, np.array([e_ang, e_ang, eps]),
+                   np.array([0.0, math.pi, 0.0, 2 * math.pi, -r3, r3]),
+                   np.ascontiguousarray(pts.T), np.array([theta, phi, dd]), inliers, "plane3d",
+                   dict(inlier_frac=inlier_frac, sigma=sigma))
+
+
+# ---------------------------------------------------------------------------
+# 3DoF camera voting (known gravity, focal length and camera height)
+# ---------------------------------------------------------------------------
+
+def pose3dof(n: int = 1_000_000, inlier_frac: float = 0.01, eps_xy: float = 0.25,
+             eps_yaw_deg: float = 0.5, noise_deg: float = 0.1, box=(100.0, 100.0, 10.0),
+             seed: int = SEED_BASE + 2, rng: np.random.Generator | None = None) -> Problem:
+    """3D points uniform in ``box``; a camera at (x, y) ~ U[0, box_x] x U[0, box_y],
+    yaw ~ U[0, 2 pi), height h ~ U[1, 9].  Inlier matches carry the true bearing
+    with N(0, noise) on azimuth and elevation; outliers pair a random point with a
+    random bearing (uniform direction).  Matches with |elevation| < 1 deg are
+    redrawn.  Each match becomes (w1, w2, a, b) with r = (w3 - h) / tan(elev),
+    a = r cos(beta), b = r sin(beta), beta the azimuth relative to the heading.
+    Voting domain yaw in [0, 2 pi], x in [0, box_x], y in [0, box_y]."""
+    if rng is None:
+        rng = np.random.default_rng(seed)
+    bx, by, bz = box
+    cam = np.array([rng.uniform(0, bx), rng.uniform(0, by)])
+    yaw = rng.uniform(0, 2 * math.pi)
+    h = rng.uniform(1.0, 9.0)
+    n_in = int(round(n * inlier_frac))
+    min_el = math.radians(1.0)
+    sig = math.radians(noise_deg)
+    out = np.empty((4, n))
+
+    def draw_points(m):
+        return np.stack([rng.uniform(0, bx, m), rng.uniform(0, by, m), rng.uniform(0, bz, m)], axis=1)
+
+    got = 0
+    while got < n_in:
+        m = 2 * (n_in - got) + 8
+        w = draw_points(m)
+        dx, dy, dz = w[:, 0] - cam[0], w[:, 1] - cam[1], w[:, 2] - h
+        rho = np.hypot(dx, dy)
+        beta = np.arctan2(dy, dx) - yaw + rng.normal(0, sig, m)
+        el = np.arctan2(dz, rho) + rng.normal(0, sig, m)
+        ok = (np.abs(el) >= min_el) & (rho > 1e-3)
+        w, beta, el = w[ok][: n_in - got], beta[ok][: n_in - got], el[ok][: n_in - got]
+        r = (w[:, 2] - h) / np.tan(el)
+        sl = slice(got, got + len(w))
+        out[0, sl], out[1, sl] = w[:, 0], w[:, 1]
+        out[2, sl], out[3, sl] = r * np.cos(beta), r * np.sin(beta)
+        got += len(w)
+    while got < n:
+        m = 2 * (n - got) + 8
+        w = draw_points(m)
+        v = rng.normal(size=(m, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        el = np.arcsin(np.clip(v[:, 2], -1, 1))
+        beta = np.arctan2(v[:, 1], v[:, 0])
+        ok = np.abs(el) >= min_el
+        w, beta, el = w[ok][: n - got], beta[ok][: n - got], el[ok][: n - got]
+        r = (w[:, 2] - h) / np.tan(el)
+        sl = slice(got, got + len(w))
+        out[0, sl], out[1, sl] = w[:, 0], w[:, 1]
+        out[2, sl], out[3, sl] = r * np.cos(beta), r * np.sin(beta)
+        got += len(w)
+    perm = rng.permutation(n)
+    out = out[:, perm]
+    inliers = np.nonzero(perm < n_in)[0]
+    e_yaw = math.radians(eps_yaw_deg)
+    return Problem(POSE3DOF, np.array([e_yaw, eps_xy, eps_xy]),
+                   np.array([0.0, 2 * math.pi, 0.0, bx, 0.0, by]),
+                   np.ascontiguousarray(out), np.array([yaw, cam[0], cam[1]]), inliers, "pose3dof",
+                   dict(inlier_frac=inlier_frac, height=h))
+
+
+def pose3dof_batch(num: int = 256, n_lo: float = 1e3, n_hi: float = 1e6, frac_lo: float = 0.005,
+                   frac_hi: float = 0.05, seed: int = SEED_BASE + 3) -> list[Problem]:
+    """``num`` independent 3DoF problems, n = round(10^U[log10 n_lo, log10 n_hi]) and
+    inlier ratio ~ U[frac_lo, frac_hi]."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for _ in range(num):
+        n = int(round(10 ** rng.uniform(math.log10(n_lo), math.log10(n_hi))))
+        frac = rng.uniform(frac_lo, frac_hi)
+        probs.append(pose3dof(n=n, inlier_frac=frac, rng=rng))
+    return probs
+
+
+# ---------------------------------------------------------------------------
+# Standard workloads
+# ---------------------------------------------------------------------------
+
+WORKLOADS = {
+    "line2d_n1e4": lambda: line2d(),
+    "plane3d_n1e6": lambda: plane3d(),
+    "pose3dof_n1e6": lambda: pose3dof(),
+}
+
+
+def random_small(family: int, n: int, seed: int, inlier_frac: float = 0.3, **kw) -> Problem:
+    """Small instances for parity and invariance tests."""
+    if family == LINE2D:
+        return line2d(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
+    if family == PLANE3D_SPH:
+        return plane3d(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
+    if family == POSE3DOF:
+        return pose3dof(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
+    raise ValueError(family)
