@@ -1,0 +1,168 @@
+/*
+ * vote.h -- C ABI of the GB300 general-voting library (libvote.so).
+ *
+ * General voting (Aiger, Lynen, Hosang, Zeisl, arXiv 2107.11810) finds a point of
+ * approximately maximal depth among n k-surfaces in R^d: the point that lies
+ * within eps (per dependent coordinate, vertical distance) of the most surfaces.
+ * Each surface has the parametric form of Sec. 3, Eq. 1:
+ *     x_j = F_j(x_1..x_k; t) + f_j,   j = k+1..d,
+ * with t the essential and f the free additive parameters.  The search is
+ * Algorithm 2 (SurfaceConsensus) with canonization (Sec. 3.2) and bound-based
+ * pruning (Sec. 3.3): level by level, the surfaces reaching a cell are rounded to
+ * a grid tied to the cell size, identical rounded surfaces are merged, every
+ * child cell is tested against every surface for proximity within eps plus the
+ * cell radius (the "subset of the conditions" surface-box test of Sec. 3.2),
+ * cells whose upper bound is below the best lower bound are dropped, and the
+ * rest split 2^d ways.  Leaves are cells no wider than eps in any coordinate.
+ *
+ * Conventions for every entry point:
+ *   - Return value: VOTE_OK or an error code; vote_last_error() gives a message
+ *     (thread-local).  No exception crosses the ABI and no kernel traps.  On
+ *     error the outputs are unspecified and the context stays usable.
+ *   - Ownership: the caller owns every input/output buffer.  The context owns
+ *     its device working memory (grown on demand, reused, freed by
+ *     vote_destroy).
+ *   - Threads: one context per host thread; calls on one context are serial.
+ *   - Work runs on the context's CUDA stream (vote_set_stream; default: the
+ *     legacy default stream).  Entry points that return host results
+ *     synchronise that stream before returning.
+ *   - Results are fully determined by the inputs (not by scheduling or GPU
+ *     work order): counts, depth, leaf and mask are bit-identical to the FP64
+ *     definition for both precision modes.
+ */
+#ifndef GV_VOTE_H
+#define GV_VOTE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vote_ctx vote_ctx;
+
+typedef enum {
+    VOTE_OK = 0,
+    VOTE_EINVAL = 1,       /* bad argument, non-finite input, value out of range    */
+    VOTE_ENOMEM = 2,       /* device or host allocation failed                       */
+    VOTE_ECUDA = 3,        /* a CUDA runtime call failed                             */
+    VOTE_ECAPACITY = 4,    /* a fixed-size buffer (trace) or key width was exceeded  */
+    VOTE_ETIMEOUT = 5,     /* a bounded device-side wait ran out                     */
+    VOTE_EUNSUPPORTED = 6, /* family / size combination not supported                */
+    VOTE_EINTERNAL = 7     /* a self-check failed (e.g. popcount(mask) != depth)     */
+} vote_status;
+
+/* Surface families.  Coordinates are ordered free first, then dependent.
+ *   VOTE_LINE2D      d=2 k=1: coords (m, b); input rows (x, y) of image points;
+ *                    surface b = y - x m (point-line duality, Sec. 3, Eq. 2).
+ *   VOTE_PLANE3D_SPH d=3 k=2: coords (theta, phi, d); input rows (qx, qy, qz);
+ *                    surface d = q . (sin th cos ph, sin th sin ph, cos th)
+ *                    (hyperplane fitting of Sec. 4.1 in spherical form).
+ *   VOTE_POSE3DOF    d=3 k=1: coords (yaw, x, y); input rows (w1, w2, a, b);
+ *                    surfaces x = w1 - (a cos yaw - b sin yaw),
+ *                    y = w2 - (a sin yaw + b cos yaw) (camera posing with known
+ *                    gravity, focal length and height; the 3DoF reduction of
+ *                    the Sec. 4.2.1 formulation). */
+typedef enum {
+    VOTE_LINE2D = 1,
+    VOTE_PLANE3D_SPH = 2,
+    VOTE_POSE3DOF = 3
+} vote_family;
+
+/* Options for vote_set_option. */
+typedef enum {
+    VOTE_OPT_PRECISION = 1,   /* 0 = plain FP64 predicate; 1 = FP32 screen with FP64
+                                 recheck of the borderline band (default 1)          */
+    VOTE_OPT_PRUNE = 2,       /* 1 = prune cells with UB < best LB (default); 0 = off */
+    VOTE_OPT_CHUNK_RECORDS = 3, /* records processed per expansion step (default 2^23) */
+    VOTE_OPT_TRACE_CAP = 4,   /* >0: record (level, coords, UB, LB) of every tested
+                                 child, up to this many entries (debug; default 0)   */
+    VOTE_OPT_GROUP = 5,       /* merging of identical canonical surfaces:
+                                 0 = off, 1 = on (default 0; results do not depend
+                                 on it)                                             */
+    VOTE_OPT_FAULT_ALLOC_AT = 6 /* test hook: fail the k-th device allocation with
+                                 VOTE_ENOMEM (0 = off)                               */
+} vote_option;
+
+/* Per-solve counters (vote_get_stats). */
+typedef struct {
+    int64_t levels;          /* L                                                 */
+    int64_t cells;           /* cells expanded (canonized and tested)            */
+    int64_t records;         /* (cell, canonical surface) records tested          */
+    int64_t tests;           /* (child cell, canonical surface) predicate calls   */
+    int64_t rechecks;        /* tests decided by the FP64 recheck                 */
+    int64_t chunks;          /* expansion steps                                   */
+    int64_t leaves;          /* leaves evaluated                                  */
+    int64_t peak_records;    /* largest record count held at one level            */
+    double  seconds;         /* wall time of the last solve                       */
+} vote_stats;
+
+/* Create a context for one surface family.
+ *   eps[d]      > 0: per-coordinate eps; for dependent coordinates it is the
+ *               inlier tolerance (Sec. 3.2 uses a different eps per coordinate),
+ *               for every coordinate the leaf width.
+ *   bounds[2d]  lo0, hi0, lo1, hi1, ...: the voting domain (Sec. 3 scales it to
+ *               the unit cube; here each coordinate keeps its own range).
+ * d and k must match the family (LINE2D 2/1, PLANE3D_SPH 3/2, POSE3DOF 3/1). */
+vote_status vote_create(int family, int d, int k, const double *eps, const double *bounds,
+                        vote_ctx **out);
+
+/* Set an option (see vote_option).  Returns VOTE_EINVAL for unknown keys or
+ * out-of-range values. */
+vote_status vote_set_option(vote_ctx *ctx, int key, double value);
+
+/* Use this CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for all work of the context. */
+vote_status vote_set_stream(vote_ctx *ctx, void *cuda_stream);
+
+/* Solve one problem whose surfaces are already on the device.
+ *   surfaces     device pointer, FP64, structure of arrays [P][n] (P = 2, 3, 4
+ *                rows for LINE2D, PLANE3D_SPH, POSE3DOF); not modified.
+ *   n            number of surfaces, >= 0.
+ *   best_point   host [d]: centre of the best leaf (Algorithm 2 returns B_c).
+ *   best_leaf    host [d] or NULL: integer coordinates of the best leaf.
+ *   depth        host: number of surfaces reaching the best leaf (its upper bound).
+ *   inlier_mask  device [(n+31)/32] uint32 or NULL: bit i set iff surface i
+ *                reaches the best leaf (merges are tracked, Sec. 3.2); the
+ *                popcount equals depth.
+ * Ties between leaves of equal depth go to the lexicographically smallest leaf
+ * coordinates.  n = 0 gives depth 0 and leaf (0, .., 0). */
+vote_status vote_solve(vote_ctx *ctx, const double *surfaces, int64_t n, double *best_point,
+                       int64_t *best_leaf, int64_t *depth, uint32_t *inlier_mask);
+
+/* Same as vote_solve with HOST buffers: surfaces host [P][n], inlier_mask host
+ * [(n+31)/32] or NULL.  Copies in and out through the context's stream. */
+vote_status vote_solve_host(vote_ctx *ctx, const double *surfaces, int64_t n, double *best_point,
+                            int64_t *best_leaf, int64_t *depth, uint32_t *inlier_mask);
+
+/* Upper and lower bound of one cell, by replaying every surface from the root
+ * along the path to the cell (the counts Algorithm 2 assigns to that cell,
+ * independent of pruning).
+ *   surfaces  device [P][n];  level in [0, L];  coords host [d], coordinate j in
+ *             [0, 2^min(level, L_j));  ub, lb host;  reach device
+ *             [(n+31)/32] or NULL (bit set per surface reaching the cell). */
+vote_status vote_cell_counts(vote_ctx *ctx, const double *surfaces, int64_t n, int level,
+                             const int64_t *coords, int64_t *ub, int64_t *lb, uint32_t *reach);
+
+/* Number of levels L and per-coordinate split counts L_j (host [d]). */
+vote_status vote_levels(vote_ctx *ctx, int *L, int *Lj);
+
+/* Debug trace of the last solve (needs VOTE_OPT_TRACE_CAP > 0): host arrays of
+ * capacity cap; level[i], coords[i*d + j], ub[i], lb[i]; *count = entries
+ * written.  Returns VOTE_ECAPACITY if the trace overflowed. */
+vote_status vote_get_trace(vote_ctx *ctx, int64_t cap, int32_t *level, int64_t *coords,
+                           int64_t *ub, int64_t *lb, int64_t *count);
+
+/* Counters of the last solve. */
+vote_status vote_get_stats(vote_ctx *ctx, vote_stats *out);
+
+/* Message for the last error on this host thread (static storage). */
+const char *vote_last_error(void);
+
+/* Free the context and all device memory it owns.  NULL is ignored. */
+void vote_destroy(vote_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GV_VOTE_H */

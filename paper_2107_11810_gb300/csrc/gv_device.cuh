@@ -1,0 +1,268 @@
+// gv_device.cuh -- device-side definitions of the general-voting hot path.
+//
+// Surfaces follow Sec. 3, Eq. 1 of Aiger et al. (arXiv 2107.11810):
+// x_j = F_j(x_free; t) + f_j.  A record holds one canonical surface in the frame of
+// its cell: the free parameter as an integer multiple q_f of the snap step s_f
+// (its vertical residual at the cell centre), the essential parameters as integer
+// multiples q_t of the level's step s_t (canonization, Sec. 3.2), and the number of
+// original surfaces it stands for.
+//
+// Every FP64 operation that decides a count is issued as one explicitly rounded
+// IEEE operation (__dadd_rn, __dmul_rn, ...), in a fixed order, so the compiler
+// cannot fuse or reorder it; the results are bit-identical to the definition.
+#pragma once
+#include <cstdint>
+
+#define GV_MAXD 6
+#define GV_MAXT 5
+#define GV_MAXL 32
+
+namespace gv {
+
+// ---------------------------------------------------------------------------
+// Problem and level constants (computed once on the host, passed by value).
+// ---------------------------------------------------------------------------
+struct Problem {
+    int fam, d, k, nd, le, np, L;
+    int Lj[GV_MAXD];
+    int coord_shift[GV_MAXD];  // bit offset of coordinate j in a packed leaf key
+    int coord_bits;            // sum of Lj
+    double lo[GV_MAXD], W[GV_MAXD], eps[GV_MAXD];
+    double s_f[GV_MAXD], inv_s_f[GV_MAXD];  // per dependent coordinate
+    float s_ff[GV_MAXD], inv_s_ff[GV_MAXD];
+};
+
+struct Level {                 // tests of the children of a level-l cell
+    int l;
+    int split_mask;            // bit j: coordinate j splits at this level
+    int leaf_children;         // children are leaves (l + 1 == L)
+    int st_ratio_log2[GV_MAXT];// log2(s_t(l+1) / s_t(l)), 0 or 1
+    double h[GV_MAXD];         // half-widths at level l
+    double h1[GV_MAXD];        // half-widths at level l+1
+    double s_t[GV_MAXT];       // essential-parameter snap step at level l
+    double inv_s_t[GV_MAXT];
+    double Rbase[GV_MAXD];     // eps_j + h1_j            (dependent index)
+    double A1[GV_MAXD];        // accumulated canonization error at level l+1
+    double rlb[GV_MAXD];       // eps_j - A1_j             (lower-bound radius)
+    float h1f[GV_MAXD];        // FP32 copies for the screen
+    float Rbasef[GV_MAXD], A1f[GV_MAXD], rlbf[GV_MAXD], s_tf[GV_MAXT];
+};
+
+// ---------------------------------------------------------------------------
+// Explicitly rounded FP64 operations.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+
+// ---------------------------------------------------------------------------
+// sin / cos of cell-centre angles: Cody-Waite reduction by pi/2 with a three-part
+// constant (two 33-bit parts, so k*part is exact for small k), then the Taylor
+// series of sin (to r^19) and cos (to r^20) with coefficients (-1)^n/n! rounded to
+// double, evaluated by Horner's rule in explicitly rounded steps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double taylor_sin(double r) {
+    const double c[9] = {-0x1.5555555555555p-3, 0x1.1111111111111p-7, -0x1.a01a01a01a01ap-13,
+                         0x1.71de3a556c734p-19, -0x1.ae64567f544e4p-26, 0x1.6124613a86d09p-33,
+                         -0x1.ae7f3e733b81fp-41, 0x1.952c77030ad4ap-49, -0x1.2f49b46814157p-57};
+    double s = dmul(r, r);
+    double p = c[8];
+#pragma unroll
+    for (int n = 7; n >= 0; --n) p = dadd(dmul(p, s), c[n]);
+    return dadd(r, dmul(r, dmul(s, p)));
+}
+
+__device__ __forceinline__ double taylor_cos(double r) {
+    const double c[10] = {-0x1.0000000000000p-1, 0x1.5555555555555p-5, -0x1.6c16c16c16c17p-10,
+                          0x1.a01a01a01a01ap-16, -0x1.27e4fb7789f5cp-22, 0x1.1eed8eff8d898p-29,
+                          -0x1.93974a8c07c9dp-37, 0x1.ae7f3e733b81fp-45, -0x1.6827863b97d97p-53,
+                          0x1.e542ba4020225p-62};
+    double s = dmul(r, r);
+    double p = c[9];
+#pragma unroll
+    for (int n = 8; n >= 0; --n) p = dadd(dmul(p, s), c[n]);
+    return dadd(1.0, dmul(s, p));
+}
+
+__device__ __forceinline__ void vsincos(double x, double *sn, double *cs) {
+    const double pio2_hi = 0x1.921fb544p+0, pio2_mid = 0x1.0b4611a6p-34,
+                 pio2_lo = 0x1.3198a2e037073p-69, two_over_pi = 0x1.45f306dc9c883p-1;
+    double k = rint(dmul(x, two_over_pi));
+    double r = dsub(x, dmul(k, pio2_hi));
+    r = dsub(r, dmul(k, pio2_mid));
+    r = dsub(r, dmul(k, pio2_lo));
+    long long ki = (long long)k;
+    int q = (int)(((ki % 4) + 4) % 4);
+    double ts = taylor_sin(r), tc = taylor_cos(r);
+    switch (q) {
+    case 0: *sn = ts; *cs = tc; break;
+    case 1: *sn = tc; *cs = -ts; break;
+    case 2: *sn = -ts; *cs = -tc; break;
+    default: *sn = -tc; *cs = ts; break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cell geometry.  Cells are keyed by their leaf-aligned packed coordinates:
+// coordinate j of a level-l cell occupies the top e_j = min(l, L_j) bits of its
+// L_j-bit field; coordinate 0 sits in the most significant field, so the packed
+// key orders leaves lexicographically.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int splits_at(const Problem &P, int l, int j) { return l < P.Lj[j] ? l : P.Lj[j]; }
+
+__device__ __forceinline__ int64_t cell_coord(const Problem &P, uint64_t key, int l, int j) {
+    int e = splits_at(P, l, j);
+    return (int64_t)((key >> (P.coord_shift[j] + P.Lj[j] - e)) & ((1ull << e) - 1ull));
+}
+
+__device__ __forceinline__ double cell_center(const Problem &P, const double *h, int j, int64_t i) {
+    return dadd(P.lo[j], dmul((double)(2 * i + 1), h[j]));
+}
+
+__device__ __forceinline__ uint64_t child_key(const Problem &P, uint64_t key, int l, int slot) {
+    for (int j = 0; j < P.d; ++j)
+        if (l < P.Lj[j] && ((slot >> j) & 1)) key |= 1ull << (P.coord_shift[j] + P.Lj[j] - (l + 1));
+    return key;
+}
+
+// ---------------------------------------------------------------------------
+// Families.  For each: D, K (free coords), ND (dependent), LE (essential params),
+// NP (input rows), NB (basis values); basis(), lift(), residual64(), lipschitz64(),
+// and the FP32 screen versions residual32(), lipschitz32() with errmag32(), the
+// magnitude sum that bounds the FP32 residual's distance from the FP64 one.
+// ---------------------------------------------------------------------------
+enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3 };
+
+template <int FAM> struct Fam;
+
+// LINE2D: coords (m, b); b = y - x m.  t = x, psi = m (linear: its change across a
+// child shift is the shift itself).
+template <> struct Fam<FAM_LINE2D> {
+    static constexpr int D = 2, K = 1, ND = 1, LE = 1, NP = 2, NB = 1;
+    static constexpr bool LINEAR_BASIS = true;
+    __device__ static void basis(const double *c, double *psi) { psi[0] = c[0]; }
+    __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
+                                double *f, double *t) {
+        double x = prm[i], y = prm[n + i];
+        t[0] = x;
+        f[0] = dsub(dsub(y, dmul(x, c[0])), c[1]);
+        (void)psi;
+    }
+    __device__ static void residual64(const double *f, const double *t, const double *dpsi, const double *sh,
+                                      double *fo) {
+        fo[0] = dsub(dsub(f[0], dmul(t[0], dpsi[0])), sh[1]);
+    }
+    __device__ static void lipschitz64(const double *t, double *lam) { lam[0] = fabs(t[0]); }
+    // FP32 screen: residual, and the magnitude sum its rounding error scales with
+    // (dpsi_max/sh_max: largest |dpsi| and |shift| over the cell's children)
+    __device__ static void residual32(const float *f, const float *t, const float *dpsi, const float *sh,
+                                      float *fo) {
+        fo[0] = (f[0] - t[0] * dpsi[0]) - sh[1];
+    }
+    __device__ static void errmag32(const float *f, const float *t, const float *dpsi_max, const float *sh_max,
+                                    float *err) {
+        err[0] = fabsf(f[0]) + fabsf(t[0]) * dpsi_max[0] + sh_max[1];
+    }
+    __device__ static void lipschitz32(const float *t, float *lam) { lam[0] = fabsf(t[0]); }
+};
+
+// PLANE3D_SPH: coords (theta, phi, d); d = q . n(theta, phi).  t = q; psi = n.
+template <> struct Fam<FAM_PLANE3D_SPH> {
+    static constexpr int D = 3, K = 2, ND = 1, LE = 3, NP = 3, NB = 3;
+    static constexpr bool LINEAR_BASIS = false;
+    __device__ static void basis(const double *c, double *psi) {
+        double st, ct, sp, cp;
+        vsincos(c[0], &st, &ct);
+        vsincos(c[1], &sp, &cp);
+        psi[0] = dmul(st, cp);
+        psi[1] = dmul(st, sp);
+        psi[2] = ct;
+    }
+    __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
+                                double *f, double *t) {
+        double qx = prm[i], qy = prm[n + i], qz = prm[2 * n + i];
+        t[0] = qx; t[1] = qy; t[2] = qz;
+        f[0] = dsub(dadd(dadd(dmul(qx, psi[0]), dmul(qy, psi[1])), dmul(qz, psi[2])), c[2]);
+    }
+    __device__ static void residual64(const double *f, const double *t, const double *dpsi, const double *sh,
+                                      double *fo) {
+        double s = dadd(dadd(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1])), dmul(t[2], dpsi[2]));
+        fo[0] = dsub(dadd(f[0], s), sh[2]);
+    }
+    __device__ static void lipschitz64(const double *t, double *lam) {
+        double xy = dadd(dmul(t[0], t[0]), dmul(t[1], t[1]));
+        lam[0] = dsqrt(dadd(xy, dmul(t[2], t[2])));
+        lam[1] = dsqrt(xy);
+    }
+    __device__ static void residual32(const float *f, const float *t, const float *dpsi, const float *sh,
+                                      float *fo) {
+        float s = __fmaf_rn(t[2], dpsi[2], __fmaf_rn(t[1], dpsi[1], t[0] * dpsi[0]));
+        fo[0] = (f[0] + s) - sh[2];
+    }
+    __device__ static void errmag32(const float *f, const float *t, const float *dpsi_max, const float *sh_max,
+                                    float *err) {
+        err[0] = fabsf(f[0]) + fabsf(t[0]) * dpsi_max[0] + fabsf(t[1]) * dpsi_max[1] +
+                 fabsf(t[2]) * dpsi_max[2] + sh_max[2];
+    }
+    __device__ static void lipschitz32(const float *t, float *lam) {
+        float xy = t[0] * t[0] + t[1] * t[1];
+        lam[0] = sqrtf(xy + t[2] * t[2]);
+        lam[1] = sqrtf(xy);
+    }
+};
+
+// POSE3DOF: coords (yaw, x, y); x = w1 - (a cos yaw - b sin yaw),
+// y = w2 - (a sin yaw + b cos yaw).  t = (a, b); psi = (cos yaw, sin yaw).
+template <> struct Fam<FAM_POSE3DOF> {
+    static constexpr int D = 3, K = 1, ND = 2, LE = 2, NP = 4, NB = 2;
+    static constexpr bool LINEAR_BASIS = false;
+    __device__ static void basis(const double *c, double *psi) {
+        double s, co;
+        vsincos(c[0], &s, &co);
+        psi[0] = co;
+        psi[1] = s;
+    }
+    __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
+                                double *f, double *t) {
+        double w1 = prm[i], w2 = prm[n + i], a = prm[2 * n + i], b = prm[3 * n + i];
+        t[0] = a; t[1] = b;
+        f[0] = dsub(dsub(w1, dsub(dmul(a, psi[0]), dmul(b, psi[1]))), c[1]);
+        f[1] = dsub(dsub(w2, dadd(dmul(a, psi[1]), dmul(b, psi[0]))), c[2]);
+    }
+    __device__ static void residual64(const double *f, const double *t, const double *dpsi, const double *sh,
+                                      double *fo) {
+        fo[0] = dsub(dsub(f[0], dsub(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1]))), sh[1]);
+        fo[1] = dsub(dsub(f[1], dadd(dmul(t[0], dpsi[1]), dmul(t[1], dpsi[0]))), sh[2]);
+    }
+    __device__ static void lipschitz64(const double *t, double *lam) {
+        double r = dsqrt(dadd(dmul(t[0], t[0]), dmul(t[1], t[1])));
+        lam[0] = r;
+        lam[1] = r;
+    }
+    __device__ static void residual32(const float *f, const float *t, const float *dpsi, const float *sh,
+                                      float *fo) {
+        fo[0] = (f[0] - __fmaf_rn(t[0], dpsi[0], -(t[1] * dpsi[1]))) - sh[1];
+        fo[1] = (f[1] - __fmaf_rn(t[0], dpsi[1], t[1] * dpsi[0])) - sh[2];
+    }
+    __device__ static void errmag32(const float *f, const float *t, const float *dpsi_max, const float *sh_max,
+                                    float *err) {
+        float m = fabsf(t[0]) * fmaxf(dpsi_max[0], dpsi_max[1]) + fabsf(t[1]) * fmaxf(dpsi_max[0], dpsi_max[1]);
+        err[0] = fabsf(f[0]) + m + sh_max[1];
+        err[1] = fabsf(f[1]) + m + sh_max[2];
+    }
+    __device__ static void lipschitz32(const float *t, float *lam) {
+        float r = sqrtf(t[0] * t[0] + t[1] * t[1]);
+        lam[0] = r;
+        lam[1] = r;
+    }
+};
+
+// Relative error factor of the FP32 screen: every FP32 residual above takes at
+// most 6 rounded steps (conversions included) on terms whose magnitudes sum to
+// err[]; its distance to the FP64 value is below 8 u32 * err (u32 = 2^-24) plus
+// the FP64 value's own error (< 8 u64 * err).  The screen uses 32 u32 * err, a
+// factor-4 margin that also covers the rounding of err itself.
+constexpr float kScreenRel = 32.0f * 5.9604645e-08f;
+
+}  // namespace gv

@@ -1,0 +1,720 @@
+// gv_engine.cu -- host engine and C ABI of libvote (see include/vote.h).
+//
+// The engine drives Algorithm 2 (SurfaceConsensus) of arXiv 2107.11810 level by
+// level on the GPU.  Each level keeps a stack of cells and of their records
+// (canonical surfaces).  One expansion step takes a chunk of cells from the top of
+// the deepest non-empty level, tests all their children (k_test count pass),
+// raises the best lower bound, drops children below it (B&B pruning, Sec. 3.3),
+// lays out the survivors and writes their records, snapped for the next level
+// (emit pass, canonization of Sec. 3.2).  Taking the deepest level first is a
+// depth-first order over chunks: memory stays bounded by one chunk's expansion per
+// level, and leaves are reached early, which raises the pruning bound early.  The
+// result does not depend on this order.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gv_kernels.h"
+#include "vote.h"
+
+using namespace gv;
+
+static thread_local char g_err[512] = "";
+
+static void set_err(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_err("%s failed: %s", #call, cudaGetErrorString(e_));                    \
+            return VOTE_ECUDA;                                                          \
+        }                                                                               \
+    } while (0)
+
+#define TRY(x)                                                                          \
+    do {                                                                                \
+        vote_status s_ = (x);                                                           \
+        if (s_ != VOTE_OK) return s_;                                                   \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct LevelStore {
+    DevBuf qf[GV_MAXD], qt[GV_MAXT], mult, cell;
+    size_t rec_cap = 0;
+    DevBuf key, rbeg, rcnt, ub;
+    size_t cell_cap = 0;
+    int64_t ncells = 0, nrecs = 0;
+};
+
+struct vote_ctx {
+    Problem P;
+    Level lev[GV_MAXL];
+    double h_leaf[GV_MAXD];
+    int ns = 0;                // 2^d child slots
+    int device = 0;
+    cudaStream_t stream = 0;
+    int precision = 1, prune = 1, group = 0;
+    int64_t chunk_records = 1 << 23;
+    int64_t trace_cap = 0;
+    int64_t fault_alloc_at = 0, alloc_count = 0;
+    LevelStore ls[GV_MAXL + 1];
+    DevBuf levs_dev, path, scal, alive, geo64, geo32, cnt, passmask, child_idx, cursor, keepflag, recn, bsums;
+    DevBuf tr_level, tr_key, tr_ub, tr_lb, surf_tmp, mask_tmp;
+    Scalars *h_sc = nullptr;   // pinned mirror of the device scalars
+    uint64_t *h_tmp = nullptr; // pinned slot for single values
+    int64_t trace_written = 0;
+    bool trace_overflow = false;
+    vote_stats stats;
+};
+
+// ---------------------------------------------------------------------------
+// problem constants (the same definition as the paper-derived oracle, written
+// independently: per-coordinate levels, power-of-two snap steps, accumulated
+// canonization error)
+// ---------------------------------------------------------------------------
+static int family_shape(int fam, int d, int k, int *le, int *np) {
+    switch (fam) {
+    case VOTE_LINE2D: if (d != 2 || k != 1) return 1; *le = 1; *np = 2; return 0;
+    case VOTE_PLANE3D_SPH: if (d != 3 || k != 2) return 1; *le = 3; *np = 3; return 0;
+    case VOTE_POSE3DOF: if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
+    default: return 1;
+    }
+}
+
+// bound on the change of each basis function across a cell of half-widths h
+static void family_sigma(int fam, const double *h, double *sigma) {
+    switch (fam) {
+    case VOTE_LINE2D: sigma[0] = h[0]; break;
+    case VOTE_PLANE3D_SPH:
+        sigma[0] = h[0] + h[1];
+        sigma[1] = h[0] + h[1];
+        sigma[2] = h[0];
+        break;
+    case VOTE_POSE3DOF:
+        sigma[0] = h[0];
+        sigma[1] = h[0];
+        break;
+    }
+}
+
+static double pow2_floor(double x, int *e_out) {
+    int e;
+    std::frexp(x, &e);
+    if (e_out) *e_out = e - 1;
+    return std::ldexp(1.0, e - 1);
+}
+
+static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double *eps, const double *bounds) {
+    int le, np;
+    if (family_shape(fam, d, k, &le, &np)) {
+        set_err("family %d does not take d=%d, k=%d", fam, d, k);
+        return VOTE_EINVAL;
+    }
+    Problem &P = c->P;
+    std::memset(&P, 0, sizeof(P));
+    P.fam = fam; P.d = d; P.k = k; P.nd = d - k; P.le = le; P.np = np;
+    P.L = 0;
+    for (int j = 0; j < d; ++j) {
+        double lo = bounds[2 * j], hi = bounds[2 * j + 1];
+        if (!(eps[j] > 0.0) || !std::isfinite(eps[j]) || !std::isfinite(lo) || !std::isfinite(hi) || !(hi > lo)) {
+            set_err("coordinate %d: need finite eps > 0 and lo < hi", j);
+            return VOTE_EINVAL;
+        }
+        P.lo[j] = lo;
+        P.W[j] = hi - lo;
+        P.eps[j] = eps[j];
+        int Lj = 0;
+        while (std::ldexp(P.W[j], -Lj) > eps[j]) ++Lj;
+        if (Lj > 30) {
+            set_err("coordinate %d needs %d levels (> 30)", j, Lj);
+            return VOTE_EUNSUPPORTED;
+        }
+        P.Lj[j] = Lj;
+        if (Lj > P.L) P.L = Lj;
+    }
+    if (P.L > GV_MAXL - 1) {
+        set_err("too many levels");
+        return VOTE_EUNSUPPORTED;
+    }
+    int bits = 0;
+    for (int j = d - 1; j >= 0; --j) {
+        P.coord_shift[j] = bits;
+        bits += P.Lj[j];
+    }
+    P.coord_bits = bits;
+    if (bits > 40) {
+        set_err("leaf key needs %d bits (> 40)", bits);
+        return VOTE_EUNSUPPORTED;
+    }
+    double h[GV_MAXL + 1][GV_MAXD];
+    for (int l = 0; l <= P.L; ++l)
+        for (int j = 0; j < d; ++j) {
+            int e = l < P.Lj[j] ? l : P.Lj[j];
+            h[l][j] = std::ldexp(P.W[j], -(e + 1));
+        }
+    for (int j = 0; j < d; ++j) c->h_leaf[j] = h[P.L][j];
+    if (P.L == 0) return VOTE_OK;
+    double epsp_min = INFINITY;
+    for (int j = 0; j < P.nd; ++j) {
+        double epsp = P.eps[k + j] / (double)P.L;
+        if (epsp < epsp_min) epsp_min = epsp;
+        P.s_f[j] = pow2_floor(epsp / (double)(le + 1), nullptr);
+        P.inv_s_f[j] = 1.0 / P.s_f[j];
+        P.s_ff[j] = (float)P.s_f[j];
+        P.inv_s_ff[j] = (float)P.inv_s_f[j];
+    }
+    double s_t[GV_MAXL + 1][GV_MAXT];
+    int s_te[GV_MAXL + 1][GV_MAXT];
+    double A[GV_MAXL + 1][GV_MAXD];
+    for (int j = 0; j < P.nd; ++j) A[0][j] = 0.0;
+    for (int l = 0; l < P.L; ++l) {
+        double sigma[GV_MAXT];
+        family_sigma(fam, h[l], sigma);
+        for (int m = 0; m < le; ++m) s_t[l][m] = pow2_floor(epsp_min / ((double)(le + 1) * sigma[m]), &s_te[l][m]);
+        for (int j = 0; j < P.nd; ++j) {
+            double delta = P.s_f[j] * 0.5;
+            for (int m = 0; m < le; ++m) delta = delta + (s_t[l][m] * 0.5) * sigma[m];
+            delta = delta + std::ldexp(P.eps[k + j], -32);
+            A[l + 1][j] = A[l][j] + delta;
+        }
+    }
+    for (int l = 0; l < P.L; ++l) {
+        Level &v = c->lev[l];
+        std::memset(&v, 0, sizeof(v));
+        v.l = l;
+        v.leaf_children = (l + 1 == P.L);
+        for (int j = 0; j < d; ++j) {
+            if (l < P.Lj[j]) v.split_mask |= 1 << j;
+            v.h[j] = h[l][j];
+            v.h1[j] = h[l + 1][j];
+            v.h1f[j] = (float)h[l + 1][j];
+        }
+        for (int m = 0; m < le; ++m) {
+            v.s_t[m] = s_t[l][m];
+            v.inv_s_t[m] = std::ldexp(1.0, -s_te[l][m]);
+            v.s_tf[m] = (float)s_t[l][m];
+            if (l + 1 < P.L) {
+                int r = s_te[l + 1][m] - s_te[l][m];
+                if (r < 0 || r > 1) {
+                    set_err("internal: snap step ratio 2^%d at level %d", r, l);
+                    return VOTE_EINTERNAL;
+                }
+                v.st_ratio_log2[m] = r;
+            }
+        }
+        for (int j = 0; j < P.nd; ++j) {
+            v.Rbase[j] = P.eps[k + j] + h[l + 1][k + j];
+            v.A1[j] = A[l + 1][j];
+            v.rlb[j] = P.eps[k + j] - A[l + 1][j];
+            v.Rbasef[j] = (float)v.Rbase[j];
+            v.A1f[j] = (float)v.A1[j];
+            v.rlbf[j] = (float)v.rlb[j];
+        }
+    }
+    return VOTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device memory
+// ---------------------------------------------------------------------------
+static vote_status ensure(vote_ctx *c, DevBuf &b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return VOTE_OK;
+    size_t want = bytes + bytes / 4 + 256;
+    if (b.p) {
+        CK(cudaFreeAsync(b.p, c->stream));
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    ++c->alloc_count;
+    if (c->fault_alloc_at && c->alloc_count == c->fault_alloc_at) {
+        set_err("injected allocation failure (allocation %lld)", (long long)c->alloc_count);
+        return VOTE_ENOMEM;
+    }
+    cudaError_t e = cudaMallocAsync(&b.p, want, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        set_err("device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+        return VOTE_ENOMEM;
+    }
+    b.bytes = want;
+    return VOTE_OK;
+}
+
+static void release(vote_ctx *c, DevBuf &b) {
+    if (b.p) cudaFreeAsync(b.p, c->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static vote_status ensure_level(vote_ctx *c, int l, size_t recs, size_t cells) {
+    LevelStore &s = c->ls[l];
+    if (recs > s.rec_cap) {
+        for (int j = 0; j < c->P.nd; ++j) TRY(ensure(c, s.qf[j], recs * 4));
+        for (int m = 0; m < c->P.le; ++m) TRY(ensure(c, s.qt[m], recs * 4));
+        TRY(ensure(c, s.mult, recs * 4));
+        TRY(ensure(c, s.cell, recs * 4));
+        s.rec_cap = recs + recs / 4;
+    }
+    if (cells > s.cell_cap) {
+        TRY(ensure(c, s.key, cells * 8));
+        TRY(ensure(c, s.rbeg, cells * 8));
+        TRY(ensure(c, s.rcnt, cells * 4));
+        TRY(ensure(c, s.ub, cells * 4));
+        s.cell_cap = cells + cells / 4;
+    }
+    return VOTE_OK;
+}
+
+static RecView rec_view(vote_ctx *c, int l) {
+    RecView v;
+    std::memset(&v, 0, sizeof(v));
+    for (int j = 0; j < c->P.nd; ++j) v.qf[j] = (int32_t *)c->ls[l].qf[j].p;
+    for (int m = 0; m < c->P.le; ++m) v.qt[m] = (int32_t *)c->ls[l].qt[m].p;
+    v.mult = (uint32_t *)c->ls[l].mult.p;
+    v.cell = (uint32_t *)c->ls[l].cell.p;
+    return v;
+}
+
+static CellView cell_view(vote_ctx *c, int l) {
+    CellView v;
+    v.key = (uint64_t *)c->ls[l].key.p;
+    v.rbeg = (uint64_t *)c->ls[l].rbeg.p;
+    v.rcnt = (uint32_t *)c->ls[l].rcnt.p;
+    v.ub = (uint32_t *)c->ls[l].ub.p;
+    return v;
+}
+
+static Scalars *dsc(vote_ctx *c) { return (Scalars *)c->scal.p; }
+
+static vote_status read_scalars(vote_ctx *c) {
+    CK(cudaMemcpyAsync(c->h_sc, c->scal.p, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return VOTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// search
+// ---------------------------------------------------------------------------
+static vote_status expand_chunk(vote_ctx *c, int l) {
+    const Problem &P = c->P;
+    LevelStore &S = c->ls[l];
+    const int ns = c->ns;
+    int nvalid = 0;
+    for (int s = 0; s < ns; ++s)
+        if (!(s & ~c->lev[l].split_mask)) ++nvalid;
+    // chunk: cells [c0, ncells) from the top of the stack, about chunk_records records
+    int64_t c1 = S.ncells, r1 = S.nrecs;
+    int64_t avg = S.nrecs / (S.ncells > 0 ? S.ncells : 1);
+    int64_t K = c->chunk_records / (avg > 0 ? avg : 1);
+    if (K < 1) K = 1;
+    if (K > (1 << 22)) K = 1 << 22;
+    int64_t c0, r0;
+    for (;;) {
+        c0 = c1 - K > 0 ? c1 - K : 0;
+        CK(cudaMemcpyAsync(c->h_tmp, (uint64_t *)S.rbeg.p + c0, 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        r0 = (int64_t)*c->h_tmp;
+        if (r1 - r0 <= 2 * c->chunk_records || K == 1) break;
+        K = K / 2;
+    }
+    int nc = (int)(c1 - c0);
+    int64_t nr = r1 - r0;
+    const Level &lev = c->lev[l];
+    int NB = P.fam == VOTE_LINE2D ? 1 : (P.fam == VOTE_PLANE3D_SPH ? 3 : 2);
+    size_t nch = (size_t)nc * ns;
+    TRY(ensure(c, c->alive, nc));
+    TRY(ensure(c, c->geo64, nch * NB * 8));
+    TRY(ensure(c, c->geo32, (size_t)nc * (ns + 1) * NB * 4));
+    TRY(ensure(c, c->cnt, nch * 12));
+    TRY(ensure(c, c->passmask, (size_t)nr));
+    TRY(ensure(c, c->child_idx, nch * 4));
+    TRY(ensure(c, c->cursor, nch * 4));
+    TRY(ensure(c, c->keepflag, nch * 4));
+    TRY(ensure(c, c->recn, nch * 4));
+    TRY(ensure(c, c->bsums, ((nch + 255) / 256) * 16 + 16));
+    if (!lev.leaf_children) TRY(ensure_level(c, l + 1, (size_t)nr * nvalid, nch));
+    CK(cudaMemsetAsync(c->cnt.p, 0, nch * 12, c->stream));
+    CK(cudaMemsetAsync(c->cursor.p, 0, nch * 4, c->stream));
+    CK(cudaMemsetAsync(&dsc(c)->n_cells, 0, 16, c->stream));
+
+    Chunk ch;
+    std::memset(&ch, 0, sizeof(ch));
+    ch.P = P;
+    ch.lev = lev;
+    ch.cells = cell_view(c, l);
+    ch.c0 = c0;
+    ch.nc = nc;
+    ch.in = rec_view(c, l);
+    ch.r0 = r0;
+    ch.r1 = r1;
+    ch.alive = (uint8_t *)c->alive.p;
+    ch.geo64 = (double *)c->geo64.p;
+    ch.geo32 = (float *)c->geo32.p;
+    ch.cnt = (uint32_t *)c->cnt.p;
+    ch.passmask = (uint8_t *)c->passmask.p;
+    ch.child_idx = (int32_t *)c->child_idx.p;
+    ch.cursor = (uint32_t *)c->cursor.p;
+    if (!lev.leaf_children) {
+        ch.next_cells = cell_view(c, l + 1);
+        ch.out = rec_view(c, l + 1);
+    }
+    ch.sc = dsc(c);
+    if (c->trace_cap > 0) {
+        ch.trace.cap = (unsigned long long)c->trace_cap;
+        ch.trace.level = (int32_t *)c->tr_level.p;
+        ch.trace.key = (uint64_t *)c->tr_key.p;
+        ch.trace.ub = (uint32_t *)c->tr_ub.p;
+        ch.trace.lb = (uint32_t *)c->tr_lb.p;
+    }
+    ch.prune = c->prune;
+    ch.precision = c->precision;
+
+    launch_cell_geo(ch, c->stream);
+    launch_test(ch, false, c->stream);
+    launch_child_lbmax(ch, c->stream);
+    launch_child_alloc(ch, (uint32_t *)c->keepflag.p, (uint32_t *)c->recn.p, (unsigned long long *)c->bsums.p,
+                       c->stream);
+    CK(cudaGetLastError());
+    c->stats.chunks++;
+    c->stats.cells += nc;
+    c->stats.records += nr;
+    S.ncells = c0;
+    S.nrecs = r0;
+    if (lev.leaf_children) {
+        c->stats.leaves += (int64_t)nc * nvalid;
+        return VOTE_OK;
+    }
+    CK(cudaMemcpyAsync(&c->h_sc->n_cells, &dsc(c)->n_cells, 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t new_cells = (int64_t)c->h_sc->n_cells, new_recs = (int64_t)c->h_sc->n_recs;
+    if (new_recs > 0) launch_test(ch, true, c->stream);
+    CK(cudaGetLastError());
+    c->ls[l + 1].ncells = new_cells;
+    c->ls[l + 1].nrecs = new_recs;
+    if (new_recs > c->stats.peak_records) c->stats.peak_records = new_recs;
+    return VOTE_OK;
+}
+
+static vote_status replay(vote_ctx *c, const double *surfaces, int64_t n, int lam, uint64_t key, uint32_t *reach,
+                          int64_t *ub, int64_t *lb) {
+    CK(cudaMemsetAsync(&dsc(c)->replay_ub, 0, 16, c->stream));
+    if (lam > 0) launch_path_geo(c->P, (const Level *)c->levs_dev.p, lam, key, (PathStep *)c->path.p, c->stream);
+    launch_replay(c->P, (const Level *)c->levs_dev.p, (const PathStep *)c->path.p, lam, surfaces, n, reach,
+                  dsc(c), c->stream);
+    CK(cudaGetLastError());
+    TRY(read_scalars(c));
+    *ub = (int64_t)c->h_sc->replay_ub;
+    *lb = (int64_t)c->h_sc->replay_lb;
+    return VOTE_OK;
+}
+
+static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, double *best_point,
+                                int64_t *best_leaf, int64_t *depth, uint32_t *mask) {
+    auto t0 = std::chrono::steady_clock::now();
+    const Problem &P = c->P;
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.levels = P.L;
+    if (n < 0 || !best_point || !depth || (n > 0 && !surfaces)) {
+        set_err("invalid arguments");
+        return VOTE_EINVAL;
+    }
+    if (n >= (int64_t)1 << 31 || (P.coord_bits < 64 && (uint64_t)n >= (1ull << (64 - P.coord_bits)))) {
+        set_err("n = %lld too large", (long long)n);
+        return VOTE_EUNSUPPORTED;
+    }
+    CK(cudaMemsetAsync(c->scal.p, 0, sizeof(Scalars), c->stream));
+    c->trace_written = 0;
+    c->trace_overflow = false;
+    for (int l = 0; l <= P.L; ++l) c->ls[l].ncells = c->ls[l].nrecs = 0;
+    uint64_t leafkey = 0;
+    int64_t dep = 0;
+    if (n > 0 && P.L == 0) {
+        dep = n;                                   // the domain is a leaf: every surface counts
+    } else if (n > 0) {
+        TRY(ensure_level(c, 0, (size_t)n, 1));
+        launch_lift(P, c->lev[0], surfaces, n, rec_view(c, 0), dsc(c), c->stream);
+        CK(cudaGetLastError());
+        uint64_t key0 = 0, rb0 = 0;
+        uint32_t cnt0 = (uint32_t)n;
+        CK(cudaMemcpyAsync(c->ls[0].key.p, &key0, 8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->ls[0].rbeg.p, &rb0, 8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->ls[0].rcnt.p, &cnt0, 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->ls[0].ub.p, &cnt0, 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));    // host sources above live on this frame
+        c->ls[0].ncells = 1;
+        c->ls[0].nrecs = n;
+        TRY(read_scalars(c));
+        if (c->h_sc->err) {
+            set_err("surface parameters are not finite or out of the representable range");
+            return VOTE_EINVAL;
+        }
+        for (;;) {
+            int l = -1;
+            for (int x = P.L - 1; x >= 0; --x)
+                if (c->ls[x].ncells > 0) {
+                    l = x;
+                    break;
+                }
+            if (l < 0) break;
+            TRY(expand_chunk(c, l));
+        }
+        TRY(read_scalars(c));
+        if (c->h_sc->err) {
+            set_err("internal: residual out of range (err %u)", c->h_sc->err);
+            return VOTE_EINTERNAL;
+        }
+        unsigned long long bk = c->h_sc->best_key;
+        if (bk) {
+            dep = (int64_t)(bk >> P.coord_bits);
+            leafkey = ~bk & ((1ull << P.coord_bits) - 1ull);
+        }
+        c->stats.tests = (int64_t)c->h_sc->tests;
+        c->stats.rechecks = (int64_t)c->h_sc->rechecks;
+        c->trace_written = (int64_t)c->h_sc->trace_n;
+        if (c->trace_cap && c->trace_written > c->trace_cap) c->trace_overflow = true;
+    }
+    *depth = dep;
+    for (int j = 0; j < P.d; ++j) {
+        int64_t i = (int64_t)((leafkey >> P.coord_shift[j]) & ((1ull << P.Lj[j]) - 1ull));
+        if (best_leaf) best_leaf[j] = i;
+        best_point[j] = P.lo[j] + (double)(2 * i + 1) * c->h_leaf[j];
+    }
+    if (mask && n > 0) {
+        if (dep > 0) {
+            int64_t ub = 0, lb = 0;
+            TRY(replay(c, surfaces, n, P.L, leafkey, mask, &ub, &lb));
+            if (ub != dep) {
+                set_err("internal: replayed inlier count %lld != depth %lld", (long long)ub, (long long)dep);
+                return VOTE_EINTERNAL;
+            }
+        } else {
+            CK(cudaMemsetAsync(mask, 0, (size_t)((n + 31) / 32) * 4, c->stream));
+        }
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return VOTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *vote_last_error(void) { return g_err; }
+
+vote_status vote_create(int family, int d, int k, const double *eps, const double *bounds, vote_ctx **out) {
+    if (!out || !eps || !bounds) {
+        set_err("null argument");
+        return VOTE_EINVAL;
+    }
+    *out = nullptr;
+    vote_ctx *c = new (std::nothrow) vote_ctx();
+    if (!c) {
+        set_err("out of host memory");
+        return VOTE_ENOMEM;
+    }
+    vote_status s = problem_init(c, family, d, k, eps, bounds);
+    if (s != VOTE_OK) {
+        delete c;
+        return s;
+    }
+    c->ns = 1 << d;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_sc, sizeof(Scalars));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_tmp, 64);
+    if (e != cudaSuccess) {
+        set_err("CUDA unavailable: %s", cudaGetErrorString(e));
+        delete c;
+        return VOTE_ECUDA;
+    }
+    s = ensure(c, c->scal, sizeof(Scalars));
+    if (s == VOTE_OK) s = ensure(c, c->levs_dev, sizeof(Level) * (c->P.L > 0 ? c->P.L : 1));
+    if (s == VOTE_OK) s = ensure(c, c->path, sizeof(PathStep) * (c->P.L > 0 ? c->P.L : 1));
+    if (s == VOTE_OK && c->P.L > 0) {
+        e = cudaMemcpyAsync(c->levs_dev.p, c->lev, sizeof(Level) * c->P.L, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            set_err("upload of level constants failed: %s", cudaGetErrorString(e));
+            s = VOTE_ECUDA;
+        }
+    }
+    if (s != VOTE_OK) {
+        vote_destroy(c);
+        return s;
+    }
+    *out = c;
+    return VOTE_OK;
+}
+
+vote_status vote_set_option(vote_ctx *c, int key, double v) {
+    if (!c) { set_err("null context"); return VOTE_EINVAL; }
+    switch (key) {
+    case VOTE_OPT_PRECISION:
+        if (v != 0 && v != 1) break;
+        c->precision = (int)v;
+        return VOTE_OK;
+    case VOTE_OPT_PRUNE:
+        if (v != 0 && v != 1) break;
+        c->prune = (int)v;
+        return VOTE_OK;
+    case VOTE_OPT_CHUNK_RECORDS:
+        if (!(v >= 1 && v <= 1e10)) break;
+        c->chunk_records = (int64_t)v;
+        return VOTE_OK;
+    case VOTE_OPT_TRACE_CAP: {
+        if (!(v >= 0 && v <= 1e9)) break;
+        c->trace_cap = (int64_t)v;
+        if (c->trace_cap > 0) {
+            size_t m = (size_t)c->trace_cap;
+            TRY(ensure(c, c->tr_level, m * 4));
+            TRY(ensure(c, c->tr_key, m * 8));
+            TRY(ensure(c, c->tr_ub, m * 4));
+            TRY(ensure(c, c->tr_lb, m * 4));
+        }
+        return VOTE_OK;
+    }
+    case VOTE_OPT_GROUP:
+        if (v != 0 && v != 1) break;
+        c->group = (int)v;
+        return VOTE_OK;
+    case VOTE_OPT_FAULT_ALLOC_AT:
+        if (!(v >= 0)) break;
+        c->fault_alloc_at = (int64_t)v;
+        c->alloc_count = 0;
+        return VOTE_OK;
+    default:
+        set_err("unknown option %d", key);
+        return VOTE_EINVAL;
+    }
+    set_err("option %d: value %g out of range", key, v);
+    return VOTE_EINVAL;
+}
+
+vote_status vote_set_stream(vote_ctx *c, void *stream) {
+    if (!c) { set_err("null context"); return VOTE_EINVAL; }
+    c->stream = (cudaStream_t)stream;
+    return VOTE_OK;
+}
+
+vote_status vote_solve(vote_ctx *c, const double *surfaces, int64_t n, double *best_point, int64_t *best_leaf,
+                       int64_t *depth, uint32_t *inlier_mask) {
+    if (!c) { set_err("null context"); return VOTE_EINVAL; }
+    return solve_device(c, surfaces, n, best_point, best_leaf, depth, inlier_mask);
+}
+
+vote_status vote_solve_host(vote_ctx *c, const double *surfaces, int64_t n, double *best_point, int64_t *best_leaf,
+                            int64_t *depth, uint32_t *inlier_mask) {
+    if (!c) { set_err("null context"); return VOTE_EINVAL; }
+    if (n < 0 || (n > 0 && !surfaces)) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    size_t in_bytes = (size_t)n * c->P.np * 8, words = (size_t)(n + 31) / 32;
+    TRY(ensure(c, c->surf_tmp, in_bytes > 0 ? in_bytes : 8));
+    TRY(ensure(c, c->mask_tmp, words > 0 ? words * 4 : 4));
+    if (n > 0) CK(cudaMemcpyAsync(c->surf_tmp.p, surfaces, in_bytes, cudaMemcpyHostToDevice, c->stream));
+    TRY(solve_device(c, (const double *)c->surf_tmp.p, n, best_point, best_leaf, depth,
+                     inlier_mask ? (uint32_t *)c->mask_tmp.p : nullptr));
+    if (inlier_mask && words) {
+        CK(cudaMemcpyAsync(inlier_mask, c->mask_tmp.p, words * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return VOTE_OK;
+}
+
+vote_status vote_cell_counts(vote_ctx *c, const double *surfaces, int64_t n, int level, const int64_t *coords,
+                             int64_t *ub, int64_t *lb, uint32_t *reach) {
+    if (!c || !coords || !ub || !lb || n < 0 || (n > 0 && !surfaces)) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    const Problem &P = c->P;
+    if (level < 0 || level > P.L) { set_err("level %d outside [0, %d]", level, P.L); return VOTE_EINVAL; }
+    uint64_t key = 0;
+    for (int j = 0; j < P.d; ++j) {
+        int e = level < P.Lj[j] ? level : P.Lj[j];
+        if (coords[j] < 0 || coords[j] >= ((int64_t)1 << e)) { set_err("coordinate %d out of range", j); return VOTE_EINVAL; }
+        key |= (uint64_t)coords[j] << (P.coord_shift[j] + P.Lj[j] - e);
+    }
+    if (n == 0) { *ub = 0; *lb = 0; return VOTE_OK; }
+    TRY(replay(c, surfaces, n, level, key, reach, ub, lb));
+    return VOTE_OK;
+}
+
+vote_status vote_levels(vote_ctx *c, int *L, int *Lj) {
+    if (!c || !L) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    *L = c->P.L;
+    if (Lj) for (int j = 0; j < c->P.d; ++j) Lj[j] = c->P.Lj[j];
+    return VOTE_OK;
+}
+
+vote_status vote_get_trace(vote_ctx *c, int64_t cap, int32_t *level, int64_t *coords, int64_t *ub, int64_t *lb,
+                           int64_t *count) {
+    if (!c || !count || cap < 0) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    int64_t m = c->trace_written < c->trace_cap ? c->trace_written : c->trace_cap;
+    if (m > cap) m = cap;
+    *count = m;
+    if (m > 0) {
+        int32_t *lv = new int32_t[m];
+        uint64_t *ky = new uint64_t[m];
+        uint32_t *u = new uint32_t[m], *b = new uint32_t[m];
+        cudaError_t e = cudaMemcpy(lv, c->tr_level.p, m * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(ky, c->tr_key.p, m * 8, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(u, c->tr_ub.p, m * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(b, c->tr_lb.p, m * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            const Problem &P = c->P;
+            for (int64_t i = 0; i < m; ++i) {
+                if (level) level[i] = lv[i];
+                if (ub) ub[i] = u[i];
+                if (lb) lb[i] = b[i];
+                if (coords)
+                    for (int j = 0; j < P.d; ++j) {
+                        int ex = lv[i] < P.Lj[j] ? lv[i] : P.Lj[j];
+                        coords[i * P.d + j] = (int64_t)((ky[i] >> (P.coord_shift[j] + P.Lj[j] - ex)) & ((1ull << ex) - 1ull));
+                    }
+            }
+        }
+        delete[] lv; delete[] ky; delete[] u; delete[] b;
+        if (e != cudaSuccess) { set_err("trace copy failed: %s", cudaGetErrorString(e)); return VOTE_ECUDA; }
+    }
+    if (c->trace_overflow) { set_err("trace overflowed (%lld entries)", (long long)c->trace_written); return VOTE_ECAPACITY; }
+    return VOTE_OK;
+}
+
+vote_status vote_get_stats(vote_ctx *c, vote_stats *out) {
+    if (!c || !out) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    *out = c->stats;
+    return VOTE_OK;
+}
+
+void vote_destroy(vote_ctx *c) {
+    if (!c) return;
+    for (int l = 0; l <= GV_MAXL; ++l) {
+        LevelStore &s = c->ls[l];
+        for (int j = 0; j < GV_MAXD; ++j) release(c, s.qf[j]);
+        for (int m = 0; m < GV_MAXT; ++m) release(c, s.qt[m]);
+        release(c, s.mult); release(c, s.cell); release(c, s.key); release(c, s.rbeg); release(c, s.rcnt); release(c, s.ub);
+    }
+    DevBuf *bufs[] = {&c->levs_dev, &c->path, &c->scal, &c->alive, &c->geo64, &c->geo32, &c->cnt, &c->passmask,
+                      &c->child_idx, &c->cursor, &c->keepflag, &c->recn, &c->bsums, &c->tr_level, &c->tr_key,
+                      &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp};
+    for (DevBuf *b : bufs) release(c, *b);
+    cudaStreamSynchronize(c->stream);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->h_tmp) cudaFreeHost(c->h_tmp);
+    delete c;
+}
+
+}  // extern "C"

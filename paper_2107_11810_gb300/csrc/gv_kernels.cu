@@ -1,0 +1,685 @@
+// gv_kernels.cu -- kernels of the level-wise voting search (Algorithm 2 of
+// arXiv 2107.11810 with canonization, Sec. 3.2, and B&B pruning, Sec. 3.3).
+//
+//   k_lift        root records of the original surfaces (Eq. 1 in the frame of the
+//                 domain centre), snapped for level 0
+//   k_cell_geo    per cell of a chunk: pruning re-check and the change of the
+//                 family's basis functions from the cell centre to each child
+//                 centre (own sin/cos, FP64)
+//   k_test        the cell x surface proximity test ("eps plus the cell radius"),
+//                 count pass (UB / LB / record count per child, warp-reduced) and
+//                 emit pass (child records, snapped for the next level)
+//   k_child_*     best lower bound, pruning, allocation of surviving children,
+//                 leaf argmax as a packed 64-bit atomicMax
+//   k_path_geo,   replay of every original surface along one root-to-cell path:
+//   k_replay      inlier mask of the best leaf and per-cell counts
+#include <cstdio>
+
+#include "gv_kernels.h"
+
+namespace gv {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned prune_threshold(const Problem &P, const Scalars *sc, int prune) {
+    if (!prune) return 1u;
+    unsigned lb = *(volatile const unsigned *)&sc->best_lb;
+    unsigned long long bk = *(volatile const unsigned long long *)&sc->best_key;
+    unsigned leaf = (unsigned)(bk >> P.coord_bits);
+    unsigned t = lb > leaf ? lb : leaf;
+    return t > 1u ? t : 1u;
+}
+
+// round-half-even of q/2: re-snap of an essential parameter when the step doubles
+__device__ __forceinline__ int32_t resnap_half(int32_t q) {
+    int32_t k = q >> 1;
+    return k + ((q & 1) & (k & 1));
+}
+
+// ---------------------------------------------------------------------------
+// A0 lift
+// ---------------------------------------------------------------------------
+template <int FAM>
+__global__ void k_lift(Problem P, Level lev0, const double *__restrict__ prm, int64_t n, RecView out,
+                       Scalars *sc) {
+    using F = Fam<FAM>;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double c[F::D], psi[F::NB], f[F::ND], t[F::LE];
+#pragma unroll
+    for (int j = 0; j < F::D; ++j) c[j] = cell_center(P, lev0.h, j, 0);
+    F::basis(c, psi);
+    F::lift(prm, n, i, c, psi, f, t);
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) {
+        double q = rint(dmul(f[j], P.inv_s_f[j]));
+        bad |= !(fabs(q) < 1073741824.0);
+        out.qf[j][i] = bad ? 0 : (int32_t)q;
+    }
+#pragma unroll
+    for (int m = 0; m < F::LE; ++m) {
+        double q = rint(dmul(t[m], lev0.inv_s_t[m]));
+        bad |= !(fabs(q) < 1073741824.0);
+        out.qt[m][i] = bad ? 0 : (int32_t)q;
+    }
+    out.mult[i] = 1u;
+    out.cell[i] = 0u;
+    if (bad) atomicOr(&sc->err, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// A1 cell geometry: basis change from the parent centre to each child centre
+// ---------------------------------------------------------------------------
+template <int FAM>
+__device__ __forceinline__ void child_dpsi(const Problem &P, const Level &lev, uint64_t key, int fs,
+                                           const double *psi_par, double *dpsi) {
+    using F = Fam<FAM>;
+    if constexpr (F::LINEAR_BASIS) {
+        // psi is the free coordinate itself: its change is the exact child shift
+        bool split = (lev.split_mask >> 0) & 1;
+        dpsi[0] = split ? ((fs & 1) ? lev.h1[0] : -lev.h1[0]) : 0.0;
+        return;
+    } else {
+    double cch[F::D];
+#pragma unroll
+    for (int j = 0; j < F::K; ++j) {
+        int64_t i = cell_coord(P, key, lev.l, j);
+        bool split = (lev.split_mask >> j) & 1;
+        int64_t ic = split ? 2 * i + ((fs >> j) & 1) : i;
+        cch[j] = cell_center(P, lev.h1, j, ic);
+    }
+    double psi_ch[F::NB];
+    F::basis(cch, psi_ch);
+#pragma unroll
+    for (int m = 0; m < F::NB; ++m) dpsi[m] = dsub(psi_ch[m], psi_par[m]);
+    }
+}
+
+template <int FAM>
+__device__ __forceinline__ void parent_psi(const Problem &P, const Level &lev, uint64_t key, double *psi) {
+    using F = Fam<FAM>;
+    double cpar[F::D];
+#pragma unroll
+    for (int j = 0; j < F::K; ++j) cpar[j] = cell_center(P, lev.h, j, cell_coord(P, key, lev.l, j));
+    if (!F::LINEAR_BASIS) F::basis(cpar, psi);
+}
+
+template <int FAM>
+__global__ void k_cell_geo(Chunk c) {
+    using F = Fam<FAM>;
+    constexpr int NS = 1 << F::D;
+    constexpr int NF = 1 << F::K;
+    int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= c.nc) return;
+    const Problem &P = c.P;
+    const Level &lev = c.lev;
+    unsigned thr = prune_threshold(P, c.sc, c.prune);
+    c.alive[cell] = c.cells.ub[c.c0 + cell] >= thr ? 1 : 0;
+    uint64_t key = c.cells.key[c.c0 + cell];
+    double psi_par[F::NB];
+    parent_psi<FAM>(P, lev, key, psi_par);
+    float mx[F::NB];
+#pragma unroll
+    for (int m = 0; m < F::NB; ++m) mx[m] = 0.0f;
+    for (int fs = 0; fs < NF; ++fs) {
+        if (fs & ~lev.split_mask & (NF - 1)) continue;
+        double dpsi[F::NB];
+        child_dpsi<FAM>(P, lev, key, fs, psi_par, dpsi);
+        for (int s = fs; s < NS; s += NF) {          // dependent-coordinate bits share psi
+            if (s & ~lev.split_mask) continue;
+#pragma unroll
+            for (int m = 0; m < F::NB; ++m) {
+                c.geo64[((size_t)cell * NS + s) * F::NB + m] = dpsi[m];
+                c.geo32[((size_t)cell * (NS + 1) + s) * F::NB + m] = (float)dpsi[m];
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < F::NB; ++m) mx[m] = fmaxf(mx[m], fabsf((float)dpsi[m]));
+    }
+#pragma unroll
+    for (int m = 0; m < F::NB; ++m) c.geo32[((size_t)cell * (NS + 1) + NS) * F::NB + m] = mx[m];
+}
+
+// ---------------------------------------------------------------------------
+// A4 proximity test (count pass and emit pass) and A6 emission
+// ---------------------------------------------------------------------------
+template <int FAM>
+__device__ __forceinline__ void shifts64(const Level &lev, int s, double *sh) {
+    using F = Fam<FAM>;
+#pragma unroll
+    for (int j = 0; j < F::D; ++j) {
+        bool split = (lev.split_mask >> j) & 1;
+        sh[j] = split ? (((s >> j) & 1) ? lev.h1[j] : -lev.h1[j]) : 0.0;
+    }
+}
+
+template <int FAM>
+__device__ __forceinline__ void shifts32(const Level &lev, int s, float *sh) {
+    using F = Fam<FAM>;
+#pragma unroll
+    for (int j = 0; j < F::D; ++j) {
+        bool split = (lev.split_mask >> j) & 1;
+        sh[j] = split ? (((s >> j) & 1) ? lev.h1f[j] : -lev.h1f[j]) : 0.0f;
+    }
+}
+
+// FP64 upper-bound radius of a record (Lipschitz test): R_j = ((eps_j + h1_j) +
+// sum_i lam_ji h1_i) + A1_j, in this order.
+template <int FAM>
+__device__ __forceinline__ void radius64(const Level &lev, const double *t, double *R) {
+    using F = Fam<FAM>;
+    double lam[F::ND * F::K];
+    F::lipschitz64(t, lam);
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) {
+        double r = lev.Rbase[j];
+#pragma unroll
+        for (int i = 0; i < F::K; ++i) r = dadd(r, dmul(lam[j * F::K + i], lev.h1[i]));
+        R[j] = dadd(r, lev.A1[j]);
+    }
+}
+
+// exact FP64 test of one (record, child): bit 0 UB pass, bit 1 LB pass
+template <int FAM>
+__device__ __forceinline__ int test64(const Level &lev, const double *f, const double *t, const double *R,
+                                      const double *dpsi, int s, double *fo) {
+    using F = Fam<FAM>;
+    double sh[F::D];
+    shifts64<FAM>(lev, s, sh);
+    F::residual64(f, t, dpsi, sh, fo);
+    int ub = 1, lb = 1;
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) {
+        double a = fabs(fo[j]);
+        ub &= a <= R[j];
+        lb &= a <= lev.rlb[j];
+    }
+    return ub | (lb << 1);
+}
+
+template <int FAM, int PREC, bool EMIT>
+__global__ void __launch_bounds__(256) k_test(Chunk c) {
+    using F = Fam<FAM>;
+    constexpr int NS = 1 << F::D;
+    const Problem &P = c.P;
+    const Level &lev = c.lev;
+    const int lane = threadIdx.x & 31;
+    const int smask = lev.split_mask;
+    int64_t r = c.r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool act = false;
+    int cl = 0;
+    uint32_t mult = 0;
+    int32_t qf[F::ND], qt[F::LE];
+    if (r < c.r1) {
+        cl = (int)((int64_t)c.in.cell[r] - c.c0);
+        act = c.alive[cl] != 0;
+        if (act) {
+#pragma unroll
+            for (int j = 0; j < F::ND; ++j) qf[j] = c.in.qf[j][r];
+#pragma unroll
+            for (int m = 0; m < F::LE; ++m) qt[m] = c.in.qt[m][r];
+            mult = c.in.mult[r];
+        }
+    }
+    unsigned ubm = 0, lbm = 0;
+    unsigned long long ntest = 0, nrecheck = 0;
+    // FP64 canonical values of the record
+    double f64[F::ND], t64[F::LE], R64[F::ND];
+    bool have64 = false;
+    auto need64 = [&]() {
+        if (have64) return;
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) f64[j] = dmul((double)qf[j], P.s_f[j]);
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) t64[m] = dmul((double)qt[m], lev.s_t[m]);
+        radius64<FAM>(lev, t64, R64);
+        have64 = true;
+    };
+    float f32[F::ND], t32[F::LE], R32[F::ND], Eub[F::ND], Elb[F::ND];
+    if (act && PREC == 1) {
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) f32[j] = (float)qf[j] * P.s_ff[j];
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) t32[m] = (float)qt[m] * lev.s_tf[m];
+        float lam[F::ND * F::K];
+        F::lipschitz32(t32, lam);
+        float shmax[F::D], err[F::ND];
+#pragma unroll
+        for (int j = 0; j < F::D; ++j) shmax[j] = ((smask >> j) & 1) ? lev.h1f[j] : 0.0f;
+        F::errmag32(f32, t32, c.geo32 + ((size_t)cl * (NS + 1) + NS) * F::NB, shmax, err);
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) {
+            float rr = lev.Rbasef[j];
+#pragma unroll
+            for (int i = 0; i < F::K; ++i) rr = rr + lam[j * F::K + i] * lev.h1f[i];
+            R32[j] = rr + lev.A1f[j];
+            Eub[j] = kScreenRel * (err[j] + R32[j]);
+            Elb[j] = kScreenRel * (err[j] + fabsf(lev.rlbf[j]));
+        }
+    }
+    if (!EMIT) {
+        if (act) {
+            if (PREC == 0) need64();
+            for (int s = 0; s < NS; ++s) {
+                if (s & ~smask) continue;
+                ++ntest;
+                int res;
+                if (PREC == 0) {
+                    double fo[F::ND];
+                    res = test64<FAM>(lev, f64, t64, R64, c.geo64 + ((size_t)cl * NS + s) * F::NB, s, fo);
+                } else {
+                    float sh[F::D], fo[F::ND];
+                    shifts32<FAM>(lev, s, sh);
+                    F::residual32(f32, t32, c.geo32 + ((size_t)cl * (NS + 1) + s) * F::NB, sh, fo);
+                    int ub_fail = 0, ub_unsure = 0, lb_fail = 0, lb_unsure = 0;
+#pragma unroll
+                    for (int j = 0; j < F::ND; ++j) {
+                        float a = fabsf(fo[j]);
+                        ub_fail |= a - Eub[j] > R32[j];
+                        ub_unsure |= !(a + Eub[j] < R32[j]);
+                        lb_fail |= a - Elb[j] > lev.rlbf[j];
+                        lb_unsure |= !(a + Elb[j] < lev.rlbf[j]);
+                    }
+                    if (ub_fail) {
+                        res = 0;
+                    } else if (!ub_unsure && (lb_fail || !lb_unsure)) {
+                        res = 1 | ((lb_fail ? 0 : 1) << 1);
+                    } else {
+                        need64();
+                        ++nrecheck;
+                        double fo64[F::ND];
+                        res = test64<FAM>(lev, f64, t64, R64, c.geo64 + ((size_t)cl * NS + s) * F::NB, s, fo64);
+                    }
+                }
+                ubm |= (unsigned)(res & 1) << s;
+                lbm |= (unsigned)((res >> 1) & 1) << s;
+            }
+        }
+        // per-child sums: warp-reduced when the whole warp works on one cell
+        unsigned actb = __ballot_sync(kFull, act);
+        if (actb) {
+            int leader = __ffs(actb) - 1;
+            int cl0 = __shfl_sync(kFull, cl, leader);
+            bool uniform = __all_sync(kFull, !act || cl == cl0);
+            for (int s = 0; s < NS; ++s) {
+                if (s & ~smask) continue;
+                unsigned pu = act && ((ubm >> s) & 1);
+                unsigned pl = act && ((lbm >> s) & 1);
+                unsigned vub = pu ? mult : 0u, vlb = pl ? mult : 0u;
+                if (uniform) {
+                    vub = __reduce_add_sync(kFull, vub);
+                    vlb = __reduce_add_sync(kFull, vlb);
+                    unsigned vn = __reduce_add_sync(kFull, pu);
+                    if (lane == leader) {
+                        uint32_t *b = c.cnt + ((size_t)cl0 * NS + s) * 3;
+                        if (vub) atomicAdd(b, vub);
+                        if (vlb) atomicAdd(b + 1, vlb);
+                        if (vn) atomicAdd(b + 2, vn);
+                    }
+                } else if (act && pu) {
+                    uint32_t *b = c.cnt + ((size_t)cl * NS + s) * 3;
+                    atomicAdd(b, vub);
+                    if (vlb) atomicAdd(b + 1, vlb);
+                    atomicAdd(b + 2, 1u);
+                }
+            }
+        }
+        if (r < c.r1) c.passmask[r - c.r0] = (uint8_t)ubm;
+    } else {
+        if (act) ubm = c.passmask[r - c.r0];
+        unsigned actb = __ballot_sync(kFull, act && ubm != 0);
+        if (actb) {
+            int leader = __ffs(actb) - 1;
+            int cl0 = __shfl_sync(kFull, cl, leader);
+            bool uniform = __all_sync(kFull, !(act && ubm) || cl == cl0);
+            for (int s = 0; s < NS; ++s) {
+                if (s & ~smask) continue;
+                bool want = act && ((ubm >> s) & 1);
+                int ci = -1;
+                if (want) {
+                    ci = c.child_idx[(size_t)cl * NS + s];
+                    want = ci >= 0;
+                }
+                unsigned bal = __ballot_sync(kFull, want);
+                if (!bal) continue;
+                unsigned pos = 0;
+                if (uniform) {
+                    int ldr = __ffs(bal) - 1;
+                    unsigned base = 0;
+                    if (lane == ldr) base = atomicAdd(&c.cursor[(size_t)cl0 * NS + s], (unsigned)__popc(bal));
+                    base = __shfl_sync(kFull, base, ldr);
+                    pos = base + __popc(bal & ((1u << lane) - 1u));
+                } else if (want) {
+                    pos = atomicAdd(&c.cursor[(size_t)cl * NS + s], 1u);
+                }
+                if (!want) continue;
+                // residual at the child centre, snapped for the child's level
+                int32_t qn[F::ND];
+                bool done = false;
+                if (PREC == 1) {
+                    float sh[F::D], fo[F::ND];
+                    shifts32<FAM>(lev, s, sh);
+                    F::residual32(f32, t32, c.geo32 + ((size_t)cl * (NS + 1) + s) * F::NB, sh, fo);
+                    done = true;
+#pragma unroll
+                    for (int j = 0; j < F::ND; ++j) {
+                        float y = fo[j] * P.inv_s_ff[j];
+                        float q = rintf(y);
+                        float margin = 0.5f - fabsf(y - q);
+                        float e = Eub[j] * P.inv_s_ff[j];
+                        if (margin > e && fabsf(q) < 1.6e7f) qn[j] = (int32_t)q;
+                        else done = false;
+                    }
+                    if (!done) ++nrecheck;
+                }
+                if (!done) {
+                    need64();
+                    double sh[F::D], fo[F::ND];
+                    shifts64<FAM>(lev, s, sh);
+                    F::residual64(f64, t64, c.geo64 + ((size_t)cl * NS + s) * F::NB, sh, fo);
+#pragma unroll
+                    for (int j = 0; j < F::ND; ++j) {
+                        double q = rint(dmul(fo[j], P.inv_s_f[j]));
+                        if (!(fabs(q) < 1073741824.0)) {
+                            atomicOr(&c.sc->err, 2u);
+                            q = 0.0;
+                        }
+                        qn[j] = (int32_t)q;
+                    }
+                }
+                uint64_t at = c.next_cells.rbeg[ci] + pos;
+#pragma unroll
+                for (int j = 0; j < F::ND; ++j) c.out.qf[j][at] = qn[j];
+#pragma unroll
+                for (int m = 0; m < F::LE; ++m) c.out.qt[m][at] = lev.st_ratio_log2[m] ? resnap_half(qt[m]) : qt[m];
+                c.out.mult[at] = mult;
+                c.out.cell[at] = (uint32_t)ci;
+            }
+        }
+    }
+    // counters
+    ntest = __reduce_add_sync(kFull, (unsigned)ntest);
+    nrecheck = __reduce_add_sync(kFull, (unsigned)nrecheck);
+    if (lane == 0) {
+        if (!EMIT && ntest) atomicAdd(&c.sc->tests, ntest);
+        if (nrecheck) atomicAdd(&c.sc->rechecks, nrecheck);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A5 best lower bound, pruning, allocation of surviving children, leaf argmax
+// ---------------------------------------------------------------------------
+template <int NS>
+__global__ void k_child_lbmax(Chunk c) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int cl = idx / NS, s = idx % NS;
+    unsigned v = 0;
+    if (cl < c.nc && !(s & ~c.lev.split_mask) && c.alive[cl]) v = c.cnt[(size_t)idx * 3 + 1];
+    v = __reduce_max_sync(kFull, v);
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(&c.sc->best_lb, v);
+}
+
+// Block-wide exclusive scan of one 64-bit value per thread (blockDim = 256).
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long *total) {
+    __shared__ unsigned long long warp_tot[8];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long t = lane < 8 ? warp_tot[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < 8) warp_tot[lane] = t;   // inclusive warp prefix
+    }
+    __syncthreads();
+    unsigned long long before = w ? warp_tot[w - 1] : 0ull;
+    *total = warp_tot[7];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Phase A: per child of the chunk -- trace, pruning decision, leaf argmax, and
+// per-block totals of surviving children and their records.
+template <int NS>
+__global__ void __launch_bounds__(256) k_child_mark(Chunk c, uint32_t *keepflag, uint32_t *recn,
+                                                    unsigned long long *bs_cells, unsigned long long *bs_recs) {
+    const Problem &P = c.P;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int cl = idx / NS, s = idx % NS;
+    bool exists = cl < c.nc && !(s & ~c.lev.split_mask) && c.alive[cl];
+    unsigned ub = 0, lb = 0, nrec = 0;
+    uint64_t key = 0;
+    if (exists) {
+        ub = c.cnt[(size_t)idx * 3];
+        lb = c.cnt[(size_t)idx * 3 + 1];
+        nrec = c.cnt[(size_t)idx * 3 + 2];
+        key = child_key(P, c.cells.key[c.c0 + cl], c.lev.l, s);
+        if (c.trace.cap) {
+            unsigned long long t = atomicAdd(&c.sc->trace_n, 1ull);
+            if (t < c.trace.cap) {
+                c.trace.level[t] = c.lev.l + 1;
+                c.trace.key[t] = key;
+                c.trace.ub[t] = ub;
+                c.trace.lb[t] = lb;
+            }
+        }
+    }
+    unsigned thr = prune_threshold(P, c.sc, c.prune);
+    bool keep = exists && ub >= thr;
+    if (c.lev.leaf_children) {
+        if (keep) {
+            unsigned long long kmask = (1ull << P.coord_bits) - 1ull;
+            unsigned long long cand = ((unsigned long long)ub << P.coord_bits) | (~key & kmask);
+            atomicMax(&c.sc->best_key, cand);
+        }
+        return;
+    }
+    if (idx < c.nc * NS) {
+        keepflag[idx] = keep ? 1u : 0u;
+        recn[idx] = keep ? nrec : 0u;
+    }
+    unsigned long long tc, tr;
+    block_excl_scan(keep ? 1ull : 0ull, &tc);
+    block_excl_scan(keep ? (unsigned long long)nrec : 0ull, &tr);
+    if (threadIdx.x == 0) {
+        bs_cells[blockIdx.x] = tc;
+        bs_recs[blockIdx.x] = tr;
+    }
+}
+
+// Phase B: exclusive scan of the per-block totals (one block of 256 threads).
+__global__ void __launch_bounds__(256) k_scan_sums(unsigned long long *a, unsigned long long *b, int nb, Scalars *sc) {
+    unsigned long long ca = 0, cb = 0;
+    for (int base = 0; base < nb; base += 256) {
+        int i = base + threadIdx.x;
+        unsigned long long va = i < nb ? a[i] : 0ull, vb = i < nb ? b[i] : 0ull;
+        unsigned long long ta, tb;
+        unsigned long long ea = block_excl_scan(va, &ta);
+        unsigned long long eb = block_excl_scan(vb, &tb);
+        if (i < nb) {
+            a[i] = ca + ea;
+            b[i] = cb + eb;
+        }
+        ca += ta;
+        cb += tb;
+    }
+    if (threadIdx.x == 0) {
+        sc->n_cells = ca;
+        sc->n_recs = cb;
+    }
+}
+
+// Phase C: surviving children get consecutive cell indices and record ranges in
+// (parent, slot) order.
+template <int NS>
+__global__ void __launch_bounds__(256) k_child_write(Chunk c, const uint32_t *keepflag, const uint32_t *recn,
+                                                     const unsigned long long *bs_cells,
+                                                     const unsigned long long *bs_recs) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    bool in = idx < c.nc * NS;
+    unsigned keep = in ? keepflag[idx] : 0u;
+    unsigned nrec = in ? recn[idx] : 0u;
+    unsigned long long tc, tr;
+    unsigned long long ec = block_excl_scan(keep, &tc);
+    unsigned long long er = block_excl_scan(nrec, &tr);
+    if (!in) return;
+    if (keep) {
+        int cl = idx / NS, s = idx % NS;
+        unsigned long long ci = bs_cells[blockIdx.x] + ec;
+        c.next_cells.key[ci] = child_key(c.P, c.cells.key[c.c0 + cl], c.lev.l, s);
+        c.next_cells.rbeg[ci] = bs_recs[blockIdx.x] + er;
+        c.next_cells.rcnt[ci] = nrec;
+        c.next_cells.ub[ci] = c.cnt[(size_t)idx * 3];
+        c.child_idx[idx] = (int32_t)ci;
+    } else {
+        c.child_idx[idx] = -1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A7 replay of the original surfaces along one root-to-cell path
+// ---------------------------------------------------------------------------
+template <int FAM>
+__global__ void k_path_geo(Problem P, const Level *__restrict__ levs, int lam, uint64_t key, PathStep *path) {
+    using F = Fam<FAM>;
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= lam) return;
+    const Level &lev = levs[l];
+    int slot = 0;
+    for (int j = 0; j < F::D; ++j)
+        if (l < P.Lj[j]) slot |= (int)(cell_coord(P, key, l + 1, j) & 1) << j;
+    double psi_par[F::NB], dpsi[F::NB];
+    parent_psi<FAM>(P, lev, key, psi_par);
+    child_dpsi<FAM>(P, lev, key, slot & ((1 << F::K) - 1), psi_par, dpsi);
+    path[l].slot = slot;
+#pragma unroll
+    for (int m = 0; m < F::NB; ++m) path[l].dpsi[m] = dpsi[m];
+}
+
+template <int FAM>
+__global__ void __launch_bounds__(256) k_replay(Problem P, const Level *__restrict__ levs,
+                                               const PathStep *__restrict__ path, int lam,
+                                               const double *__restrict__ prm, int64_t n, uint32_t *reach,
+                                               Scalars *sc) {
+    using F = Fam<FAM>;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int lane = threadIdx.x & 31;
+    bool reached = false, lbp = false;
+    if (i < n) {
+        double c[F::D], psi[F::NB], f[F::ND], t[F::LE];
+#pragma unroll
+        for (int j = 0; j < F::D; ++j) c[j] = cell_center(P, levs[0].h, j, 0);
+        F::basis(c, psi);
+        F::lift(prm, n, i, c, psi, f, t);
+        reached = true;
+        for (int l = 0; l < lam; ++l) {
+            const Level &lev = levs[l];
+#pragma unroll
+            for (int j = 0; j < F::ND; ++j) f[j] = dmul(rint(dmul(f[j], P.inv_s_f[j])), P.s_f[j]);
+#pragma unroll
+            for (int m = 0; m < F::LE; ++m) t[m] = dmul(rint(dmul(t[m], lev.inv_s_t[m])), lev.s_t[m]);
+            double R[F::ND], fo[F::ND];
+            radius64<FAM>(lev, t, R);
+            int res = test64<FAM>(lev, f, t, R, path[l].dpsi, path[l].slot, fo);
+            if (!(res & 1)) {
+                reached = false;
+                break;
+            }
+            if (l == lam - 1) lbp = (res >> 1) & 1;
+#pragma unroll
+            for (int j = 0; j < F::ND; ++j) f[j] = fo[j];
+        }
+    }
+    unsigned b = __ballot_sync(kFull, reached);
+    unsigned bl = __ballot_sync(kFull, lbp);
+    if (lane == 0 && i < n) {
+        if (reach) reach[i >> 5] = b;
+        if (b) atomicAdd(&sc->replay_ub, (unsigned long long)__popc(b));
+        if (bl) atomicAdd(&sc->replay_lb, (unsigned long long)__popc(bl));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+#define GV_DISPATCH(fam, CALL)                                      \
+    switch (fam) {                                                  \
+    case FAM_LINE2D: { constexpr int FAMV = FAM_LINE2D; CALL; } break;           \
+    case FAM_PLANE3D_SPH: { constexpr int FAMV = FAM_PLANE3D_SPH; CALL; } break; \
+    case FAM_POSE3DOF: { constexpr int FAMV = FAM_POSE3DOF; CALL; } break;       \
+    default: break;                                                 \
+    }
+
+void launch_lift(const Problem &P, const Level &lev0, const double *prm, int64_t n, RecView out, Scalars *sc,
+                 cudaStream_t st) {
+    if (n <= 0) return;
+    GV_DISPATCH(P.fam, (k_lift<FAMV><<<blocks_for(n, 256), 256, 0, st>>>(P, lev0, prm, n, out, sc)));
+}
+
+void launch_cell_geo(const Chunk &c, cudaStream_t st) {
+    if (c.nc <= 0) return;
+    GV_DISPATCH(c.P.fam, (k_cell_geo<FAMV><<<blocks_for(c.nc, 128), 128, 0, st>>>(c)));
+}
+
+void launch_test(const Chunk &c, bool emit, cudaStream_t st) {
+    int64_t nr = c.r1 - c.r0;
+    if (nr <= 0) return;
+    unsigned g = blocks_for(nr, 256);
+    if (c.precision == 0) {
+        if (emit) { GV_DISPATCH(c.P.fam, (k_test<FAMV, 0, true><<<g, 256, 0, st>>>(c))); }
+        else      { GV_DISPATCH(c.P.fam, (k_test<FAMV, 0, false><<<g, 256, 0, st>>>(c))); }
+    } else {
+        if (emit) { GV_DISPATCH(c.P.fam, (k_test<FAMV, 1, true><<<g, 256, 0, st>>>(c))); }
+        else      { GV_DISPATCH(c.P.fam, (k_test<FAMV, 1, false><<<g, 256, 0, st>>>(c))); }
+    }
+}
+
+void launch_child_lbmax(const Chunk &c, cudaStream_t st) {
+    int ns = 1 << c.P.d;
+    int64_t n = (int64_t)c.nc * ns;
+    if (n <= 0) return;
+    if (ns == 4) k_child_lbmax<4><<<blocks_for(n, 256), 256, 0, st>>>(c);
+    else k_child_lbmax<8><<<blocks_for(n, 256), 256, 0, st>>>(c);
+}
+
+void launch_child_alloc(const Chunk &c, uint32_t *keepflag, uint32_t *recn, unsigned long long *bsums,
+                        cudaStream_t st) {
+    int ns = 1 << c.P.d;
+    int64_t n = (int64_t)c.nc * ns;
+    if (n <= 0) return;
+    unsigned nb = blocks_for(n, 256);
+    unsigned long long *ba = bsums, *bb = bsums + nb;
+    if (ns == 4) k_child_mark<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else k_child_mark<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    if (c.lev.leaf_children) return;
+    k_scan_sums<<<1, 256, 0, st>>>(ba, bb, (int)nb, c.sc);
+    if (ns == 4) k_child_write<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else k_child_write<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+}
+
+void launch_path_geo(const Problem &P, const Level *levs_dev, int lam, uint64_t key, PathStep *path,
+                     cudaStream_t st) {
+    if (lam <= 0) return;
+    GV_DISPATCH(P.fam, (k_path_geo<FAMV><<<blocks_for(lam, 64), 64, 0, st>>>(P, levs_dev, lam, key, path)));
+}
+
+void launch_replay(const Problem &P, const Level *levs_dev, const PathStep *path, int lam, const double *prm,
+                   int64_t n, uint32_t *reach, Scalars *sc, cudaStream_t st) {
+    if (n <= 0) return;
+    GV_DISPATCH(P.fam, (k_replay<FAMV><<<blocks_for(n, 256), 256, 0, st>>>(P, levs_dev, path, lam, prm, n,
+                                                                            reach, sc)));
+}
+
+}  // namespace gv

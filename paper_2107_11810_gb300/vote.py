@@ -1,0 +1,217 @@
+"""Python binding of libvote.so (argument marshalling only).
+
+Every step of the search runs in the CUDA library; this module converts torch
+tensors and numpy arrays to pointers and sizes and raises on error codes.  There
+is no CPU fallback: if the library is missing, :func:`load` raises.
+
+Names follow the C ABI in ``include/vote.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .inputs import LINE2D, PLANE3D_SPH, POSE3DOF, FAMILY_DK
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvote.so")
+_lock = threading.Lock()
+_lib = None
+
+VOTE_OPT_PRECISION, VOTE_OPT_PRUNE, VOTE_OPT_CHUNK_RECORDS = 1, 2, 3
+VOTE_OPT_TRACE_CAP, VOTE_OPT_GROUP, VOTE_OPT_FAULT_ALLOC_AT = 4, 5, 6
+STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
+          5: "VOTE_ETIMEOUT", 6: "VOTE_EUNSUPPORTED", 7: "VOTE_EINTERNAL"}
+NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4}
+EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
+           "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_last_error",
+           "vote_destroy"]
+
+
+class VoteError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int64), ("cells", ctypes.c_int64), ("records", ctypes.c_int64),
+                ("tests", ctypes.c_int64), ("rechecks", ctypes.c_int64), ("chunks", ctypes.c_int64),
+                ("leaves", ctypes.c_int64), ("peak_records", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def load(path: str | None = None):
+    """Load libvote.so (build it first with ``paper_2107_11810_gb300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"libvote.so not found at {p}; run paper_2107_11810_gb300.build.build()")
+            lib = ctypes.CDLL(p)
+            P, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            lib.vote_create.argtypes = [i32, i32, i32, P, P, ctypes.POINTER(ctypes.c_void_p)]
+            lib.vote_set_option.argtypes = [P, i32, d]
+            lib.vote_set_stream.argtypes = [P, P]
+            lib.vote_solve.argtypes = [P, P, i64, P, P, P, P]
+            lib.vote_solve_host.argtypes = [P, P, i64, P, P, P, P]
+            lib.vote_cell_counts.argtypes = [P, P, i64, i32, P, P, P, P]
+            lib.vote_levels.argtypes = [P, P, P]
+            lib.vote_get_trace.argtypes = [P, i64, P, P, P, P, P]
+            lib.vote_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+            lib.vote_last_error.restype = ctypes.c_char_p
+            lib.vote_last_error.argtypes = []
+            lib.vote_destroy.argtypes = [P]
+            lib.vote_destroy.restype = None
+            for name in EXPORTS:
+                if name not in ("vote_last_error", "vote_destroy"):
+                    getattr(lib, name).restype = i32
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise VoteError(rc, load().vote_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Solver:
+    """One voting problem shape: family, per-coordinate eps, domain bounds.
+
+    ``solve(surfaces)`` takes a CUDA float64 tensor [P, n] (structure of arrays)
+    and returns the best leaf centre, its integer coordinates, the depth and the
+    inlier mask (CUDA int32 tensor holding the uint32 words)."""
+
+    def __init__(self, family: int, eps, bounds, precision: int = 1, prune: bool = True,
+                 chunk_records: int | None = None, trace_cap: int = 0, stream=None):
+        self.lib = load()
+        self.family = family
+        self.d, self.k = FAMILY_DK[family]
+        self.np = NPARAM[family]
+        e = np.ascontiguousarray(eps, dtype=np.float64).reshape(self.d)
+        b = np.ascontiguousarray(bounds, dtype=np.float64).reshape(2 * self.d)
+        h = ctypes.c_void_p()
+        _check(self.lib.vote_create(family, self.d, self.k, _ptr(e), _ptr(b), ctypes.byref(h)))
+        self.h = h
+        self.set_option(VOTE_OPT_PRECISION, precision)
+        self.set_option(VOTE_OPT_PRUNE, 1 if prune else 0)
+        if chunk_records:
+            self.set_option(VOTE_OPT_CHUNK_RECORDS, chunk_records)
+        if trace_cap:
+            self.set_option(VOTE_OPT_TRACE_CAP, trace_cap)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_option(self, key: int, value: float):
+        _check(self.lib.vote_set_option(self.h, key, float(value)))
+
+    def set_stream(self, stream):
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(self.lib.vote_set_stream(self.h, ctypes.c_void_p(handle)))
+
+    def levels(self):
+        L = ctypes.c_int()
+        Lj = np.zeros(self.d, np.int32)
+        _check(self.lib.vote_levels(self.h, ctypes.byref(L), _ptr(Lj)))
+        return L.value, Lj
+
+    def _check_surfaces(self, surfaces):
+        if tuple(surfaces.shape[:1]) != (self.np,) or surfaces.ndim != 2:
+            raise ValueError(f"surfaces must be [{self.np}, n]")
+
+    def solve(self, surfaces, want_mask: bool = True):
+        import torch
+        self._check_surfaces(surfaces)
+        if not (surfaces.is_cuda and surfaces.dtype == torch.float64 and surfaces.is_contiguous()):
+            raise ValueError("surfaces must be a contiguous CUDA float64 tensor")
+        n = surfaces.shape[1]
+        bp = np.zeros(self.d)
+        bl = np.zeros(self.d, np.int64)
+        dep = np.zeros(1, np.int64)
+        mask = torch.zeros(max((n + 31) // 32, 1), dtype=torch.int32, device=surfaces.device) if want_mask else None
+        _check(self.lib.vote_solve(self.h, _ptr(surfaces), n, _ptr(bp), _ptr(bl), _ptr(dep), _ptr(mask)))
+        out = dict(best_point=bp, best_leaf=bl, depth=int(dep[0]))
+        if want_mask:
+            out["mask"] = mask[: (n + 31) // 32]
+        return out
+
+    def solve_host(self, surfaces, want_mask: bool = True):
+        """Host buffers in and out (copies inside the call)."""
+        self._check_surfaces(surfaces)
+        if hasattr(surfaces, "data_ptr"):
+            if surfaces.is_cuda or not surfaces.is_contiguous():
+                raise ValueError("surfaces must be a contiguous CPU tensor")
+            n = surfaces.shape[1]
+        else:
+            surfaces = np.ascontiguousarray(surfaces, dtype=np.float64)
+            n = surfaces.shape[1]
+        bp = np.zeros(self.d)
+        bl = np.zeros(self.d, np.int64)
+        dep = np.zeros(1, np.int64)
+        mask = np.zeros(max((n + 31) // 32, 1), np.uint32) if want_mask else None
+        _check(self.lib.vote_solve_host(self.h, _ptr(surfaces), n, _ptr(bp), _ptr(bl), _ptr(dep), _ptr(mask)))
+        out = dict(best_point=bp, best_leaf=bl, depth=int(dep[0]))
+        if want_mask:
+            out["mask"] = mask[: (n + 31) // 32]
+        return out
+
+    def cell_counts(self, surfaces, level: int, coords, want_reach: bool = False):
+        import torch
+        self._check_surfaces(surfaces)
+        n = surfaces.shape[1]
+        c = np.ascontiguousarray(coords, dtype=np.int64).reshape(self.d)
+        ub = np.zeros(1, np.int64)
+        lb = np.zeros(1, np.int64)
+        reach = torch.zeros(max((n + 31) // 32, 1), dtype=torch.int32, device=surfaces.device) if want_reach else None
+        _check(self.lib.vote_cell_counts(self.h, _ptr(surfaces), n, int(level), _ptr(c), _ptr(ub), _ptr(lb),
+                                         _ptr(reach)))
+        if want_reach:
+            return int(ub[0]), int(lb[0]), reach[: (n + 31) // 32]
+        return int(ub[0]), int(lb[0])
+
+    def trace(self, cap: int):
+        lv = np.zeros(max(cap, 1), np.int32)
+        co = np.zeros((max(cap, 1), self.d), np.int64)
+        ub = np.zeros(max(cap, 1), np.int64)
+        lb = np.zeros(max(cap, 1), np.int64)
+        cnt = np.zeros(1, np.int64)
+        _check(self.lib.vote_get_trace(self.h, cap, _ptr(lv), _ptr(co), _ptr(ub), _ptr(lb), _ptr(cnt)))
+        m = int(cnt[0])
+        return dict(level=lv[:m], coords=co[:m], ub=ub[:m], lb=lb[:m])
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self.lib.vote_get_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vote_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mask_words_to_numpy(mask) -> np.ndarray:
+    """CUDA int32 tensor of mask words -> numpy uint32."""
+    if hasattr(mask, "cpu"):
+        mask = mask.cpu().numpy()
+    return np.asarray(mask).view(np.uint32)

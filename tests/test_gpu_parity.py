@@ -1,0 +1,208 @@
+"""Parity of the CUDA path with the oracle, through the C ABI.
+
+Counts, depth, best leaf and inlier mask are integer results decided by FP64
+comparisons and must be bit-exact, in both precision modes (plain FP64 predicate
+and FP32 screen with FP64 recheck).  The best point is the leaf centre computed
+by the same formula on both sides; it is compared exactly as well.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_11810_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_11810_gb300 import build
+    build.build()
+
+
+def vote_mod():
+    from paper_2107_11810_gb300 import vote
+    return vote
+
+
+def dev(p):
+    return torch.from_numpy(np.ascontiguousarray(p.params)).cuda()
+
+
+def gpu_solve(p, precision=1, **kw):
+    v = vote_mod()
+    s = v.Solver(p.family, p.eps, p.bounds, precision=precision, **kw)
+    r = s.solve(dev(p))
+    r["mask"] = v.mask_words_to_numpy(r["mask"])
+    r["stats"] = s.stats()
+    r["solver"] = s
+    return r
+
+
+def assert_same(g, o, n):
+    assert g["depth"] == o["depth"]
+    assert np.array_equal(g["best_leaf"], o["best_leaf"])
+    assert np.array_equal(g["best_point"], o["best_point"])
+    assert np.array_equal(g["mask"][: (n + 31) // 32], o["mask"])
+
+
+def small(family, n, seed):
+    if family == inputs.LINE2D:
+        return inputs.line2d(n=n, inlier_frac=0.2, eps=0.02, seed=seed)
+    if family == inputs.PLANE3D_SPH:
+        return inputs.plane3d(n=n, inlier_frac=0.2, eps=0.06, sigma=0.002, seed=seed)
+    return inputs.pose3dof(n=n, inlier_frac=0.2, eps_xy=1.0, eps_yaw_deg=2.0, noise_deg=0.05, seed=seed)
+
+
+FAMS = [inputs.LINE2D, inputs.PLANE3D_SPH, inputs.POSE3DOF]
+
+
+@pytest.mark.parametrize("family", FAMS)
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n,seed", [(1, 1), (33, 2), (517, 3), (2000, 4)])
+def test_small_parity(family, precision, n, seed):
+    p = small(family, n, seed)
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    g = gpu_solve(p, precision)
+    assert_same(g, o, p.n)
+    assert int(np.unpackbits(g["mask"].view(np.uint8)).sum()) == g["depth"]
+
+
+def test_line2d_workload_parity_both_modes():
+    p = inputs.line2d()                         # 10,000 points, eps = 0.01
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    for prec in (0, 1):
+        g = gpu_solve(p, prec)
+        assert_same(g, o, p.n)
+
+
+def test_pose3dof_1e5_parity():
+    p = inputs.pose3dof(n=100_000, seed=inputs.SEED_BASE + 2)
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    g = gpu_solve(p, 1)
+    assert_same(g, o, p.n)
+
+
+def test_plane3d_parity_several_tiles():
+    p = inputs.plane3d(n=3000, inlier_frac=0.05, eps=0.03, sigma=0.002, seed=9)
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    g1 = gpu_solve(p, 1)
+    g0 = gpu_solve(p, 0)
+    assert_same(g1, o, p.n)
+    assert_same(g0, o, p.n)
+    assert g1["stats"]["tests"] > 0
+
+
+@pytest.mark.parametrize("family", FAMS)
+def test_full_trace_without_pruning_equals_oracle(family):
+    p = small(family, 300, 5)
+    cap = 400_000
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params, flags=oracle.NO_PRUNE, trace_cap=cap)
+    g = gpu_solve(p, 1, prune=False, trace_cap=cap)
+    tg = g["solver"].trace(cap)
+    to = o["trace"]
+    key = lambda l, c: (int(l), tuple(int(x) for x in c))
+    dg = {key(l, c): (int(u), int(b)) for l, c, u, b in zip(tg["level"], tg["coords"], tg["ub"], tg["lb"])}
+    do = {key(l, c): (int(u), int(b)) for l, c, u, b in zip(to["level"], to["coords"], to["ub"], to["lb"])}
+    assert dg == do
+    assert_same(g, o, p.n)
+
+
+@pytest.mark.parametrize("family", FAMS)
+def test_pruned_trace_entries_equal_oracle_cell_counts(family):
+    p = small(family, 1500, 6)
+    g = gpu_solve(p, 1, trace_cap=200_000)
+    tg = g["solver"].trace(200_000)
+    rng = np.random.default_rng(1)
+    for x in rng.choice(len(tg["ub"]), size=min(30, len(tg["ub"])), replace=False):
+        ub, lb = oracle.cell_counts(p.family, p.eps, p.bounds, p.params, tg["level"][x], tg["coords"][x])
+        assert (ub, lb) == (tg["ub"][x], tg["lb"][x])
+
+
+@pytest.mark.parametrize("family", FAMS)
+def test_cell_counts_replay_equals_oracle(family):
+    p = small(family, 2500, 7)
+    v = vote_mod()
+    s = v.Solver(p.family, p.eps, p.bounds)
+    t = dev(p)
+    L, Lj = s.levels()
+    rng = np.random.default_rng(3)
+    for level in sorted(set([0, 1, L // 2, L])):
+        for _ in range(3):
+            coords = [int(rng.integers(0, 2 ** min(level, int(Lj[j])))) for j in range(p.d)]
+            ub, lb, reach = s.cell_counts(t, level, coords, want_reach=True)
+            oub, olb, oreach = oracle.cell_counts(p.family, p.eps, p.bounds, p.params, level, coords, want_reach=True)
+            assert (ub, lb) == (oub, olb)
+            assert np.array_equal(v.mask_words_to_numpy(reach), oreach)
+
+
+@pytest.mark.parametrize("chunk", [1, 7, 1000])
+def test_chunking_does_not_change_results(chunk):
+    p = small(inputs.POSE3DOF, 3000, 8)
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    g = gpu_solve(p, 1, chunk_records=chunk)
+    assert_same(g, o, p.n)
+
+
+def test_empty_and_degenerate_inputs():
+    v = vote_mod()
+    p = small(inputs.LINE2D, 50, 9)
+    s = v.Solver(p.family, p.eps, p.bounds)
+    r = s.solve(torch.zeros((2, 0), dtype=torch.float64, device="cuda"))
+    assert r["depth"] == 0 and np.all(r["best_leaf"] == 0)
+    same = np.repeat(p.params[:, :1], 77, axis=1)
+    r = s.solve(torch.from_numpy(same).cuda())
+    o = oracle.solve(p.family, p.eps, p.bounds, same)
+    assert r["depth"] == o["depth"] == 77
+    assert np.array_equal(r["best_leaf"], o["best_leaf"])
+    # eps covering the whole domain: the root is the only leaf
+    s2 = v.Solver(p.family, [5.0, 5.0], p.bounds)
+    r = s2.solve(dev(p))
+    assert r["depth"] == p.n
+    assert np.all(v.mask_words_to_numpy(r["mask"])[: p.n // 32] == 0xFFFFFFFF)
+
+
+def test_invalid_inputs_return_einval_and_context_survives():
+    v = vote_mod()
+    p = small(inputs.LINE2D, 100, 10)
+    s = v.Solver(p.family, p.eps, p.bounds)
+    bad = p.params.copy()
+    bad[1, 17] = np.inf
+    with pytest.raises(v.VoteError) as ei:
+        s.solve(torch.from_numpy(bad).cuda())
+    assert ei.value.code == 1
+    huge = p.params.copy()
+    huge[0, 3] = 1e300
+    with pytest.raises(v.VoteError):
+        s.solve(torch.from_numpy(huge).cuda())
+    r = s.solve(dev(p))
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    assert r["depth"] == o["depth"]
+
+
+def test_injected_allocation_failure_is_reported_and_recoverable():
+    v = vote_mod()
+    p = small(inputs.POSE3DOF, 500, 11)
+    s = v.Solver(p.family, p.eps, p.bounds)
+    s.set_option(v.VOTE_OPT_FAULT_ALLOC_AT, 3)
+    with pytest.raises(v.VoteError) as ei:
+        s.solve(dev(p))
+    assert ei.value.code == 2
+    s.set_option(v.VOTE_OPT_FAULT_ALLOC_AT, 0)
+    r = s.solve(dev(p))
+    assert r["depth"] == oracle.solve(p.family, p.eps, p.bounds, p.params)["depth"]
+
+
+def test_solve_host_equals_solve_device():
+    v = vote_mod()
+    p = small(inputs.PLANE3D_SPH, 800, 12)
+    s = v.Solver(p.family, p.eps, p.bounds)
+    a = s.solve(dev(p))
+    b = s.solve_host(p.params)
+    assert a["depth"] == b["depth"]
+    assert np.array_equal(a["best_leaf"], b["best_leaf"])
+    assert np.array_equal(v.mask_words_to_numpy(a["mask"]), b["mask"])
