@@ -1,0 +1,326 @@
+"""Benchmark of the voting hot path on GB300.
+
+One step = one complete solve (lift, every level's snap / proximity test /
+prune / split, leaf argmax, inlier-mask replay) of one synthetic problem shaped
+like the paper's workloads; the default is 3D plane fitting with 1,000,000
+points (2 % on a plane, eps = 0.005, (theta, phi, d) space).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--impl gv|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own copy
+of the problem (independent problems, no collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2107_11810_gb300 import inputs  # noqa: E402
+
+WORKLOADS = {
+    "plane3d_n1e6": dict(make=lambda: inputs.plane3d(), desc="3D plane fitting, 1e6 points in the unit cube, "
+                         "2% inliers (sigma 0.001), eps_d=0.005, eps_angle=eps/sqrt3, (theta,phi,d) space"),
+    "pose3dof_n1e6": dict(make=lambda: inputs.pose3dof(), desc="3DoF camera voting, 1e6 matches, 1% inliers, "
+                          "eps 0.25 m / 0.5 deg, (yaw,x,y) space"),
+    "line2d_n1e4": dict(make=lambda: inputs.line2d(), desc="2D line fitting, 1e4 points, 10% inliers, eps 0.01, "
+                        "(m,b) space"),
+}
+# FP32-pipe instructions per (child cell, canonical surface) test, counted from
+# the formulas of each family's residual and comparisons
+INSTR_PER_TEST = {inputs.LINE2D: 7, inputs.PLANE3D_SPH: 10, inputs.POSE3DOF: 14}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return dict(hbm_gbs=float(m["hbm_gbs"]), sm_max_mhz=float(m.get("sm_max_mhz", 2070.0)), src="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["unsampled"], samples=0)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower() == "active"})
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=reasons, samples=len(self.samples))
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("gv_kernels.cu", "gv_device.cuh", "gv_kernels.h"):
+        with open(os.path.join(ROOT, "paper_2107_11810_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """Per-launch DRAM traffic of a kernel from the committed ncu summary, valid only
+    while the kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kh = kernel_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#") and parts[0] == kh and parts[1] == kernel \
+                and parts[2] == workload:
+            return float(parts[3])
+    return None
+
+
+def oracle_sample(p, budget_s: float):
+    """The oracle (plain FP64 C, one core) on a bounded sample of the workload: the
+    first n_s surfaces, n_s grown until one solve takes about budget_s/4 seconds.
+    Returns (tests per second, seconds, n_s, tests)."""
+    import oracle
+    n_s = 200
+    last = None
+    while True:
+        sub = np.ascontiguousarray(p.params[:, :n_s])
+        t0 = time.perf_counter()
+        r = oracle.solve(p.family, p.eps, p.bounds, sub)
+        dt = time.perf_counter() - t0
+        last = (r["stats"][0] / dt, dt, n_s, int(r["stats"][0]))
+        if dt > budget_s / 4 or n_s >= p.n:
+            return last
+        n_s = min(p.n, int(n_s * max(1.5, min(8.0, (budget_s / 4) / max(dt, 1e-3)))))
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    p = w["make"]()
+    import oracle
+    oracle.build()
+    tps, dt, n_s, tests = oracle_sample(p, 8.0)
+    gpu_tests = args.ref_tests_per_problem
+    sub = np.ascontiguousarray(p.params[:, :n_s])
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.solve(p.family, p.eps, p.bounds, sub)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.solve(p.family, p.eps, p.bounds, sub)
+        times.append(time.perf_counter() - t0)
+    tps = tests / statistics.mean(times)
+    # scale: problems/s = oracle tests/s / tests one full-size problem needs
+    value = tps / gpu_tests if gpu_tests else None
+    line = dict(metric="solved problems/sec (3D plane fitting, 1e6 points); surface-cell tests/sec",
+                value=value, unit="problems/s", impl="reference", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1000 * statistics.mean(times), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, desc=w["desc"]),
+                tests_per_s=tps,
+                cpu_baseline=dict(value=value, unit="problems/s", cores=1, kind="oracle",
+                                  sample=f"oracle solve of the first {n_s} of {p.n} surfaces ({tests} tests); "
+                                         f"problems/s = oracle tests/s / {gpu_tests} tests per full problem"),
+                e2e=dict(value=value, unit="problems/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gv", choices=["gv", "reference"])
+    ap.add_argument("--workload", default="plane3d_n1e6", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--ref-tests-per-problem", type=float, default=0.0)
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        if not args.ref_tests_per_problem:
+            args.ref_tests_per_problem = REF_TESTS.get(args.workload, 0.0)
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_2107_11810_gb300 import build, vote
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    w = WORKLOADS[args.workload]
+    p = w["make"]()
+    stream = torch.cuda.current_stream()
+    s = vote.Solver(p.family, p.eps, p.bounds, precision=args.precision, stream=stream,
+                    chunk_records=args.chunk or None)
+    s.set_option(vote.VOTE_OPT_KERNEL_TIMING, 1)
+    surf = torch.from_numpy(p.params).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        r = s.solve(surf)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times, tests, kt = [], [], {}
+    launches = 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                      # L2 flush between timed steps
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = s.solve(surf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1000.0)
+            st = s.stats()
+            tests.append(st["tests"])
+            launches += st["launches"]
+            for k, v in s.kernel_times().items():
+                a = kt.setdefault(k, [0.0, 0, 0.0])
+                a[0] += v[0]; a[1] += v[1]; a[2] += v[2]
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    depth, leaf = r["depth"], r["best_leaf"].tolist()
+    pk = peaks()
+    value = world * args.steps / total
+    tests_per_problem = statistics.mean(tests)
+    # roofline of the dominant kernel class
+    dom = max(("test_count", "test_emit"), key=lambda k: kt[k][0])
+    ms, nl, by = kt[dom]
+    avg_s = ms / 1000.0 / max(nl, 1)
+    if dom == "test_count" and args.precision == 1:
+        instr = INSTR_PER_TEST[p.family] * tests_per_problem * args.steps / max(nl, 1)
+        achieved = instr / avg_s / 1e12
+        alu_peak = 152 * 128 * pk["sm_max_mhz"] * 1e6 / 1e12
+        roof = dict(bound="alu", achieved=achieved, peak=alu_peak, unit="TFP32-instr/s",
+                    frac=achieved / alu_peak, kernel="k_test<count>",
+                    peak_src="152 SMs x 128 FP32 lanes x max SM clock (instructions/s, no FMA doubling)",
+                    traffic=recorded_traffic("k_test_count", args.workload), bytes_per_launch=by / max(nl, 1))
+    else:
+        achieved = by / max(nl, 1) / avg_s / 1e9
+        roof = dict(bound="hbm", achieved=achieved, peak=pk["hbm_gbs"], unit="GB/s",
+                    frac=achieved / pk["hbm_gbs"], kernel=f"k_test<{dom[5:]}>", peak_src=pk["src"],
+                    traffic=recorded_traffic("k_" + dom, args.workload), bytes_per_launch=by / max(nl, 1))
+    roof["share_of_step"] = kt[dom][0] / 1000.0 / total * world
+    # end to end through the public API with host buffers
+    pinned = torch.from_numpy(p.params).pin_memory()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rh = s.solve_host(pinned)
+        e2e_times.append(time.perf_counter() - t0)
+    assert rh["depth"] == depth
+    e2e = dict(value=1.0 / statistics.mean(e2e_times), unit="problems/s",
+               h2d_bytes_per_step=int(p.params.nbytes), d2h_bytes_per_step=int(((p.n + 31) // 32) * 4))
+    out = dict(metric="solved problems/sec (3D plane fitting, 1e6 points); surface-cell tests/sec",
+               value=value, unit="problems/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+               ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+               dtype="f32+f64" if args.precision == 1 else "f64", data="synthetic",
+               config=dict(workload=args.workload, desc=w["desc"], n=p.n, l2="flushed between timed steps",
+                           precision="FP32 screen + FP64 recheck" if args.precision == 1 else "FP64"),
+               tests_per_s=world * sum(tests) / total, tests_per_problem=tests_per_problem,
+               result=dict(depth=depth, best_leaf=leaf, best_point=r["best_point"].tolist()),
+               gpu_launches=launches, roofline=roof, e2e=e2e, clocks=clk.summary(),
+               kernel_ms={k: round(v[0] / args.steps, 3) for k, v in kt.items() if v[1]})
+    if not args.no_fp64 and args.precision == 1:
+        s.set_option(vote.VOTE_OPT_PRECISION, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r64 = s.solve(surf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1000.0
+        same = (r64["depth"] == depth and r64["best_leaf"].tolist() == leaf and
+                torch.equal(r64["mask"], r["mask"]))
+        out["fp64_plain"] = dict(value=1.0 / t64, unit="problems/s", tests_per_s=s.stats()["tests"] / t64,
+                                 identical_results=bool(same), speedup_fp32_screen=value / world * t64)
+        s.set_option(vote.VOTE_OPT_PRECISION, 1)
+    if rank == 0 and not args.no_cpu:
+        try:
+            tps, dt, n_s, ot = oracle_sample(p, 16.0)
+            out["cpu_baseline"] = dict(value=tps / tests_per_problem, unit="problems/s", cores=1, kind="oracle",
+                                       tests_per_s=tps,
+                                       sample=f"oracle solve of the first {n_s} of {p.n} surfaces "
+                                              f"({ot} tests, {dt:.1f} s); problems/s = oracle tests/s / "
+                                              f"{tests_per_problem:.4g} tests per full problem (GPU count)")
+        except Exception as e:   # the baseline must not sink the GPU line
+            out["cpu_baseline"] = dict(value=None, unit="problems/s", cores=1, kind="oracle", sample=f"failed: {e}")
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# tests per full problem measured by the GPU path (used to scale the reference
+# arm's oracle sample to problems/s); refreshed from bench runs
+REF_TESTS = {"plane3d_n1e6": 0.0, "pose3dof_n1e6": 3.538858716e9, "line2d_n1e4": 8.324422e6}
+
+if __name__ == "__main__":
+    main()

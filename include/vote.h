@@ -80,9 +80,20 @@ typedef enum {
     VOTE_OPT_GROUP = 5,       /* merging of identical canonical surfaces:
                                  0 = off, 1 = on (default 0; results do not depend
                                  on it)                                             */
-    VOTE_OPT_FAULT_ALLOC_AT = 6 /* test hook: fail the k-th device allocation with
+    VOTE_OPT_FAULT_ALLOC_AT = 6, /* test hook: fail the k-th device allocation with
                                  VOTE_ENOMEM (0 = off)                               */
+    VOTE_OPT_INITIAL_LB = 7,  /* a known lower bound on the best depth (warm start of
+                                 the B&B bound, e.g. from a previous frame); must not
+                                 exceed the true maximum depth; default 0            */
+    VOTE_OPT_KERNEL_TIMING = 8 /* 1 = time each kernel class with CUDA events on the
+                                 context's stream (see vote_get_kernel_times)        */
 } vote_option;
+
+/* Kernel classes reported by vote_get_kernel_times. */
+enum {
+    VOTE_K_LIFT = 0, VOTE_K_CELL_GEO = 1, VOTE_K_TEST_COUNT = 2, VOTE_K_TEST_EMIT = 3,
+    VOTE_K_CHILDREN = 4, VOTE_K_REPLAY = 5, VOTE_K_GROUP = 6, VOTE_K_CLASSES = 8
+};
 
 /* Per-solve counters (vote_get_stats). */
 typedef struct {
@@ -94,6 +105,7 @@ typedef struct {
     int64_t chunks;          /* expansion steps                                   */
     int64_t leaves;          /* leaves evaluated                                  */
     int64_t peak_records;    /* largest record count held at one level            */
+    int64_t launches;        /* kernels launched                                  */
     double  seconds;         /* wall time of the last solve                       */
 } vote_stats;
 
@@ -155,6 +167,12 @@ vote_status vote_get_trace(vote_ctx *ctx, int64_t cap, int32_t *level, int64_t *
 
 /* Counters of the last solve. */
 vote_status vote_get_stats(vote_ctx *ctx, vote_stats *out);
+
+/* Per kernel class (VOTE_K_*): summed device milliseconds, launches and
+ * algorithmic bytes (records read/written, as defined per class) of the last
+ * solve, measured with CUDA events when VOTE_OPT_KERNEL_TIMING is 1.  Arrays of
+ * VOTE_K_CLASSES entries (host). */
+vote_status vote_get_kernel_times(vote_ctx *ctx, double *ms, int64_t *launches, double *bytes);
 
 /* Message for the last error on this host thread (static storage). */
 const char *vote_last_error(void);

@@ -69,7 +69,15 @@ struct vote_ctx {
     int device = 0;
     cudaStream_t stream = 0;
     int precision = 1, prune = 1, group = 0;
-    int64_t chunk_records = 1 << 23;
+    int64_t chunk_records = 1 << 25;
+    uint32_t initial_lb = 0;
+    int kernel_timing = 0;
+    cudaEvent_t ev[6] = {};
+    int ev_pending = 0;        // events of the previous chunk not yet read
+    int ev_emit = 0;           // ... and whether it had an emit pass
+    double kms[VOTE_K_CLASSES] = {};
+    int64_t klaunch[VOTE_K_CLASSES] = {};
+    double kbytes[VOTE_K_CLASSES] = {};
     int64_t trace_cap = 0;
     int64_t fault_alloc_at = 0, alloc_count = 0;
     LevelStore ls[GV_MAXL + 1];
@@ -309,6 +317,27 @@ static vote_status read_scalars(vote_ctx *c) {
 }
 
 // ---------------------------------------------------------------------------
+// kernel timing (CUDA events on the context's stream, read after the stream has
+// passed them)
+// ---------------------------------------------------------------------------
+static void ev_record(vote_ctx *c, int i) {
+    if (c->kernel_timing) cudaEventRecord(c->ev[i], c->stream);
+}
+
+static void ev_collect(vote_ctx *c) {
+    if (!c->kernel_timing || !c->ev_pending) return;
+    float ms;
+    const int cls[4] = {VOTE_K_CELL_GEO, VOTE_K_TEST_COUNT, VOTE_K_CHILDREN, VOTE_K_TEST_EMIT};
+    int last = c->ev_emit ? 4 : 3;
+    for (int i = 0; i < last; ++i)
+        if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) {
+            c->kms[cls[i]] += ms;
+            c->klaunch[cls[i]] += 1;
+        }
+    c->ev_pending = 0;
+}
+
+// ---------------------------------------------------------------------------
 // search
 // ---------------------------------------------------------------------------
 static vote_status expand_chunk(vote_ctx *c, int l) {
@@ -329,6 +358,7 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
         c0 = c1 - K > 0 ? c1 - K : 0;
         CK(cudaMemcpyAsync(c->h_tmp, (uint64_t *)S.rbeg.p + c0, 8, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        ev_collect(c);
         r0 = (int64_t)*c->h_tmp;
         if (r1 - r0 <= 2 * c->chunk_records || K == 1) break;
         K = K / 2;
@@ -385,13 +415,23 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     ch.prune = c->prune;
     ch.precision = c->precision;
 
+    int rec_bytes = 4 * (P.nd + P.le + 2);
+    ev_record(c, 0);
     launch_cell_geo(ch, c->stream);
+    ev_record(c, 1);
     launch_test(ch, false, c->stream);
+    ev_record(c, 2);
     launch_child_lbmax(ch, c->stream);
     launch_child_alloc(ch, (uint32_t *)c->keepflag.p, (uint32_t *)c->recn.p, (unsigned long long *)c->bsums.p,
                        c->stream);
+    ev_record(c, 3);
+    c->ev_pending = c->kernel_timing;
+    c->ev_emit = 0;
+    c->kbytes[VOTE_K_TEST_COUNT] += (double)nr * (rec_bytes + 1);
+    c->kbytes[VOTE_K_CELL_GEO] += (double)nc * (8 + 4);
     CK(cudaGetLastError());
     c->stats.chunks++;
+    c->stats.launches += lev.leaf_children ? 4 : 6;
     c->stats.cells += nc;
     c->stats.records += nr;
     S.ncells = c0;
@@ -403,7 +443,13 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     CK(cudaMemcpyAsync(&c->h_sc->n_cells, &dsc(c)->n_cells, 16, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     int64_t new_cells = (int64_t)c->h_sc->n_cells, new_recs = (int64_t)c->h_sc->n_recs;
-    if (new_recs > 0) launch_test(ch, true, c->stream);
+    if (new_recs > 0) {
+        launch_test(ch, true, c->stream);
+        c->stats.launches += 1;
+        ev_record(c, 4);
+        c->ev_emit = c->kernel_timing;
+        c->kbytes[VOTE_K_TEST_EMIT] += (double)nr * (rec_bytes + 1) + (double)new_recs * rec_bytes;
+    }
     CK(cudaGetLastError());
     c->ls[l + 1].ncells = new_cells;
     c->ls[l + 1].nrecs = new_recs;
@@ -414,11 +460,20 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
 static vote_status replay(vote_ctx *c, const double *surfaces, int64_t n, int lam, uint64_t key, uint32_t *reach,
                           int64_t *ub, int64_t *lb) {
     CK(cudaMemsetAsync(&dsc(c)->replay_ub, 0, 16, c->stream));
+    ev_record(c, 0);
     if (lam > 0) launch_path_geo(c->P, (const Level *)c->levs_dev.p, lam, key, (PathStep *)c->path.p, c->stream);
     launch_replay(c->P, (const Level *)c->levs_dev.p, (const PathStep *)c->path.p, lam, surfaces, n, reach,
                   dsc(c), c->stream);
+    c->stats.launches += lam > 0 ? 2 : 1;
+    ev_record(c, 5);
     CK(cudaGetLastError());
     TRY(read_scalars(c));
+    if (c->kernel_timing) {
+        float ms;
+        if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]) == cudaSuccess) c->kms[VOTE_K_REPLAY] += ms;
+        c->klaunch[VOTE_K_REPLAY] += 1;
+        c->kbytes[VOTE_K_REPLAY] += (double)n * (8 * c->P.np) + (double)((n + 31) / 32) * 4;
+    }
     *ub = (int64_t)c->h_sc->replay_ub;
     *lb = (int64_t)c->h_sc->replay_lb;
     return VOTE_OK;
@@ -439,6 +494,9 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         return VOTE_EUNSUPPORTED;
     }
     CK(cudaMemsetAsync(c->scal.p, 0, sizeof(Scalars), c->stream));
+    if (c->initial_lb) CK(cudaMemcpyAsync(&dsc(c)->best_lb, &c->initial_lb, 4, cudaMemcpyHostToDevice, c->stream));
+    for (int i = 0; i < VOTE_K_CLASSES; ++i) c->kms[i] = c->kbytes[i] = 0, c->klaunch[i] = 0;
+    c->ev_pending = 0;
     c->trace_written = 0;
     c->trace_overflow = false;
     for (int l = 0; l <= P.L; ++l) c->ls[l].ncells = c->ls[l].nrecs = 0;
@@ -448,7 +506,10 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         dep = n;                                   // the domain is a leaf: every surface counts
     } else if (n > 0) {
         TRY(ensure_level(c, 0, (size_t)n, 1));
+        ev_record(c, 0);
         launch_lift(P, c->lev[0], surfaces, n, rec_view(c, 0), dsc(c), c->stream);
+        c->stats.launches += 1;
+        ev_record(c, 5);
         CK(cudaGetLastError());
         uint64_t key0 = 0, rb0 = 0;
         uint32_t cnt0 = (uint32_t)n;
@@ -460,6 +521,12 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         c->ls[0].ncells = 1;
         c->ls[0].nrecs = n;
         TRY(read_scalars(c));
+        if (c->kernel_timing) {
+            float ms;
+            if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]) == cudaSuccess) c->kms[VOTE_K_LIFT] += ms;
+            c->klaunch[VOTE_K_LIFT] += 1;
+            c->kbytes[VOTE_K_LIFT] += (double)n * (8 * P.np + 4 * (P.nd + P.le + 2));
+        }
         if (c->h_sc->err) {
             set_err("surface parameters are not finite or out of the representable range");
             return VOTE_EINVAL;
@@ -475,6 +542,7 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
             TRY(expand_chunk(c, l));
         }
         TRY(read_scalars(c));
+        ev_collect(c);
         if (c->h_sc->err) {
             set_err("internal: residual out of range (err %u)", c->h_sc->err);
             return VOTE_EINTERNAL;
@@ -599,6 +667,16 @@ vote_status vote_set_option(vote_ctx *c, int key, double v) {
         c->fault_alloc_at = (int64_t)v;
         c->alloc_count = 0;
         return VOTE_OK;
+    case VOTE_OPT_INITIAL_LB:
+        if (!(v >= 0 && v < 4294967295.0)) break;
+        c->initial_lb = (uint32_t)v;
+        return VOTE_OK;
+    case VOTE_OPT_KERNEL_TIMING:
+        if (v != 0 && v != 1) break;
+        if (v == 1 && !c->ev[0])
+            for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&c->ev[i]));
+        c->kernel_timing = (int)v;
+        return VOTE_OK;
     default:
         set_err("unknown option %d", key);
         return VOTE_EINVAL;
@@ -693,6 +771,16 @@ vote_status vote_get_trace(vote_ctx *c, int64_t cap, int32_t *level, int64_t *co
     return VOTE_OK;
 }
 
+vote_status vote_get_kernel_times(vote_ctx *c, double *ms, int64_t *launches, double *bytes) {
+    if (!c) { set_err("null context"); return VOTE_EINVAL; }
+    for (int i = 0; i < VOTE_K_CLASSES; ++i) {
+        if (ms) ms[i] = c->kms[i];
+        if (launches) launches[i] = c->klaunch[i];
+        if (bytes) bytes[i] = c->kbytes[i];
+    }
+    return VOTE_OK;
+}
+
 vote_status vote_get_stats(vote_ctx *c, vote_stats *out) {
     if (!c || !out) { set_err("invalid arguments"); return VOTE_EINVAL; }
     *out = c->stats;
@@ -712,6 +800,8 @@ void vote_destroy(vote_ctx *c) {
                       &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp};
     for (DevBuf *b : bufs) release(c, *b);
     cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 6; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_tmp) cudaFreeHost(c->h_tmp);
     delete c;

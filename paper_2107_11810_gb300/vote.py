@@ -23,12 +23,14 @@ _lib = None
 
 VOTE_OPT_PRECISION, VOTE_OPT_PRUNE, VOTE_OPT_CHUNK_RECORDS = 1, 2, 3
 VOTE_OPT_TRACE_CAP, VOTE_OPT_GROUP, VOTE_OPT_FAULT_ALLOC_AT = 4, 5, 6
+VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING = 7, 8
+KERNEL_CLASSES = ["lift", "cell_geo", "test_count", "test_emit", "children", "replay", "group", "spare"]
 STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
           5: "VOTE_ETIMEOUT", 6: "VOTE_EUNSUPPORTED", 7: "VOTE_EINTERNAL"}
 NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4}
 EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
-           "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_last_error",
-           "vote_destroy"]
+           "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_get_kernel_times",
+           "vote_last_error", "vote_destroy"]
 
 
 class VoteError(RuntimeError):
@@ -40,7 +42,8 @@ class VoteError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int64), ("cells", ctypes.c_int64), ("records", ctypes.c_int64),
                 ("tests", ctypes.c_int64), ("rechecks", ctypes.c_int64), ("chunks", ctypes.c_int64),
-                ("leaves", ctypes.c_int64), ("peak_records", ctypes.c_int64), ("seconds", ctypes.c_double)]
+                ("leaves", ctypes.c_int64), ("peak_records", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("seconds", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,6 +68,7 @@ def load(path: str | None = None):
             lib.vote_levels.argtypes = [P, P, P]
             lib.vote_get_trace.argtypes = [P, i64, P, P, P, P, P]
             lib.vote_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+            lib.vote_get_kernel_times.argtypes = [P, P, P, P]
             lib.vote_last_error.restype = ctypes.c_char_p
             lib.vote_last_error.argtypes = []
             lib.vote_destroy.argtypes = [P]
@@ -192,6 +196,15 @@ class Solver:
         _check(self.lib.vote_get_trace(self.h, cap, _ptr(lv), _ptr(co), _ptr(ub), _ptr(lb), _ptr(cnt)))
         m = int(cnt[0])
         return dict(level=lv[:m], coords=co[:m], ub=ub[:m], lb=lb[:m])
+
+    def kernel_times(self) -> dict:
+        """{class: (ms, launches, algorithmic bytes)} of the last solve (needs
+        VOTE_OPT_KERNEL_TIMING = 1)."""
+        ms = np.zeros(8)
+        nl = np.zeros(8, np.int64)
+        by = np.zeros(8)
+        _check(self.lib.vote_get_kernel_times(self.h, _ptr(ms), _ptr(nl), _ptr(by)))
+        return {k: (float(ms[i]), int(nl[i]), float(by[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def stats(self) -> dict:
         s = Stats()

@@ -99,8 +99,8 @@ def test_plane3d_parity_several_tiles():
 
 @pytest.mark.parametrize("family", FAMS)
 def test_full_trace_without_pruning_equals_oracle(family):
-    p = small(family, 300, 5)
-    cap = 400_000
+    p = small(family, 300 if family != inputs.PLANE3D_SPH else 60, 5)
+    cap = 4_000_000
     o = oracle.solve(p.family, p.eps, p.bounds, p.params, flags=oracle.NO_PRUNE, trace_cap=cap)
     g = gpu_solve(p, 1, prune=False, trace_cap=cap)
     tg = g["solver"].trace(cap)
