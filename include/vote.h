@@ -174,6 +174,10 @@ vote_status vote_get_stats(vote_ctx *ctx, vote_stats *out);
  * VOTE_K_CLASSES entries (host). */
 vote_status vote_get_kernel_times(vote_ctx *ctx, double *ms, int64_t *launches, double *bytes);
 
+/* Per-level work of the last solve: cells[l] expanded and records[l] tested at
+ * level l, for l in [0, L) (host arrays of at least L entries). */
+vote_status vote_get_level_stats(vote_ctx *ctx, int64_t *cells, int64_t *records);
+
 /* Message for the last error on this host thread (static storage). */
 const char *vote_last_error(void);
 

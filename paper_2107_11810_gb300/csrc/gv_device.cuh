@@ -154,6 +154,13 @@ template <> struct Fam<FAM_LINE2D> {
         fo[0] = dsub(dsub(f[0], dmul(t[0], dpsi[0])), sh[1]);
     }
     __device__ static void lipschitz64(const double *t, double *lam) { lam[0] = fabs(t[0]); }
+    // residual before subtracting the dependent-coordinate shift (same op order)
+    __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
+        p[0] = dsub(f[0], dmul(t[0], dpsi[0]));
+    }
+    __device__ static void partial32(const float *f, const float *t, const float *dpsi, float *p) {
+        p[0] = f[0] - t[0] * dpsi[0];
+    }
     // FP32 screen: residual, and the magnitude sum its rounding error scales with
     // (dpsi_max/sh_max: largest |dpsi| and |shift| over the cell's children)
     __device__ static void residual32(const float *f, const float *t, const float *dpsi, const float *sh,
@@ -189,6 +196,12 @@ template <> struct Fam<FAM_PLANE3D_SPH> {
                                       double *fo) {
         double s = dadd(dadd(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1])), dmul(t[2], dpsi[2]));
         fo[0] = dsub(dadd(f[0], s), sh[2]);
+    }
+    __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
+        p[0] = dadd(f[0], dadd(dadd(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1])), dmul(t[2], dpsi[2])));
+    }
+    __device__ static void partial32(const float *f, const float *t, const float *dpsi, float *p) {
+        p[0] = f[0] + __fmaf_rn(t[2], dpsi[2], __fmaf_rn(t[1], dpsi[1], t[0] * dpsi[0]));
     }
     __device__ static void lipschitz64(const double *t, double *lam) {
         double xy = dadd(dmul(t[0], t[0]), dmul(t[1], t[1]));
@@ -234,6 +247,14 @@ template <> struct Fam<FAM_POSE3DOF> {
                                       double *fo) {
         fo[0] = dsub(dsub(f[0], dsub(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1]))), sh[1]);
         fo[1] = dsub(dsub(f[1], dadd(dmul(t[0], dpsi[1]), dmul(t[1], dpsi[0]))), sh[2]);
+    }
+    __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
+        p[0] = dsub(f[0], dsub(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1])));
+        p[1] = dsub(f[1], dadd(dmul(t[0], dpsi[1]), dmul(t[1], dpsi[0])));
+    }
+    __device__ static void partial32(const float *f, const float *t, const float *dpsi, float *p) {
+        p[0] = f[0] - __fmaf_rn(t[0], dpsi[0], -(t[1] * dpsi[1]));
+        p[1] = f[1] - __fmaf_rn(t[0], dpsi[1], t[1] * dpsi[0]);
     }
     __device__ static void lipschitz64(const double *t, double *lam) {
         double r = dsqrt(dadd(dmul(t[0], t[0]), dmul(t[1], t[1])));

@@ -78,6 +78,7 @@ struct vote_ctx {
     double kms[VOTE_K_CLASSES] = {};
     int64_t klaunch[VOTE_K_CLASSES] = {};
     double kbytes[VOTE_K_CLASSES] = {};
+    int64_t lv_cells[GV_MAXL] = {}, lv_recs[GV_MAXL] = {};
     int64_t trace_cap = 0;
     int64_t fault_alloc_at = 0, alloc_count = 0;
     LevelStore ls[GV_MAXL + 1];
@@ -434,6 +435,8 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     c->stats.launches += lev.leaf_children ? 4 : 6;
     c->stats.cells += nc;
     c->stats.records += nr;
+    c->lv_cells[l] += nc;
+    c->lv_recs[l] += nr;
     S.ncells = c0;
     S.nrecs = r0;
     if (lev.leaf_children) {
@@ -484,6 +487,7 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
     auto t0 = std::chrono::steady_clock::now();
     const Problem &P = c->P;
     std::memset(&c->stats, 0, sizeof(c->stats));
+    for (int l = 0; l < GV_MAXL; ++l) c->lv_cells[l] = c->lv_recs[l] = 0;
     c->stats.levels = P.L;
     if (n < 0 || !best_point || !depth || (n > 0 && !surfaces)) {
         set_err("invalid arguments");
@@ -777,6 +781,15 @@ vote_status vote_get_kernel_times(vote_ctx *c, double *ms, int64_t *launches, do
         if (ms) ms[i] = c->kms[i];
         if (launches) launches[i] = c->klaunch[i];
         if (bytes) bytes[i] = c->kbytes[i];
+    }
+    return VOTE_OK;
+}
+
+vote_status vote_get_level_stats(vote_ctx *c, int64_t *cells, int64_t *records) {
+    if (!c) { set_err("null context"); return VOTE_EINVAL; }
+    for (int l = 0; l < c->P.L; ++l) {
+        if (cells) cells[l] = c->lv_cells[l];
+        if (records) records[l] = c->lv_recs[l];
     }
     return VOTE_OK;
 }

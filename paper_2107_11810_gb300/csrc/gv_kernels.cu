@@ -198,228 +198,6 @@ __device__ __forceinline__ int test64(const Level &lev, const double *f, const d
     return ub | (lb << 1);
 }
 
-template <int FAM, int PREC, bool EMIT>
-__global__ void __launch_bounds__(256) k_test(Chunk c) {
-    using F = Fam<FAM>;
-    constexpr int NS = 1 << F::D;
-    const Problem &P = c.P;
-    const Level &lev = c.lev;
-    const int lane = threadIdx.x & 31;
-    const int smask = lev.split_mask;
-    int64_t r = c.r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool act = false;
-    int cl = 0;
-    uint32_t mult = 0;
-    int32_t qf[F::ND], qt[F::LE];
-    if (r < c.r1) {
-        cl = (int)((int64_t)c.in.cell[r] - c.c0);
-        act = c.alive[cl] != 0;
-        if (act) {
-#pragma unroll
-            for (int j = 0; j < F::ND; ++j) qf[j] = c.in.qf[j][r];
-#pragma unroll
-            for (int m = 0; m < F::LE; ++m) qt[m] = c.in.qt[m][r];
-            mult = c.in.mult[r];
-        }
-    }
-    unsigned ubm = 0, lbm = 0;
-    unsigned long long ntest = 0, nrecheck = 0;
-    // FP64 canonical values of the record
-    double f64[F::ND], t64[F::LE], R64[F::ND];
-    bool have64 = false;
-    auto need64 = [&]() {
-        if (have64) return;
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) f64[j] = dmul((double)qf[j], P.s_f[j]);
-#pragma unroll
-        for (int m = 0; m < F::LE; ++m) t64[m] = dmul((double)qt[m], lev.s_t[m]);
-        radius64<FAM>(lev, t64, R64);
-        have64 = true;
-    };
-    float f32[F::ND], t32[F::LE], R32[F::ND], Eub[F::ND], Elb[F::ND];
-    if (act && PREC == 1) {
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) f32[j] = (float)qf[j] * P.s_ff[j];
-#pragma unroll
-        for (int m = 0; m < F::LE; ++m) t32[m] = (float)qt[m] * lev.s_tf[m];
-        float lam[F::ND * F::K];
-        F::lipschitz32(t32, lam);
-        float shmax[F::D], err[F::ND];
-#pragma unroll
-        for (int j = 0; j < F::D; ++j) shmax[j] = ((smask >> j) & 1) ? lev.h1f[j] : 0.0f;
-        F::errmag32(f32, t32, c.geo32 + ((size_t)cl * (NS + 1) + NS) * F::NB, shmax, err);
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) {
-            float rr = lev.Rbasef[j];
-#pragma unroll
-            for (int i = 0; i < F::K; ++i) rr = rr + lam[j * F::K + i] * lev.h1f[i];
-            R32[j] = rr + lev.A1f[j];
-            Eub[j] = kScreenRel * (err[j] + R32[j]);
-            Elb[j] = kScreenRel * (err[j] + fabsf(lev.rlbf[j]));
-        }
-    }
-    if (!EMIT) {
-        if (act) {
-            if (PREC == 0) need64();
-            for (int s = 0; s < NS; ++s) {
-                if (s & ~smask) continue;
-                ++ntest;
-                int res;
-                if (PREC == 0) {
-                    double fo[F::ND];
-                    res = test64<FAM>(lev, f64, t64, R64, c.geo64 + ((size_t)cl * NS + s) * F::NB, s, fo);
-                } else {
-                    float sh[F::D], fo[F::ND];
-                    shifts32<FAM>(lev, s, sh);
-                    F::residual32(f32, t32, c.geo32 + ((size_t)cl * (NS + 1) + s) * F::NB, sh, fo);
-                    int ub_fail = 0, ub_unsure = 0, lb_fail = 0, lb_unsure = 0;
-#pragma unroll
-                    for (int j = 0; j < F::ND; ++j) {
-                        float a = fabsf(fo[j]);
-                        ub_fail |= a - Eub[j] > R32[j];
-                        ub_unsure |= !(a + Eub[j] < R32[j]);
-                        lb_fail |= a - Elb[j] > lev.rlbf[j];
-                        lb_unsure |= !(a + Elb[j] < lev.rlbf[j]);
-                    }
-                    if (ub_fail) {
-                        res = 0;
-                    } else if (!ub_unsure && (lb_fail || !lb_unsure)) {
-                        res = 1 | ((lb_fail ? 0 : 1) << 1);
-                    } else {
-                        need64();
-                        ++nrecheck;
-                        double fo64[F::ND];
-                        res = test64<FAM>(lev, f64, t64, R64, c.geo64 + ((size_t)cl * NS + s) * F::NB, s, fo64);
-                    }
-                }
-                ubm |= (unsigned)(res & 1) << s;
-                lbm |= (unsigned)((res >> 1) & 1) << s;
-            }
-        }
-        // per-child sums: warp-reduced when the whole warp works on one cell
-        unsigned actb = __ballot_sync(kFull, act);
-        if (actb) {
-            int leader = __ffs(actb) - 1;
-            int cl0 = __shfl_sync(kFull, cl, leader);
-            bool uniform = __all_sync(kFull, !act || cl == cl0);
-            for (int s = 0; s < NS; ++s) {
-                if (s & ~smask) continue;
-                unsigned pu = act && ((ubm >> s) & 1);
-                unsigned pl = act && ((lbm >> s) & 1);
-                unsigned vub = pu ? mult : 0u, vlb = pl ? mult : 0u;
-                if (uniform) {
-                    vub = __reduce_add_sync(kFull, vub);
-                    vlb = __reduce_add_sync(kFull, vlb);
-                    unsigned vn = __reduce_add_sync(kFull, pu);
-                    if (lane == leader) {
-                        uint32_t *b = c.cnt + ((size_t)cl0 * NS + s) * 3;
-                        if (vub) atomicAdd(b, vub);
-                        if (vlb) atomicAdd(b + 1, vlb);
-                        if (vn) atomicAdd(b + 2, vn);
-                    }
-                } else if (act && pu) {
-                    uint32_t *b = c.cnt + ((size_t)cl * NS + s) * 3;
-                    atomicAdd(b, vub);
-                    if (vlb) atomicAdd(b + 1, vlb);
-                    atomicAdd(b + 2, 1u);
-                }
-            }
-        }
-        if (r < c.r1) c.passmask[r - c.r0] = (uint8_t)ubm;
-    } else {
-        if (act) ubm = c.passmask[r - c.r0];
-        unsigned actb = __ballot_sync(kFull, act && ubm != 0);
-        if (actb) {
-            int leader = __ffs(actb) - 1;
-            int cl0 = __shfl_sync(kFull, cl, leader);
-            bool uniform = __all_sync(kFull, !(act && ubm) || cl == cl0);
-            for (int s = 0; s < NS; ++s) {
-                if (s & ~smask) continue;
-                bool want = act && ((ubm >> s) & 1);
-                int ci = -1;
-                if (want) {
-                    ci = c.child_idx[(size_t)cl * NS + s];
-                    want = ci >= 0;
-                }
-                unsigned bal = __ballot_sync(kFull, want);
-                if (!bal) continue;
-                unsigned pos = 0;
-                if (uniform) {
-                    int ldr = __ffs(bal) - 1;
-                    unsigned base = 0;
-                    if (lane == ldr) base = atomicAdd(&c.cursor[(size_t)cl0 * NS + s], (unsigned)__popc(bal));
-                    base = __shfl_sync(kFull, base, ldr);
-                    pos = base + __popc(bal & ((1u << lane) - 1u));
-                } else if (want) {
-                    pos = atomicAdd(&c.cursor[(size_t)cl * NS + s], 1u);
-                }
-                if (!want) continue;
-                // residual at the child centre, snapped for the child's level
-                int32_t qn[F::ND];
-                bool done = false;
-                if (PREC == 1) {
-                    float sh[F::D], fo[F::ND];
-                    shifts32<FAM>(lev, s, sh);
-                    F::residual32(f32, t32, c.geo32 + ((size_t)cl * (NS + 1) + s) * F::NB, sh, fo);
-                    done = true;
-#pragma unroll
-                    for (int j = 0; j < F::ND; ++j) {
-                        float y = fo[j] * P.inv_s_ff[j];
-                        float q = rintf(y);
-                        float margin = 0.5f - fabsf(y - q);
-                        float e = Eub[j] * P.inv_s_ff[j];
-                        if (margin > e && fabsf(q) < 1.6e7f) qn[j] = (int32_t)q;
-                        else done = false;
-                    }
-                    if (!done) ++nrecheck;
-                }
-                if (!done) {
-                    need64();
-                    double sh[F::D], fo[F::ND];
-                    shifts64<FAM>(lev, s, sh);
-                    F::residual64(f64, t64, c.geo64 + ((size_t)cl * NS + s) * F::NB, sh, fo);
-#pragma unroll
-                    for (int j = 0; j < F::ND; ++j) {
-                        double q = rint(dmul(fo[j], P.inv_s_f[j]));
-                        if (!(fabs(q) < 1073741824.0)) {
-                            atomicOr(&c.sc->err, 2u);
-                            q = 0.0;
-                        }
-                        qn[j] = (int32_t)q;
-                    }
-                }
-                uint64_t at = c.next_cells.rbeg[ci] + pos;
-#pragma unroll
-                for (int j = 0; j < F::ND; ++j) c.out.qf[j][at] = qn[j];
-#pragma unroll
-                for (int m = 0; m < F::LE; ++m) c.out.qt[m][at] = lev.st_ratio_log2[m] ? resnap_half(qt[m]) : qt[m];
-                c.out.mult[at] = mult;
-                c.out.cell[at] = (uint32_t)ci;
-            }
-        }
-    }
-    // counters
-    ntest = __reduce_add_sync(kFull, (unsigned)ntest);
-    nrecheck = __reduce_add_sync(kFull, (unsigned)nrecheck);
-    if (lane == 0) {
-        if (!EMIT && ntest) atomicAdd(&c.sc->tests, ntest);
-        if (nrecheck) atomicAdd(&c.sc->rechecks, nrecheck);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// A5 best lower bound, pruning, allocation of surviving children, leaf argmax
-// ---------------------------------------------------------------------------
-template <int NS>
-__global__ void k_child_lbmax(Chunk c) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    int cl = idx / NS, s = idx % NS;
-    unsigned v = 0;
-    if (cl < c.nc && !(s & ~c.lev.split_mask) && c.alive[cl]) v = c.cnt[(size_t)idx * 3 + 1];
-    v = __reduce_max_sync(kFull, v);
-    if ((threadIdx.x & 31) == 0 && v) atomicMax(&c.sc->best_lb, v);
-}
-
 // Block-wide exclusive scan of one 64-bit value per thread (blockDim = 256).
 __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long *total) {
     __shared__ unsigned long long warp_tot[8];
@@ -446,6 +224,440 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
     *total = warp_tot[7];
     __syncthreads();
     return before + x - v;
+}
+
+// Per-record state of the proximity test: the canonical record in FP32 (screen)
+// and, on demand, in FP64 (exact definition).
+template <int FAM, int PREC>
+struct RecState {
+    using F = Fam<FAM>;
+    int32_t qf[F::ND], qt[F::LE];
+    uint32_t mult;
+    float f32[F::ND], t32[F::LE], R32[F::ND], Eub[F::ND], Elb[F::ND];
+    double f64[F::ND], t64[F::LE], R64[F::ND];
+    bool have64;
+
+    __device__ __forceinline__ void load(const RecView &in, int64_t r) {
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) qf[j] = in.qf[j][r];
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) qt[m] = in.qt[m][r];
+        mult = in.mult[r];
+        have64 = false;
+    }
+    __device__ __forceinline__ void need64(const Problem &P, const Level &lev) {
+        if (have64) return;
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) f64[j] = dmul((double)qf[j], P.s_f[j]);
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) t64[m] = dmul((double)qt[m], lev.s_t[m]);
+        radius64<FAM>(lev, t64, R64);
+        have64 = true;
+    }
+    // FP32 values and the screen's error margins; gmax = max |dpsi| over children
+    __device__ __forceinline__ void prep32(const Problem &P, const Level &lev, const float *gmax) {
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) f32[j] = (float)qf[j] * P.s_ff[j];
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) t32[m] = (float)qt[m] * lev.s_tf[m];
+        float lam[F::ND * F::K];
+        F::lipschitz32(t32, lam);
+        float shmax[F::D], err[F::ND];
+#pragma unroll
+        for (int j = 0; j < F::D; ++j) shmax[j] = ((lev.split_mask >> j) & 1) ? lev.h1f[j] : 0.0f;
+        F::errmag32(f32, t32, gmax, shmax, err);
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) {
+            float rr = lev.Rbasef[j];
+#pragma unroll
+            for (int i = 0; i < F::K; ++i) rr = rr + lam[j * F::K + i] * lev.h1f[i];
+            R32[j] = rr + lev.A1f[j];
+            Eub[j] = kScreenRel * (err[j] + R32[j]);
+            Elb[j] = kScreenRel * (err[j] + fabsf(lev.rlbf[j]));
+        }
+    }
+};
+
+// Signed shift of dependent coordinate j (index k + j) for child slot s.
+template <int FAM>
+__device__ __forceinline__ double dep_shift64(const Level &lev, int j, int s) {
+    constexpr int K = Fam<FAM>::K;
+    bool split = (lev.split_mask >> (K + j)) & 1;
+    return split ? (((s >> (K + j)) & 1) ? lev.h1[K + j] : -lev.h1[K + j]) : 0.0;
+}
+template <int FAM>
+__device__ __forceinline__ float dep_shift32(const Level &lev, int j, int s) {
+    constexpr int K = Fam<FAM>::K;
+    bool split = (lev.split_mask >> (K + j)) & 1;
+    return split ? (((s >> (K + j)) & 1) ? lev.h1f[K + j] : -lev.h1f[K + j]) : 0.0f;
+}
+
+// UB/LB decisions of one record against every child.  g32 / g64: the cell's basis
+// changes per child slot ([slot][NB]; slots that differ only in dependent bits share
+// them).  Returns the UB-pass and LB-pass slot masks; counts FP64 rechecks.
+template <int FAM, int PREC>
+__device__ __forceinline__ void eval_record(const Problem &P, const Level &lev, RecState<FAM, PREC> &st,
+                                            const float *g32, const double *g64, unsigned &ubm, unsigned &lbm,
+                                            unsigned &nrechk) {
+    using F = Fam<FAM>;
+    constexpr int NS = 1 << F::D;
+    constexpr int NF = 1 << F::K;
+    const int smask = lev.split_mask;
+    ubm = 0;
+    lbm = 0;
+#pragma unroll
+    for (int fs = 0; fs < NF; ++fs) {
+        if (fs & ~smask) continue;
+        if (PREC == 0) {
+            double pr[F::ND];
+            F::partial64(st.f64, st.t64, g64 + fs * F::NB, pr);
+#pragma unroll
+            for (int s = fs; s < NS; s += NF) {
+                if (s & ~smask) continue;
+                int ub = 1, lb = 1;
+#pragma unroll
+                for (int j = 0; j < F::ND; ++j) {
+                    double a = fabs(dsub(pr[j], dep_shift64<FAM>(lev, j, s)));
+                    ub &= a <= st.R64[j];
+                    lb &= a <= lev.rlb[j];
+                }
+                ubm |= (unsigned)ub << s;
+                lbm |= (unsigned)lb << s;
+            }
+        } else {
+            float pr[F::ND];
+            F::partial32(st.f32, st.t32, g32 + fs * F::NB, pr);
+#pragma unroll
+            for (int s = fs; s < NS; s += NF) {
+                if (s & ~smask) continue;
+                int ub_fail = 0, ub_unsure = 0, lb_fail = 0, lb_unsure = 0;
+#pragma unroll
+                for (int j = 0; j < F::ND; ++j) {
+                    float a = fabsf(pr[j] - dep_shift32<FAM>(lev, j, s));
+                    float du = a - st.R32[j], dl = a - lev.rlbf[j];
+                    ub_fail |= du > st.Eub[j];
+                    ub_unsure |= !(du < -st.Eub[j]);
+                    lb_fail |= dl > st.Elb[j];
+                    lb_unsure |= !(dl < -st.Elb[j]);
+                }
+                int res;
+                if (ub_fail) {
+                    res = 0;
+                } else if (!ub_unsure && (lb_fail || !lb_unsure)) {
+                    res = 1 | ((lb_fail ? 0 : 1) << 1);
+                } else {
+                    st.need64(P, lev);
+                    ++nrechk;
+                    double p64[F::ND];
+                    F::partial64(st.f64, st.t64, g64 + fs * F::NB, p64);
+                    int ub = 1, lb = 1;
+#pragma unroll
+                    for (int j = 0; j < F::ND; ++j) {
+                        double a = fabs(dsub(p64[j], dep_shift64<FAM>(lev, j, s)));
+                        ub &= a <= st.R64[j];
+                        lb &= a <= lev.rlb[j];
+                    }
+                    res = ub | (lb << 1);
+                }
+                ubm |= (unsigned)(res & 1) << s;
+                lbm |= (unsigned)((res >> 1) & 1) << s;
+            }
+        }
+    }
+}
+
+// Snapped free parameters of the record's surface at the centre of child s.
+template <int FAM, int PREC>
+__device__ __forceinline__ void child_qf(const Problem &P, const Level &lev, RecState<FAM, PREC> &st,
+                                         const float *g32, const double *g64, int s, int32_t *qn, unsigned &nrechk,
+                                         Scalars *sc) {
+    using F = Fam<FAM>;
+    constexpr int NF = 1 << F::K;
+    const int fs = s & (NF - 1);
+    bool done = false;
+    if (PREC == 1) {
+        float pr[F::ND];
+        F::partial32(st.f32, st.t32, g32 + fs * F::NB, pr);
+        done = true;
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) {
+            float y = (pr[j] - dep_shift32<FAM>(lev, j, s)) * P.inv_s_ff[j];
+            float q = rintf(y);
+            float margin = 0.5f - fabsf(y - q);
+            if (margin > st.Eub[j] * P.inv_s_ff[j] && fabsf(q) < 1.6e7f) qn[j] = (int32_t)q;
+            else done = false;
+        }
+        if (!done) ++nrechk;
+    }
+    if (!done) {
+        st.need64(P, lev);
+        double pr[F::ND];
+        F::partial64(st.f64, st.t64, g64 + fs * F::NB, pr);
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) {
+            double q = rint(dmul(dsub(pr[j], dep_shift64<FAM>(lev, j, s)), P.inv_s_f[j]));
+            if (!(fabs(q) < 1073741824.0)) {
+                atomicOr(&sc->err, 2u);
+                q = 0.0;
+            }
+            qn[j] = (int32_t)q;
+        }
+    }
+}
+
+template <int FAM, int PREC>
+__device__ __forceinline__ void write_child(const Chunk &c, const RecState<FAM, PREC> &st, const int32_t *qn,
+                                            int ci, uint64_t at) {
+    using F = Fam<FAM>;
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) c.out.qf[j][at] = qn[j];
+#pragma unroll
+    for (int m = 0; m < F::LE; ++m) c.out.qt[m][at] = c.lev.st_ratio_log2[m] ? resnap_half(st.qt[m]) : st.qt[m];
+    c.out.mult[at] = st.mult;
+    c.out.cell[at] = (uint32_t)ci;
+}
+
+constexpr int kRPT = 4;              // records per thread in one tile
+constexpr int kTile = 256 * kRPT;    // records per block
+
+// Proximity test of a chunk's records against all children of their cells.
+// Count pass (EMIT = false): per child UB = sum of mult over UB-passing records,
+// LB likewise, and the number of passing records; per record the UB-pass mask.
+// Emit pass (EMIT = true): every UB-passing record of a surviving child is
+// written into the child's record range, snapped for the next level.
+// A block takes a tile of kTile consecutive records.  Records are sorted by cell,
+// so a tile whose first and last record share a cell lies in one cell: then the
+// cell's geometry is staged in shared memory, counts are reduced in registers
+// and across the block (one global atomic per counter), and the emit pass
+// reserves the child ranges with one atomic per child and a block scan.  Tiles
+// spanning several cells fall back to warp-level aggregation.
+template <int FAM, int PREC, bool EMIT>
+__global__ void __launch_bounds__(256) k_test(Chunk c) {
+    using F = Fam<FAM>;
+    constexpr int NS = 1 << F::D;
+    const Problem &P = c.P;
+    const Level &lev = c.lev;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int smask = lev.split_mask;
+    __shared__ float s_g32[(NS + 1) * F::NB];
+    __shared__ double s_g64[NS * F::NB];
+    __shared__ unsigned s_red[8][3 * NS];
+    __shared__ int s_ci[NS];
+    __shared__ unsigned long long s_base[NS];
+    const int64_t t0 = c.r0 + (int64_t)blockIdx.x * kTile;
+    const int64_t t1 = t0 + kTile < c.r1 ? t0 + kTile : c.r1;
+    const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
+    const int clast = (int)((int64_t)c.in.cell[t1 - 1] - c.c0);
+    unsigned nrechk = 0, ntest = 0;
+    if (cfirst == clast) {
+        // ------------------------------ one cell ------------------------------
+        const int cl = cfirst;
+        if (!c.alive[cl]) return;                        // uniform: whole block exits
+        for (int i = threadIdx.x; i < (NS + 1) * F::NB; i += blockDim.x)
+            s_g32[i] = c.geo32[(size_t)cl * (NS + 1) * F::NB + i];
+        for (int i = threadIdx.x; i < NS * F::NB; i += blockDim.x) s_g64[i] = c.geo64[(size_t)cl * NS * F::NB + i];
+        if (EMIT && threadIdx.x < NS) s_ci[threadIdx.x] = c.child_idx[(size_t)cl * NS + threadIdx.x];
+        __syncthreads();
+        if (!EMIT) {
+            unsigned aub[NS], alb[NS], an[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) aub[s] = alb[s] = an[s] = 0;
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {
+                int64_t r = t0 + threadIdx.x + k * 256;
+                if (r >= t1) break;
+                RecState<FAM, PREC> st;
+                st.load(c.in, r);
+                if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
+                else st.need64(P, lev);
+                unsigned ubm, lbm;
+                eval_record<FAM, PREC>(P, lev, st, s_g32, s_g64, ubm, lbm, nrechk);
+                c.passmask[r - c.r0] = (uint8_t)ubm;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    if (s & ~smask) continue;
+                    ++ntest;
+                    aub[s] += ((ubm >> s) & 1) ? st.mult : 0u;
+                    alb[s] += ((lbm >> s) & 1) ? st.mult : 0u;
+                    an[s] += (ubm >> s) & 1;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                unsigned a = __reduce_add_sync(kFull, aub[s]);
+                unsigned b = __reduce_add_sync(kFull, alb[s]);
+                unsigned d = __reduce_add_sync(kFull, an[s]);
+                if (lane == 0) {
+                    s_red[warp][3 * s] = a;
+                    s_red[warp][3 * s + 1] = b;
+                    s_red[warp][3 * s + 2] = d;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < 3 * NS) {
+                unsigned v = 0;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) v += s_red[w][threadIdx.x];
+                if (v) atomicAdd(c.cnt + (size_t)cl * NS * 3 + threadIdx.x, v);
+            }
+        } else {
+            // per-thread counts of records to write per child, packed 16 bits x 4
+            unsigned em[kRPT];
+            unsigned long long lo = 0, hi = 0;
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {
+                int64_t r = t0 + threadIdx.x + k * 256;
+                unsigned m = 0;
+                if (r < t1) {
+                    m = c.passmask[r - c.r0];
+#pragma unroll
+                    for (int s = 0; s < NS; ++s)
+                        if (s_ci[s] < 0) m &= ~(1u << s);
+                }
+                em[k] = m;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    unsigned long long b = (m >> s) & 1;
+                    if (s < 4) lo += b << (16 * s);
+                    else hi += b << (16 * (s - 4));
+                }
+            }
+            unsigned long long tlo, thi;
+            unsigned long long elo = block_excl_scan(lo, &tlo);
+            unsigned long long ehi = block_excl_scan(hi, &thi);
+            if (threadIdx.x < NS) {
+                int s = threadIdx.x;
+                unsigned tot = (unsigned)(((s < 4 ? tlo : thi) >> (16 * (s & 3))) & 0xffff);
+                s_base[s] = (tot && s_ci[s] >= 0) ? atomicAdd(&c.cursor[(size_t)cl * NS + s], tot) : 0;
+            }
+            __syncthreads();
+            unsigned pos[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+                pos[s] = (unsigned)s_base[s] + (unsigned)(((s < 4 ? elo : ehi) >> (16 * (s & 3))) & 0xffff);
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {
+                if (!em[k]) continue;
+                int64_t r = t0 + threadIdx.x + k * 256;
+                RecState<FAM, PREC> st;
+                st.load(c.in, r);
+                if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    if (!((em[k] >> s) & 1)) continue;
+                    int32_t qn[F::ND];
+                    child_qf<FAM, PREC>(P, lev, st, s_g32, s_g64, s, qn, nrechk, c.sc);
+                    int ci = s_ci[s];
+                    write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos[s]);
+                    ++pos[s];
+                }
+            }
+        }
+    } else {
+        // --------------------------- several cells ----------------------------
+#pragma unroll 1
+        for (int k = 0; k < kRPT; ++k) {
+            int64_t r = t0 + threadIdx.x + k * 256;
+            bool act = false;
+            int cl = 0;
+            RecState<FAM, PREC> st;
+            if (r < t1) {
+                cl = (int)((int64_t)c.in.cell[r] - c.c0);
+                act = c.alive[cl] != 0;
+                if (act) {
+                    st.load(c.in, r);
+                    if (PREC == 1) st.prep32(P, lev, c.geo32 + ((size_t)cl * (NS + 1) + NS) * F::NB);
+                    else st.need64(P, lev);
+                }
+            }
+            const float *g32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
+            const double *g64 = c.geo64 + (size_t)cl * NS * F::NB;
+            unsigned actb = __ballot_sync(kFull, act);
+            if (!actb) continue;
+            int leader = __ffs(actb) - 1;
+            int cl0 = __shfl_sync(kFull, cl, leader);
+            if (!EMIT) {
+                unsigned ubm = 0, lbm = 0;
+                if (act) {
+                    eval_record<FAM, PREC>(P, lev, st, g32, g64, ubm, lbm, nrechk);
+                    c.passmask[r - c.r0] = (uint8_t)ubm;
+                }
+                bool uniform = __all_sync(kFull, !act || cl == cl0);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    if (s & ~smask) continue;
+                    if (act) ++ntest;
+                    unsigned pu = act && ((ubm >> s) & 1);
+                    unsigned vub = pu ? st.mult : 0u, vlb = (act && ((lbm >> s) & 1)) ? st.mult : 0u;
+                    if (uniform) {
+                        vub = __reduce_add_sync(kFull, vub);
+                        vlb = __reduce_add_sync(kFull, vlb);
+                        unsigned vn = __reduce_add_sync(kFull, pu);
+                        if (lane == leader) {
+                            uint32_t *b = c.cnt + ((size_t)cl0 * NS + s) * 3;
+                            if (vub) atomicAdd(b, vub);
+                            if (vlb) atomicAdd(b + 1, vlb);
+                            if (vn) atomicAdd(b + 2, vn);
+                        }
+                    } else if (pu) {
+                        uint32_t *b = c.cnt + ((size_t)cl * NS + s) * 3;
+                        atomicAdd(b, vub);
+                        if (vlb) atomicAdd(b + 1, vlb);
+                        atomicAdd(b + 2, 1u);
+                    }
+                }
+            } else {
+                unsigned ubm = act ? c.passmask[r - c.r0] : 0u;
+                bool uniform = __all_sync(kFull, !(act && ubm) || cl == cl0);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    if (s & ~smask) continue;
+                    bool want = act && ((ubm >> s) & 1);
+                    int ci = -1;
+                    if (want) {
+                        ci = c.child_idx[(size_t)cl * NS + s];
+                        want = ci >= 0;
+                    }
+                    unsigned bal = __ballot_sync(kFull, want);
+                    if (!bal) continue;
+                    unsigned pos = 0;
+                    if (uniform) {
+                        int ldr = __ffs(bal) - 1;
+                        unsigned base = 0;
+                        if (lane == ldr) base = atomicAdd(&c.cursor[(size_t)cl0 * NS + s], (unsigned)__popc(bal));
+                        base = __shfl_sync(kFull, base, ldr);
+                        pos = base + __popc(bal & ((1u << lane) - 1u));
+                    } else if (want) {
+                        pos = atomicAdd(&c.cursor[(size_t)cl * NS + s], 1u);
+                    }
+                    if (!want) continue;
+                    int32_t qn[F::ND];
+                    child_qf<FAM, PREC>(P, lev, st, g32, g64, s, qn, nrechk, c.sc);
+                    write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos);
+                }
+            }
+        }
+    }
+    // counters (all threads of the block reach this point unless the block exited above)
+    ntest = __reduce_add_sync(kFull, ntest);
+    nrechk = __reduce_add_sync(kFull, nrechk);
+    if (lane == 0) {
+        if (!EMIT && ntest) atomicAdd(&c.sc->tests, (unsigned long long)ntest);
+        if (nrechk) atomicAdd(&c.sc->rechecks, (unsigned long long)nrechk);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A5 best lower bound, pruning, allocation of surviving children, leaf argmax
+// ---------------------------------------------------------------------------
+template <int NS>
+__global__ void k_child_lbmax(Chunk c) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int cl = idx / NS, s = idx % NS;
+    unsigned v = 0;
+    if (cl < c.nc && !(s & ~c.lev.split_mask) && c.alive[cl]) v = c.cnt[(size_t)idx * 3 + 1];
+    v = __reduce_max_sync(kFull, v);
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(&c.sc->best_lb, v);
 }
 
 // Phase A: per child of the chunk -- trace, pruning decision, leaf argmax, and
@@ -636,7 +848,7 @@ void launch_cell_geo(const Chunk &c, cudaStream_t st) {
 void launch_test(const Chunk &c, bool emit, cudaStream_t st) {
     int64_t nr = c.r1 - c.r0;
     if (nr <= 0) return;
-    unsigned g = blocks_for(nr, 256);
+    unsigned g = blocks_for(nr, kTile);
     if (c.precision == 0) {
         if (emit) { GV_DISPATCH(c.P.fam, (k_test<FAMV, 0, true><<<g, 256, 0, st>>>(c))); }
         else      { GV_DISPATCH(c.P.fam, (k_test<FAMV, 0, false><<<g, 256, 0, st>>>(c))); }

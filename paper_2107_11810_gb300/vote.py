@@ -30,6 +30,7 @@ STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: 
 NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4}
 EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
            "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_get_kernel_times",
+           "vote_get_level_stats",
            "vote_last_error", "vote_destroy"]
 
 
@@ -69,6 +70,7 @@ def load(path: str | None = None):
             lib.vote_get_trace.argtypes = [P, i64, P, P, P, P, P]
             lib.vote_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
             lib.vote_get_kernel_times.argtypes = [P, P, P, P]
+            lib.vote_get_level_stats.argtypes = [P, P, P]
             lib.vote_last_error.restype = ctypes.c_char_p
             lib.vote_last_error.argtypes = []
             lib.vote_destroy.argtypes = [P]
@@ -205,6 +207,14 @@ class Solver:
         by = np.zeros(8)
         _check(self.lib.vote_get_kernel_times(self.h, _ptr(ms), _ptr(nl), _ptr(by)))
         return {k: (float(ms[i]), int(nl[i]), float(by[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def level_stats(self):
+        """(cells[l], records[l]) expanded / tested per level in the last solve."""
+        L, _ = self.levels()
+        cells = np.zeros(max(L, 1), np.int64)
+        recs = np.zeros(max(L, 1), np.int64)
+        _check(self.lib.vote_get_level_stats(self.h, _ptr(cells), _ptr(recs)))
+        return cells[:L], recs[:L]
 
     def stats(self) -> dict:
         s = Stats()

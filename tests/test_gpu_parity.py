@@ -115,8 +115,8 @@ def test_full_trace_without_pruning_equals_oracle(family):
 @pytest.mark.parametrize("family", FAMS)
 def test_pruned_trace_entries_equal_oracle_cell_counts(family):
     p = small(family, 1500, 6)
-    g = gpu_solve(p, 1, trace_cap=200_000)
-    tg = g["solver"].trace(200_000)
+    g = gpu_solve(p, 1, trace_cap=4_000_000)
+    tg = g["solver"].trace(4_000_000)
     rng = np.random.default_rng(1)
     for x in rng.choice(len(tg["ub"]), size=min(30, len(tg["ub"])), replace=False):
         ub, lb = oracle.cell_counts(p.family, p.eps, p.bounds, p.params, tg["level"][x], tg["coords"][x])
