@@ -379,7 +379,7 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     TRY(ensure(c, c->keepflag, nch * 4));
     TRY(ensure(c, c->recn, nch * 4));
     TRY(ensure(c, c->bsums, ((nch + 255) / 256) * 16 + 16));
-    if (!lev.leaf_children) TRY(ensure_level(c, l + 1, (size_t)nr * nvalid, nch));
+    if (!lev.leaf_children) TRY(ensure_level(c, l + 1, 0, nch));    // records: sized below, exactly
     CK(cudaMemsetAsync(c->cnt.p, 0, nch * 12, c->stream));
     CK(cudaMemsetAsync(c->cursor.p, 0, nch * 4, c->stream));
     CK(cudaMemsetAsync(&dsc(c)->n_cells, 0, 16, c->stream));
@@ -447,6 +447,8 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     CK(cudaStreamSynchronize(c->stream));
     int64_t new_cells = (int64_t)c->h_sc->n_cells, new_recs = (int64_t)c->h_sc->n_recs;
     if (new_recs > 0) {
+        TRY(ensure_level(c, l + 1, (size_t)new_recs, 0));
+        ch.out = rec_view(c, l + 1);
         launch_test(ch, true, c->stream);
         c->stats.launches += 1;
         ev_record(c, 4);
@@ -493,7 +495,7 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         set_err("invalid arguments");
         return VOTE_EINVAL;
     }
-    if (n >= (int64_t)1 << 31 || (P.coord_bits < 64 && (uint64_t)n >= (1ull << (64 - P.coord_bits)))) {
+    if (n >= (int64_t)1 << 31 || (P.coord_bits > 0 && (uint64_t)n >= (1ull << (64 - P.coord_bits)))) {
         set_err("n = %lld too large", (long long)n);
         return VOTE_EUNSUPPORTED;
     }
