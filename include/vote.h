@@ -85,8 +85,12 @@ typedef enum {
     VOTE_OPT_INITIAL_LB = 7,  /* a known lower bound on the best depth (warm start of
                                  the B&B bound, e.g. from a previous frame); must not
                                  exceed the true maximum depth; default 0            */
-    VOTE_OPT_KERNEL_TIMING = 8 /* 1 = time each kernel class with CUDA events on the
+    VOTE_OPT_KERNEL_TIMING = 8, /* 1 = time each kernel class with CUDA events on the
                                  context's stream (see vote_get_kernel_times)        */
+    VOTE_OPT_TWO_LEVEL = 9    /* expand two levels per read of a chunk's records when
+                                 its children would hold more than this many times
+                                 its records (their records are then never written
+                                 to memory); 0 = never; default 2 */
 } vote_option;
 
 /* Kernel classes reported by vote_get_kernel_times. */

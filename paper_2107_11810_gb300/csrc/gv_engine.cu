@@ -72,9 +72,11 @@ struct vote_ctx {
     int64_t chunk_records = 1 << 25;
     uint32_t initial_lb = 0;
     int kernel_timing = 0;
-    cudaEvent_t ev[6] = {};
-    int ev_pending = 0;        // events of the previous chunk not yet read
-    int ev_emit = 0;           // ... and whether it had an emit pass
+    double two_level = 2.0;
+    static const int kEv = 24;
+    cudaEvent_t ev[kEv] = {};
+    int ev_n = 0;              // events recorded since the last collection
+    int ev_cls[kEv] = {};      // kernel class of the interval ending at event i
     double kms[VOTE_K_CLASSES] = {};
     int64_t klaunch[VOTE_K_CLASSES] = {};
     double kbytes[VOTE_K_CLASSES] = {};
@@ -84,6 +86,7 @@ struct vote_ctx {
     LevelStore ls[GV_MAXL + 1];
     DevBuf levs_dev, path, scal, alive, geo64, geo32, cnt, passmask, child_idx, cursor, keepflag, recn, bsums;
     DevBuf tr_level, tr_key, tr_ub, tr_lb, surf_tmp, mask_tmp;
+    DevBuf alive1, geo64b, geo32b, cntb, pm2, child_idxb, cursorb;
     Scalars *h_sc = nullptr;   // pinned mirror of the device scalars
     uint64_t *h_tmp = nullptr; // pinned slot for single values
     int64_t trace_written = 0;
@@ -321,26 +324,119 @@ static vote_status read_scalars(vote_ctx *c) {
 // kernel timing (CUDA events on the context's stream, read after the stream has
 // passed them)
 // ---------------------------------------------------------------------------
-static void ev_record(vote_ctx *c, int i) {
-    if (c->kernel_timing) cudaEventRecord(c->ev[i], c->stream);
+// Events are recorded in sequence; the interval ending at event i is charged to
+// class ev_cls[i] (-1: not charged).  They are read once the stream has passed
+// them (at the next synchronisation).
+static void ev_mark(vote_ctx *c, int cls) {
+    if (!c->kernel_timing || c->ev_n >= vote_ctx::kEv) return;
+    cudaEventRecord(c->ev[c->ev_n], c->stream);
+    c->ev_cls[c->ev_n] = cls;
+    ++c->ev_n;
 }
 
 static void ev_collect(vote_ctx *c) {
-    if (!c->kernel_timing || !c->ev_pending) return;
-    float ms;
-    const int cls[4] = {VOTE_K_CELL_GEO, VOTE_K_TEST_COUNT, VOTE_K_CHILDREN, VOTE_K_TEST_EMIT};
-    int last = c->ev_emit ? 4 : 3;
-    for (int i = 0; i < last; ++i)
-        if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) {
-            c->kms[cls[i]] += ms;
-            c->klaunch[cls[i]] += 1;
+    if (!c->kernel_timing) return;
+    for (int i = 1; i < c->ev_n; ++i) {
+        float ms;
+        int cls = c->ev_cls[i];
+        if (cls >= 0 && cudaEventElapsedTime(&ms, c->ev[i - 1], c->ev[i]) == cudaSuccess) {
+            c->kms[cls] += ms;
+            c->klaunch[cls] += 1;
         }
-    c->ev_pending = 0;
+    }
+    c->ev_n = 0;
 }
 
 // ---------------------------------------------------------------------------
 // search
 // ---------------------------------------------------------------------------
+
+// Second half of a two-level step: the chunk ch of level-l cells has been counted
+// and its surviving children (level l+1, nc1 cells holding nrec1 records) laid out
+// in ls[l+1].  Their records are not written; k_test2 derives them from the level-l
+// records, counts the grandchildren, and writes the surviving grandchildren's
+// records into ls[l+2].  The level-(l+1) cells are then fully expanded.
+static vote_status expand_two(vote_ctx *c, int l, Chunk &ch, int64_t nr, int64_t nc1, int64_t nrec1) {
+    const Problem &P = c->P;
+    const Level &lev1 = c->lev[l + 1];
+    const int ns = c->ns;
+    int NB = P.fam == VOTE_LINE2D ? 1 : (P.fam == VOTE_PLANE3D_SPH ? 3 : 2);
+    int nvalid1 = 0;
+    for (int g = 0; g < ns; ++g)
+        if (!(g & ~lev1.split_mask)) ++nvalid1;
+    size_t nch1 = (size_t)nc1 * ns;
+    TRY(ensure(c, c->alive1, nc1));
+    TRY(ensure(c, c->geo64b, nch1 * NB * 8));
+    TRY(ensure(c, c->geo32b, (size_t)nc1 * (ns + 1) * NB * 4));
+    TRY(ensure(c, c->cntb, nch1 * 12));
+    TRY(ensure(c, c->pm2, (size_t)nr * ns));
+    TRY(ensure(c, c->child_idxb, nch1 * 4));
+    TRY(ensure(c, c->cursorb, nch1 * 4));
+    TRY(ensure(c, c->keepflag, nch1 * 4));
+    TRY(ensure(c, c->recn, nch1 * 4));
+    TRY(ensure(c, c->bsums, ((nch1 + 255) / 256) * 16 + 16));
+    if (!lev1.leaf_children) TRY(ensure_level(c, l + 2, 0, nch1));
+    CK(cudaMemsetAsync(c->cntb.p, 0, nch1 * 12, c->stream));
+    CK(cudaMemsetAsync(c->cursorb.p, 0, nch1 * 4, c->stream));
+    CK(cudaMemsetAsync(&dsc(c)->n_cells, 0, 16, c->stream));
+    Chunk c1 = ch;
+    c1.lev = lev1;
+    c1.cells = cell_view(c, l + 1);
+    c1.c0 = 0;
+    c1.nc = (int)nc1;
+    c1.r0 = c1.r1 = 0;
+    c1.alive = (uint8_t *)c->alive1.p;
+    c1.geo64 = (double *)c->geo64b.p;
+    c1.geo32 = (float *)c->geo32b.p;
+    c1.cnt = (uint32_t *)c->cntb.p;
+    c1.passmask = nullptr;
+    c1.child_idx = (int32_t *)c->child_idxb.p;
+    c1.cursor = (uint32_t *)c->cursorb.p;
+    if (!lev1.leaf_children) {
+        c1.next_cells = cell_view(c, l + 2);
+        c1.out = rec_view(c, l + 2);
+    }
+    ev_mark(c, -1);
+    launch_cell_geo(c1, c->stream);
+    ev_mark(c, VOTE_K_CELL_GEO);
+    launch_test2(ch, c1, false, nullptr, (uint8_t *)c->pm2.p, c->stream);
+    ev_mark(c, VOTE_K_TEST_COUNT);
+    launch_child_lbmax(c1, c->stream);
+    launch_child_alloc(c1, (uint32_t *)c->keepflag.p, (uint32_t *)c->recn.p, (unsigned long long *)c->bsums.p,
+                       c->stream);
+    ev_mark(c, VOTE_K_CHILDREN);
+    CK(cudaGetLastError());
+    int rec_bytes = 4 * (P.nd + P.le + 2);
+    c->kbytes[VOTE_K_TEST_COUNT] += (double)nr * (rec_bytes + 1 + ns);
+    c->stats.launches += lev1.leaf_children ? 4 : 6;
+    c->stats.cells += nc1;
+    c->stats.records += nrec1;
+    c->lv_cells[l + 1] += nc1;
+    c->lv_recs[l + 1] += nrec1;
+    c->ls[l + 1].ncells = 0;
+    c->ls[l + 1].nrecs = 0;
+    if (lev1.leaf_children) {
+        c->stats.leaves += nc1 * nvalid1;
+        return VOTE_OK;
+    }
+    CK(cudaMemcpyAsync(&c->h_sc->n_cells, &dsc(c)->n_cells, 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t nc2 = (int64_t)c->h_sc->n_cells, nrec2 = (int64_t)c->h_sc->n_recs;
+    if (nrec2 > 0) {
+        TRY(ensure_level(c, l + 2, (size_t)nrec2, 0));
+        c1.out = rec_view(c, l + 2);
+        launch_test2(ch, c1, true, (const uint8_t *)c->pm2.p, nullptr, c->stream);
+        CK(cudaGetLastError());
+        c->stats.launches += 1;
+        ev_mark(c, VOTE_K_TEST_EMIT);
+        c->kbytes[VOTE_K_TEST_EMIT] += (double)nr * (rec_bytes + 1 + ns) + (double)nrec2 * rec_bytes;
+    }
+    c->ls[l + 2].ncells = nc2;
+    c->ls[l + 2].nrecs = nrec2;
+    if (nrec2 > c->stats.peak_records) c->stats.peak_records = nrec2;
+    return VOTE_OK;
+}
+
 static vote_status expand_chunk(vote_ctx *c, int l) {
     const Problem &P = c->P;
     LevelStore &S = c->ls[l];
@@ -417,17 +513,15 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     ch.precision = c->precision;
 
     int rec_bytes = 4 * (P.nd + P.le + 2);
-    ev_record(c, 0);
+    ev_mark(c, -1);
     launch_cell_geo(ch, c->stream);
-    ev_record(c, 1);
+    ev_mark(c, VOTE_K_CELL_GEO);
     launch_test(ch, false, c->stream);
-    ev_record(c, 2);
+    ev_mark(c, VOTE_K_TEST_COUNT);
     launch_child_lbmax(ch, c->stream);
     launch_child_alloc(ch, (uint32_t *)c->keepflag.p, (uint32_t *)c->recn.p, (unsigned long long *)c->bsums.p,
                        c->stream);
-    ev_record(c, 3);
-    c->ev_pending = c->kernel_timing;
-    c->ev_emit = 0;
+    ev_mark(c, VOTE_K_CHILDREN);
     c->kbytes[VOTE_K_TEST_COUNT] += (double)nr * (rec_bytes + 1);
     c->kbytes[VOTE_K_CELL_GEO] += (double)nc * (8 + 4);
     CK(cudaGetLastError());
@@ -446,13 +540,14 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     CK(cudaMemcpyAsync(&c->h_sc->n_cells, &dsc(c)->n_cells, 16, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     int64_t new_cells = (int64_t)c->h_sc->n_cells, new_recs = (int64_t)c->h_sc->n_recs;
+    if (c->two_level > 0 && l + 2 <= P.L && new_cells > 0 && (double)new_recs > c->two_level * (double)nr)
+        return expand_two(c, l, ch, nr, new_cells, new_recs);
     if (new_recs > 0) {
         TRY(ensure_level(c, l + 1, (size_t)new_recs, 0));
         ch.out = rec_view(c, l + 1);
         launch_test(ch, true, c->stream);
         c->stats.launches += 1;
-        ev_record(c, 4);
-        c->ev_emit = c->kernel_timing;
+        ev_mark(c, VOTE_K_TEST_EMIT);
         c->kbytes[VOTE_K_TEST_EMIT] += (double)nr * (rec_bytes + 1) + (double)new_recs * rec_bytes;
     }
     CK(cudaGetLastError());
@@ -465,20 +560,16 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
 static vote_status replay(vote_ctx *c, const double *surfaces, int64_t n, int lam, uint64_t key, uint32_t *reach,
                           int64_t *ub, int64_t *lb) {
     CK(cudaMemsetAsync(&dsc(c)->replay_ub, 0, 16, c->stream));
-    ev_record(c, 0);
+    ev_mark(c, -1);
     if (lam > 0) launch_path_geo(c->P, (const Level *)c->levs_dev.p, lam, key, (PathStep *)c->path.p, c->stream);
     launch_replay(c->P, (const Level *)c->levs_dev.p, (const PathStep *)c->path.p, lam, surfaces, n, reach,
                   dsc(c), c->stream);
     c->stats.launches += lam > 0 ? 2 : 1;
-    ev_record(c, 5);
+    ev_mark(c, VOTE_K_REPLAY);
     CK(cudaGetLastError());
     TRY(read_scalars(c));
-    if (c->kernel_timing) {
-        float ms;
-        if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]) == cudaSuccess) c->kms[VOTE_K_REPLAY] += ms;
-        c->klaunch[VOTE_K_REPLAY] += 1;
-        c->kbytes[VOTE_K_REPLAY] += (double)n * (8 * c->P.np) + (double)((n + 31) / 32) * 4;
-    }
+    ev_collect(c);
+    c->kbytes[VOTE_K_REPLAY] += (double)n * (8 * c->P.np) + (double)((n + 31) / 32) * 4;
     *ub = (int64_t)c->h_sc->replay_ub;
     *lb = (int64_t)c->h_sc->replay_lb;
     return VOTE_OK;
@@ -502,7 +593,7 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
     CK(cudaMemsetAsync(c->scal.p, 0, sizeof(Scalars), c->stream));
     if (c->initial_lb) CK(cudaMemcpyAsync(&dsc(c)->best_lb, &c->initial_lb, 4, cudaMemcpyHostToDevice, c->stream));
     for (int i = 0; i < VOTE_K_CLASSES; ++i) c->kms[i] = c->kbytes[i] = 0, c->klaunch[i] = 0;
-    c->ev_pending = 0;
+    c->ev_n = 0;
     c->trace_written = 0;
     c->trace_overflow = false;
     for (int l = 0; l <= P.L; ++l) c->ls[l].ncells = c->ls[l].nrecs = 0;
@@ -512,10 +603,10 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         dep = n;                                   // the domain is a leaf: every surface counts
     } else if (n > 0) {
         TRY(ensure_level(c, 0, (size_t)n, 1));
-        ev_record(c, 0);
+        ev_mark(c, -1);
         launch_lift(P, c->lev[0], surfaces, n, rec_view(c, 0), dsc(c), c->stream);
         c->stats.launches += 1;
-        ev_record(c, 5);
+        ev_mark(c, VOTE_K_LIFT);
         CK(cudaGetLastError());
         uint64_t key0 = 0, rb0 = 0;
         uint32_t cnt0 = (uint32_t)n;
@@ -527,12 +618,8 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         c->ls[0].ncells = 1;
         c->ls[0].nrecs = n;
         TRY(read_scalars(c));
-        if (c->kernel_timing) {
-            float ms;
-            if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]) == cudaSuccess) c->kms[VOTE_K_LIFT] += ms;
-            c->klaunch[VOTE_K_LIFT] += 1;
-            c->kbytes[VOTE_K_LIFT] += (double)n * (8 * P.np + 4 * (P.nd + P.le + 2));
-        }
+        ev_collect(c);
+        c->kbytes[VOTE_K_LIFT] += (double)n * (8 * P.np + 4 * (P.nd + P.le + 2));
         if (c->h_sc->err) {
             set_err("surface parameters are not finite or out of the representable range");
             return VOTE_EINVAL;
@@ -680,8 +767,12 @@ vote_status vote_set_option(vote_ctx *c, int key, double v) {
     case VOTE_OPT_KERNEL_TIMING:
         if (v != 0 && v != 1) break;
         if (v == 1 && !c->ev[0])
-            for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&c->ev[i]));
+            for (int i = 0; i < vote_ctx::kEv; ++i) CK(cudaEventCreate(&c->ev[i]));
         c->kernel_timing = (int)v;
+        return VOTE_OK;
+    case VOTE_OPT_TWO_LEVEL:
+        if (!(v >= 0 && v <= 1e6)) break;
+        c->two_level = v;
         return VOTE_OK;
     default:
         set_err("unknown option %d", key);
@@ -812,10 +903,11 @@ void vote_destroy(vote_ctx *c) {
     }
     DevBuf *bufs[] = {&c->levs_dev, &c->path, &c->scal, &c->alive, &c->geo64, &c->geo32, &c->cnt, &c->passmask,
                       &c->child_idx, &c->cursor, &c->keepflag, &c->recn, &c->bsums, &c->tr_level, &c->tr_key,
-                      &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp};
+                      &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp, &c->alive1, &c->geo64b,
+                      &c->geo32b, &c->cntb, &c->pm2, &c->child_idxb, &c->cursorb};
     for (DevBuf *b : bufs) release(c, *b);
     cudaStreamSynchronize(c->stream);
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < vote_ctx::kEv; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_tmp) cudaFreeHost(c->h_tmp);

@@ -245,6 +245,14 @@ struct RecState {
         mult = in.mult[r];
         have64 = false;
     }
+    __device__ __forceinline__ void set(const int32_t *qf_, const int32_t *qt_, uint32_t mult_) {
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) qf[j] = qf_[j];
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) qt[m] = qt_[m];
+        mult = mult_;
+        have64 = false;
+    }
     __device__ __forceinline__ void need64(const Problem &P, const Level &lev) {
         if (have64) return;
 #pragma unroll
@@ -305,6 +313,7 @@ __device__ __forceinline__ void eval_record(const Problem &P, const Level &lev, 
     const int smask = lev.split_mask;
     ubm = 0;
     lbm = 0;
+    unsigned unsure = 0;
 #pragma unroll
     for (int fs = 0; fs < NF; ++fs) {
         if (fs & ~smask) continue;
@@ -340,28 +349,36 @@ __device__ __forceinline__ void eval_record(const Problem &P, const Level &lev, 
                     lb_fail |= dl > st.Elb[j];
                     lb_unsure |= !(dl < -st.Elb[j]);
                 }
-                int res;
-                if (ub_fail) {
-                    res = 0;
-                } else if (!ub_unsure && (lb_fail || !lb_unsure)) {
-                    res = 1 | ((lb_fail ? 0 : 1) << 1);
-                } else {
-                    st.need64(P, lev);
-                    ++nrechk;
-                    double p64[F::ND];
-                    F::partial64(st.f64, st.t64, g64 + fs * F::NB, p64);
-                    int ub = 1, lb = 1;
-#pragma unroll
-                    for (int j = 0; j < F::ND; ++j) {
-                        double a = fabs(dsub(p64[j], dep_shift64<FAM>(lev, j, s)));
-                        ub &= a <= st.R64[j];
-                        lb &= a <= lev.rlb[j];
+                if (!ub_fail) {
+                    if (!ub_unsure && (lb_fail || !lb_unsure)) {
+                        ubm |= 1u << s;
+                        lbm |= (lb_fail ? 0u : 1u) << s;
+                    } else {
+                        unsure |= 1u << s;
                     }
-                    res = ub | (lb << 1);
                 }
-                ubm |= (unsigned)(res & 1) << s;
-                lbm |= (unsigned)((res >> 1) & 1) << s;
             }
+        }
+    }
+    if (PREC == 1 && unsure) {
+        // the FP32 screen could not decide these children: exact FP64 test (one
+        // copy of the code, not unrolled)
+        st.need64(P, lev);
+#pragma unroll 1
+        for (unsigned u = unsure; u; u &= u - 1) {
+            int s = __ffs(u) - 1;
+            ++nrechk;
+            double pr[F::ND];
+            F::partial64(st.f64, st.t64, g64 + (s & (NF - 1)) * F::NB, pr);
+            int ub = 1, lb = 1;
+#pragma unroll
+            for (int j = 0; j < F::ND; ++j) {
+                double a = fabs(dsub(pr[j], dep_shift64<FAM>(lev, j, s)));
+                ub &= a <= st.R64[j];
+                lb &= a <= lev.rlb[j];
+            }
+            ubm |= (unsigned)ub << s;
+            lbm |= (unsigned)lb << s;
         }
     }
 }
@@ -432,7 +449,7 @@ constexpr int kTile = 256 * kRPT;    // records per block
 // reserves the child ranges with one atomic per child and a block scan.  Tiles
 // spanning several cells fall back to warp-level aggregation.
 template <int FAM, int PREC, bool EMIT>
-__global__ void __launch_bounds__(256) k_test(Chunk c) {
+__global__ void __launch_bounds__(256, 3) k_test(Chunk c) {
     using F = Fam<FAM>;
     constexpr int NS = 1 << F::D;
     const Problem &P = c.P;
@@ -462,12 +479,17 @@ __global__ void __launch_bounds__(256) k_test(Chunk c) {
             unsigned aub[NS], alb[NS], an[NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) aub[s] = alb[s] = an[s] = 0;
+            RecState<FAM, PREC> sts[kRPT];
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {       // issue every load of the tile first
+                int64_t r = t0 + threadIdx.x + k * 256;
+                if (r < t1) sts[k].load(c.in, r);
+            }
 #pragma unroll
             for (int k = 0; k < kRPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
                 if (r >= t1) break;
-                RecState<FAM, PREC> st;
-                st.load(c.in, r);
+                RecState<FAM, PREC> &st = sts[k];
                 if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
                 else st.need64(P, lev);
                 unsigned ubm, lbm;
@@ -501,9 +523,10 @@ __global__ void __launch_bounds__(256) k_test(Chunk c) {
                 if (v) atomicAdd(c.cnt + (size_t)cl * NS * 3 + threadIdx.x, v);
             }
         } else {
-            // per-thread counts of records to write per child, packed 16 bits x 4
+            // Positions in (k, warp, lane) order so that each warp's stores for one
+            // child are contiguous: per k and slot, warp counts are scanned in smem.
+            __shared__ unsigned s_wcnt[kRPT][8][NS];
             unsigned em[kRPT];
-            unsigned long long lo = 0, hi = 0;
 #pragma unroll
             for (int k = 0; k < kRPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
@@ -517,39 +540,41 @@ __global__ void __launch_bounds__(256) k_test(Chunk c) {
                 em[k] = m;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    unsigned long long b = (m >> s) & 1;
-                    if (s < 4) lo += b << (16 * s);
-                    else hi += b << (16 * (s - 4));
+                    unsigned b = __ballot_sync(kFull, (m >> s) & 1);
+                    if (lane == 0) s_wcnt[k][warp][s] = __popc(b);
                 }
             }
-            unsigned long long tlo, thi;
-            unsigned long long elo = block_excl_scan(lo, &tlo);
-            unsigned long long ehi = block_excl_scan(hi, &thi);
+            __syncthreads();
             if (threadIdx.x < NS) {
                 int s = threadIdx.x;
-                unsigned tot = (unsigned)(((s < 4 ? tlo : thi) >> (16 * (s & 3))) & 0xffff);
-                s_base[s] = (tot && s_ci[s] >= 0) ? atomicAdd(&c.cursor[(size_t)cl * NS + s], tot) : 0;
+                unsigned run = 0;
+                for (int k = 0; k < kRPT; ++k)
+                    for (int w = 0; w < 8; ++w) {
+                        unsigned v = s_wcnt[k][w][s];
+                        s_wcnt[k][w][s] = run;
+                        run += v;
+                    }
+                s_base[s] = (run && s_ci[s] >= 0) ? atomicAdd(&c.cursor[(size_t)cl * NS + s], run) : 0;
             }
             __syncthreads();
-            unsigned pos[NS];
-#pragma unroll
-            for (int s = 0; s < NS; ++s)
-                pos[s] = (unsigned)s_base[s] + (unsigned)(((s < 4 ? elo : ehi) >> (16 * (s & 3))) & 0xffff);
 #pragma unroll
             for (int k = 0; k < kRPT; ++k) {
-                if (!em[k]) continue;
+                unsigned m = em[k];
                 int64_t r = t0 + threadIdx.x + k * 256;
                 RecState<FAM, PREC> st;
-                st.load(c.in, r);
-                if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
+                if (m) {
+                    st.load(c.in, r);
+                    if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
+                }
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    if (!((em[k] >> s) & 1)) continue;
+                    unsigned b = __ballot_sync(kFull, (m >> s) & 1);
+                    if (!((m >> s) & 1)) continue;
+                    unsigned pos = (unsigned)s_base[s] + s_wcnt[k][warp][s] + __popc(b & ((1u << lane) - 1u));
                     int32_t qn[F::ND];
                     child_qf<FAM, PREC>(P, lev, st, s_g32, s_g64, s, qn, nrechk, c.sc);
                     int ci = s_ci[s];
-                    write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos[s]);
-                    ++pos[s];
+                    write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos);
                 }
             }
         }
@@ -639,6 +664,221 @@ __global__ void __launch_bounds__(256) k_test(Chunk c) {
         }
     }
     // counters (all threads of the block reach this point unless the block exited above)
+    ntest = __reduce_add_sync(kFull, ntest);
+    nrechk = __reduce_add_sync(kFull, nrechk);
+    if (lane == 0) {
+        if (!EMIT && ntest) atomicAdd(&c.sc->tests, (unsigned long long)ntest);
+        if (nrechk) atomicAdd(&c.sc->rechecks, (unsigned long long)nrechk);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Two levels per record read.  c is a chunk of level-l cells whose counts, child
+// cells (level l+1, in c1.cells) and UB-pass masks are known; c1 describes those
+// child cells (their geometry, alive flags, grandchild counters, grandchild cells
+// in c1.next_cells).  The level-(l+1) records are never written: each block takes a
+// tile of level-l records and one child slot s, re-derives the child record of
+// every record that passes child s (residual at the child centre, snapped for
+// level l+1) and tests it against the grandchildren.  Count pass: grandchild
+// UB/LB/record counts and the grandchild pass mask per (record, s).  Emit pass:
+// the grandchild records, snapped for level l+2.
+// ---------------------------------------------------------------------------
+template <int FAM, int PREC>
+__device__ __forceinline__ void derive_child(const Problem &P, const Level &lev, RecState<FAM, PREC> &st,
+                                             const float *g32, const double *g64, int s, RecState<FAM, PREC> &ch,
+                                             unsigned &nrechk, Scalars *sc) {
+    using F = Fam<FAM>;
+    int32_t qn[F::ND], qt[F::LE];
+    child_qf<FAM, PREC>(P, lev, st, g32, g64, s, qn, nrechk, sc);
+#pragma unroll
+    for (int m = 0; m < F::LE; ++m) qt[m] = lev.st_ratio_log2[m] ? resnap_half(st.qt[m]) : st.qt[m];
+    ch.set(qn, qt, st.mult);
+}
+
+template <int FAM, int PREC, bool EMIT>
+__global__ void __launch_bounds__(256, 3) k_test2(Chunk c, Chunk c1, const uint8_t *__restrict__ pm2_in,
+                                                   uint8_t *pm2_out) {
+    using F = Fam<FAM>;
+    constexpr int NS = 1 << F::D;
+    const Problem &P = c.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = blockIdx.x % NS;
+    const int64_t tile = blockIdx.x / NS;
+    __shared__ float s_pg32[(NS + 1) * F::NB], s_cg32[(NS + 1) * F::NB];
+    __shared__ double s_pg64[NS * F::NB], s_cg64[NS * F::NB];
+    __shared__ unsigned s_red[8][3 * NS];
+    __shared__ int s_gi[NS];
+    __shared__ unsigned long long s_base[NS];
+    __shared__ unsigned s_wcnt[kRPT][8][NS];
+    if (s & ~c.lev.split_mask) return;
+    const int64_t t0 = c.r0 + tile * kTile;
+    const int64_t t1 = t0 + kTile < c.r1 ? t0 + kTile : c.r1;
+    const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
+    const int clast = (int)((int64_t)c.in.cell[t1 - 1] - c.c0);
+    unsigned nrechk = 0, ntest = 0;
+    if (cfirst == clast) {
+        const int cl = cfirst;
+        if (!c.alive[cl]) return;
+        const int ci = c.child_idx[(size_t)cl * NS + s];
+        if (ci < 0 || !c1.alive[ci]) return;                   // uniform over the block
+        for (int i = threadIdx.x; i < (NS + 1) * F::NB; i += blockDim.x) {
+            s_pg32[i] = c.geo32[(size_t)cl * (NS + 1) * F::NB + i];
+            s_cg32[i] = c1.geo32[(size_t)ci * (NS + 1) * F::NB + i];
+        }
+        for (int i = threadIdx.x; i < NS * F::NB; i += blockDim.x) {
+            s_pg64[i] = c.geo64[(size_t)cl * NS * F::NB + i];
+            s_cg64[i] = c1.geo64[(size_t)ci * NS * F::NB + i];
+        }
+        if (EMIT && threadIdx.x < NS) s_gi[threadIdx.x] = c1.child_idx[(size_t)ci * NS + threadIdx.x];
+        __syncthreads();
+        if (!EMIT) {
+            unsigned aub[NS], alb[NS], an[NS];
+#pragma unroll
+            for (int g = 0; g < NS; ++g) aub[g] = alb[g] = an[g] = 0;
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {
+                int64_t r = t0 + threadIdx.x + k * 256;
+                if (r >= t1) break;
+                if (!((c.passmask[r - c.r0] >> s) & 1)) continue;
+                RecState<FAM, PREC> st, ch;
+                st.load(c.in, r);
+                if (PREC == 1) st.prep32(P, c.lev, s_pg32 + NS * F::NB);
+                derive_child<FAM, PREC>(P, c.lev, st, s_pg32, s_pg64, s, ch, nrechk, c.sc);
+                if (PREC == 1) ch.prep32(P, c1.lev, s_cg32 + NS * F::NB);
+                else ch.need64(P, c1.lev);
+                unsigned ubm, lbm;
+                eval_record<FAM, PREC>(P, c1.lev, ch, s_cg32, s_cg64, ubm, lbm, nrechk);
+                pm2_out[(size_t)(r - c.r0) * NS + s] = (uint8_t)ubm;
+#pragma unroll
+                for (int g = 0; g < NS; ++g) {
+                    if (g & ~c1.lev.split_mask) continue;
+                    ++ntest;
+                    aub[g] += ((ubm >> g) & 1) ? ch.mult : 0u;
+                    alb[g] += ((lbm >> g) & 1) ? ch.mult : 0u;
+                    an[g] += (ubm >> g) & 1;
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < NS; ++g) {
+                unsigned a = __reduce_add_sync(kFull, aub[g]);
+                unsigned b = __reduce_add_sync(kFull, alb[g]);
+                unsigned d = __reduce_add_sync(kFull, an[g]);
+                if (lane == 0) {
+                    s_red[warp][3 * g] = a;
+                    s_red[warp][3 * g + 1] = b;
+                    s_red[warp][3 * g + 2] = d;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < 3 * NS) {
+                unsigned v = 0;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) v += s_red[w][threadIdx.x];
+                if (v) atomicAdd(c1.cnt + (size_t)ci * NS * 3 + threadIdx.x, v);
+            }
+        } else {
+            unsigned em[kRPT];
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {
+                int64_t r = t0 + threadIdx.x + k * 256;
+                unsigned m = 0;
+                if (r < t1 && ((c.passmask[r - c.r0] >> s) & 1)) {
+                    m = pm2_in[(size_t)(r - c.r0) * NS + s];
+#pragma unroll
+                    for (int g = 0; g < NS; ++g)
+                        if (s_gi[g] < 0) m &= ~(1u << g);
+                }
+                em[k] = m;
+#pragma unroll
+                for (int g = 0; g < NS; ++g) {
+                    unsigned b = __ballot_sync(kFull, (m >> g) & 1);
+                    if (lane == 0) s_wcnt[k][warp][g] = __popc(b);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < NS) {
+                int g = threadIdx.x;
+                unsigned run = 0;
+                for (int k = 0; k < kRPT; ++k)
+                    for (int w = 0; w < 8; ++w) {
+                        unsigned v = s_wcnt[k][w][g];
+                        s_wcnt[k][w][g] = run;
+                        run += v;
+                    }
+                s_base[g] = (run && s_gi[g] >= 0) ? atomicAdd(&c1.cursor[(size_t)ci * NS + g], run) : 0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {
+                unsigned m = em[k];
+                int64_t r = t0 + threadIdx.x + k * 256;
+                RecState<FAM, PREC> st, ch;
+                if (m) {
+                    st.load(c.in, r);
+                    if (PREC == 1) st.prep32(P, c.lev, s_pg32 + NS * F::NB);
+                    derive_child<FAM, PREC>(P, c.lev, st, s_pg32, s_pg64, s, ch, nrechk, c.sc);
+                    if (PREC == 1) ch.prep32(P, c1.lev, s_cg32 + NS * F::NB);
+                }
+#pragma unroll
+                for (int g = 0; g < NS; ++g) {
+                    unsigned b = __ballot_sync(kFull, (m >> g) & 1);
+                    if (!((m >> g) & 1)) continue;
+                    unsigned pos = (unsigned)s_base[g] + s_wcnt[k][warp][g] + __popc(b & ((1u << lane) - 1u));
+                    int32_t qn[F::ND];
+                    child_qf<FAM, PREC>(P, c1.lev, ch, s_cg32, s_cg64, g, qn, nrechk, c.sc);
+                    int gi = s_gi[g];
+                    write_child<FAM, PREC>(c1, ch, qn, gi, c1.next_cells.rbeg[gi] + pos);
+                }
+            }
+        }
+    } else {
+        // tile spans several level-l cells: per record, global atomics
+#pragma unroll 1
+        for (int k = 0; k < kRPT; ++k) {
+            int64_t r = t0 + threadIdx.x + k * 256;
+            if (r >= t1) break;
+            int cl = (int)((int64_t)c.in.cell[r] - c.c0);
+            if (!c.alive[cl] || !((c.passmask[r - c.r0] >> s) & 1)) continue;
+            int ci = c.child_idx[(size_t)cl * NS + s];
+            if (ci < 0 || !c1.alive[ci]) continue;
+            const float *pg32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
+            const double *pg64 = c.geo64 + (size_t)cl * NS * F::NB;
+            const float *cg32 = c1.geo32 + (size_t)ci * (NS + 1) * F::NB;
+            const double *cg64 = c1.geo64 + (size_t)ci * NS * F::NB;
+            RecState<FAM, PREC> st, ch;
+            st.load(c.in, r);
+            if (PREC == 1) st.prep32(P, c.lev, pg32 + NS * F::NB);
+            derive_child<FAM, PREC>(P, c.lev, st, pg32, pg64, s, ch, nrechk, c.sc);
+            if (PREC == 1) ch.prep32(P, c1.lev, cg32 + NS * F::NB);
+            else ch.need64(P, c1.lev);
+            if (!EMIT) {
+                unsigned ubm, lbm;
+                eval_record<FAM, PREC>(P, c1.lev, ch, cg32, cg64, ubm, lbm, nrechk);
+                pm2_out[(size_t)(r - c.r0) * NS + s] = (uint8_t)ubm;
+                for (int g = 0; g < NS; ++g) {
+                    if (g & ~c1.lev.split_mask) continue;
+                    ++ntest;
+                    uint32_t *b = c1.cnt + ((size_t)ci * NS + g) * 3;
+                    if ((ubm >> g) & 1) {
+                        atomicAdd(b, ch.mult);
+                        atomicAdd(b + 2, 1u);
+                    }
+                    if ((lbm >> g) & 1) atomicAdd(b + 1, ch.mult);
+                }
+            } else {
+                unsigned m = pm2_in[(size_t)(r - c.r0) * NS + s];
+                for (int g = 0; g < NS; ++g) {
+                    if (!((m >> g) & 1)) continue;
+                    int gi = c1.child_idx[(size_t)ci * NS + g];
+                    if (gi < 0) continue;
+                    unsigned pos = atomicAdd(&c1.cursor[(size_t)ci * NS + g], 1u);
+                    int32_t qn[F::ND];
+                    child_qf<FAM, PREC>(P, c1.lev, ch, cg32, cg64, g, qn, nrechk, c.sc);
+                    write_child<FAM, PREC>(c1, ch, qn, gi, c1.next_cells.rbeg[gi] + pos);
+                }
+            }
+        }
+    }
     ntest = __reduce_add_sync(kFull, ntest);
     nrechk = __reduce_add_sync(kFull, nrechk);
     if (lane == 0) {
@@ -855,6 +1095,21 @@ void launch_test(const Chunk &c, bool emit, cudaStream_t st) {
     } else {
         if (emit) { GV_DISPATCH(c.P.fam, (k_test<FAMV, 1, true><<<g, 256, 0, st>>>(c))); }
         else      { GV_DISPATCH(c.P.fam, (k_test<FAMV, 1, false><<<g, 256, 0, st>>>(c))); }
+    }
+}
+
+void launch_test2(const Chunk &c, const Chunk &c1, bool emit, const uint8_t *pm2_in, uint8_t *pm2_out,
+                  cudaStream_t st) {
+    int64_t nr = c.r1 - c.r0;
+    if (nr <= 0) return;
+    int ns = 1 << c.P.d;
+    unsigned g = blocks_for(nr, kTile) * ns;
+    if (c.precision == 0) {
+        if (emit) { GV_DISPATCH(c.P.fam, (k_test2<FAMV, 0, true><<<g, 256, 0, st>>>(c, c1, pm2_in, pm2_out))); }
+        else      { GV_DISPATCH(c.P.fam, (k_test2<FAMV, 0, false><<<g, 256, 0, st>>>(c, c1, pm2_in, pm2_out))); }
+    } else {
+        if (emit) { GV_DISPATCH(c.P.fam, (k_test2<FAMV, 1, true><<<g, 256, 0, st>>>(c, c1, pm2_in, pm2_out))); }
+        else      { GV_DISPATCH(c.P.fam, (k_test2<FAMV, 1, false><<<g, 256, 0, st>>>(c, c1, pm2_in, pm2_out))); }
     }
 }
 

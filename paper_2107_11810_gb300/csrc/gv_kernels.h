@@ -84,6 +84,10 @@ void launch_lift(const Problem &P, const Level &lev0, const double *prm, int64_t
 void launch_cell_geo(const Chunk &c, cudaStream_t st);
 void launch_test(const Chunk &c, bool emit, cudaStream_t st);
 void launch_child_lbmax(const Chunk &c, cudaStream_t st);
+// two levels per record read: c = level-l chunk, c1 = its level-(l+1) children
+// (pm2: grandchild pass masks, [r1 - r0][2^d] bytes)
+void launch_test2(const Chunk &c, const Chunk &c1, bool emit, const uint8_t *pm2_in, uint8_t *pm2_out,
+                  cudaStream_t st);
 // keepflag, recn: [nc * 2^d]; bsums: 2 * ceil(nc * 2^d / 256)
 void launch_child_alloc(const Chunk &c, uint32_t *keepflag, uint32_t *recn, unsigned long long *bsums,
                         cudaStream_t st);

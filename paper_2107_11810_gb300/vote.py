@@ -23,7 +23,7 @@ _lib = None
 
 VOTE_OPT_PRECISION, VOTE_OPT_PRUNE, VOTE_OPT_CHUNK_RECORDS = 1, 2, 3
 VOTE_OPT_TRACE_CAP, VOTE_OPT_GROUP, VOTE_OPT_FAULT_ALLOC_AT = 4, 5, 6
-VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING = 7, 8
+VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING, VOTE_OPT_TWO_LEVEL = 7, 8, 9
 KERNEL_CLASSES = ["lift", "cell_geo", "test_count", "test_emit", "children", "replay", "group", "spare"]
 STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
           5: "VOTE_ETIMEOUT", 6: "VOTE_EUNSUPPORTED", 7: "VOTE_EINTERNAL"}
@@ -103,7 +103,8 @@ class Solver:
     inlier mask (CUDA int32 tensor holding the uint32 words)."""
 
     def __init__(self, family: int, eps, bounds, precision: int = 1, prune: bool = True,
-                 chunk_records: int | None = None, trace_cap: int = 0, stream=None):
+                 chunk_records: int | None = None, trace_cap: int = 0, stream=None,
+                 two_level: float | None = None):
         self.lib = load()
         self.family = family
         self.d, self.k = FAMILY_DK[family]
@@ -119,6 +120,8 @@ class Solver:
             self.set_option(VOTE_OPT_CHUNK_RECORDS, chunk_records)
         if trace_cap:
             self.set_option(VOTE_OPT_TRACE_CAP, trace_cap)
+        if two_level is not None:
+            self.set_option(VOTE_OPT_TWO_LEVEL, two_level)
         if stream is not None:
             self.set_stream(stream)
 

@@ -140,6 +140,30 @@ def test_cell_counts_replay_equals_oracle(family):
             assert np.array_equal(v.mask_words_to_numpy(reach), oreach)
 
 
+@pytest.mark.parametrize("family", FAMS)
+@pytest.mark.parametrize("two_level", [0.0, 1e-9])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_level_expansion_parity(family, two_level, precision):
+    # 1e-9: every expansion with a grandchild level takes the two-level path
+    p = small(family, 2500, 13)
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    g = gpu_solve(p, precision, two_level=two_level, chunk_records=3000)
+    assert_same(g, o, p.n)
+
+
+def test_two_level_trace_equals_oracle_without_pruning():
+    p = small(inputs.POSE3DOF, 400, 14)
+    cap = 4_000_000
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params, flags=oracle.NO_PRUNE, trace_cap=cap)
+    g = gpu_solve(p, 1, prune=False, trace_cap=cap, two_level=1e-9)
+    tg = g["solver"].trace(cap)
+    to = o["trace"]
+    key = lambda l, c: (int(l), tuple(int(x) for x in c))
+    dg = {key(l, c): (int(u), int(b)) for l, c, u, b in zip(tg["level"], tg["coords"], tg["ub"], tg["lb"])}
+    do = {key(l, c): (int(u), int(b)) for l, c, u, b in zip(to["level"], to["coords"], to["ub"], to["lb"])}
+    assert dg == do
+
+
 @pytest.mark.parametrize("chunk", [1, 7, 1000])
 def test_chunking_does_not_change_results(chunk):
     p = small(inputs.POSE3DOF, 3000, 8)
