@@ -182,7 +182,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gv", choices=["gv", "reference"])
     ap.add_argument("--workload", default="plane3d_n1e6", choices=sorted(WORKLOADS))
@@ -269,7 +269,7 @@ def main():
     # end to end through the public API with host buffers
     pinned = torch.from_numpy(p.params).pin_memory()
     e2e_times = []
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rh = s.solve_host(pinned)

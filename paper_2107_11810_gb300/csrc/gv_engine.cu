@@ -540,7 +540,10 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     CK(cudaMemcpyAsync(&c->h_sc->n_cells, &dsc(c)->n_cells, 16, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     int64_t new_cells = (int64_t)c->h_sc->n_cells, new_recs = (int64_t)c->h_sc->n_recs;
-    if (c->two_level > 0 && l + 2 <= P.L && new_cells > 0 && (double)new_recs > c->two_level * (double)nr)
+    // two levels per read only pays when parent cells hold whole tiles of records
+    // (blocks then stay on one cell and reduce in registers)
+    if (c->two_level > 0 && l + 2 <= P.L && new_cells > 0 && (double)new_recs > c->two_level * (double)nr &&
+        (c->two_level < 1e-3 || nr >= 2048 * (int64_t)nc))
         return expand_two(c, l, ch, nr, new_cells, new_recs);
     if (new_recs > 0) {
         TRY(ensure_level(c, l + 1, (size_t)new_recs, 0));

@@ -449,7 +449,7 @@ constexpr int kTile = 256 * kRPT;    // records per block
 // reserves the child ranges with one atomic per child and a block scan.  Tiles
 // spanning several cells fall back to warp-level aggregation.
 template <int FAM, int PREC, bool EMIT>
-__global__ void __launch_bounds__(256, 3) k_test(Chunk c) {
+__global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
     using F = Fam<FAM>;
     constexpr int NS = 1 << F::D;
     const Problem &P = c.P;
@@ -479,17 +479,12 @@ __global__ void __launch_bounds__(256, 3) k_test(Chunk c) {
             unsigned aub[NS], alb[NS], an[NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) aub[s] = alb[s] = an[s] = 0;
-            RecState<FAM, PREC> sts[kRPT];
-#pragma unroll
-            for (int k = 0; k < kRPT; ++k) {       // issue every load of the tile first
-                int64_t r = t0 + threadIdx.x + k * 256;
-                if (r < t1) sts[k].load(c.in, r);
-            }
 #pragma unroll
             for (int k = 0; k < kRPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
                 if (r >= t1) break;
-                RecState<FAM, PREC> &st = sts[k];
+                RecState<FAM, PREC> st;
+                st.load(c.in, r);
                 if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
                 else st.need64(P, lev);
                 unsigned ubm, lbm;
@@ -696,7 +691,7 @@ __device__ __forceinline__ void derive_child(const Problem &P, const Level &lev,
 }
 
 template <int FAM, int PREC, bool EMIT>
-__global__ void __launch_bounds__(256, 3) k_test2(Chunk c, Chunk c1, const uint8_t *__restrict__ pm2_in,
+__global__ void __launch_bounds__(256, 4) k_test2(Chunk c, Chunk c1, const uint8_t *__restrict__ pm2_in,
                                                    uint8_t *pm2_out) {
     using F = Fam<FAM>;
     constexpr int NS = 1 << F::D;
