@@ -187,7 +187,9 @@ def main():
     ap.add_argument("--impl", default="gv", choices=["gv", "reference"])
     ap.add_argument("--workload", default="plane3d_n1e6", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
+    ap.add_argument("--fp64", action="store_true",
+                    help="also time the plain-FP64 predicate path on the same workload and check identical results "
+                         "(FP64 runs at a small fraction of the FP32 rate on GB300: ~400 s for the plane workload)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--ref-tests-per-problem", type=float, default=0.0)
@@ -287,7 +289,9 @@ def main():
                result=dict(depth=depth, best_leaf=leaf, best_point=r["best_point"].tolist()),
                gpu_launches=launches, roofline=roof, e2e=e2e, clocks=clk.summary(),
                kernel_ms={k: round(v[0] / args.steps, 3) for k, v in kt.items() if v[1]})
-    if not args.no_fp64 and args.precision == 1:
+    if not args.fp64:
+        out["fp64_plain"] = dict(skipped="run with --fp64 (one plain-FP64 solve of the same workload)")
+    if args.fp64 and args.precision == 1:
         s.set_option(vote.VOTE_OPT_PRECISION, 0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -320,7 +324,7 @@ def main():
 
 # tests per full problem measured by the GPU path (used to scale the reference
 # arm's oracle sample to problems/s); refreshed from bench runs
-REF_TESTS = {"plane3d_n1e6": 0.0, "pose3dof_n1e6": 3.538858716e9, "line2d_n1e4": 8.324422e6}
+REF_TESTS = {"plane3d_n1e6": 1.0234815691064e13, "pose3dof_n1e6": 3.864138264e9, "line2d_n1e4": 8.324422e6}
 
 if __name__ == "__main__":
     main()

@@ -705,6 +705,9 @@ __global__ void __launch_bounds__(256, 4) k_test2(Chunk c, Chunk c1, const uint8
     __shared__ int s_gi[NS];
     __shared__ unsigned long long s_base[NS];
     __shared__ unsigned s_wcnt[kRPT][8][NS];
+    __shared__ int s_list[kTile];
+    __shared__ uint8_t s_em[kTile];
+    __shared__ unsigned s_n;
     if (s & ~c.lev.split_mask) return;
     const int64_t t0 = c.r0 + tile * kTile;
     const int64_t t1 = t0 + kTile < c.r1 ? t0 + kTile : c.r1;
@@ -725,16 +728,44 @@ __global__ void __launch_bounds__(256, 4) k_test2(Chunk c, Chunk c1, const uint8
             s_cg64[i] = c1.geo64[(size_t)ci * NS * F::NB + i];
         }
         if (EMIT && threadIdx.x < NS) s_gi[threadIdx.x] = c1.child_idx[(size_t)ci * NS + threadIdx.x];
+        if (threadIdx.x == 0) s_n = 0;
         __syncthreads();
+        // Compact the tile's records that have work for child s (count pass: pass
+        // child s; emit pass: also reach a surviving grandchild) so that every lane
+        // of a warp works on one.
+#pragma unroll
+        for (int k = 0; k < kRPT; ++k) {
+            int64_t r = t0 + threadIdx.x + k * 256;
+            unsigned m = 0;
+            if (r < t1 && ((c.passmask[r - c.r0] >> s) & 1)) {
+                if (!EMIT) {
+                    m = 1;
+                } else {
+                    m = pm2_in[(size_t)(r - c.r0) * NS + s];
+#pragma unroll
+                    for (int g = 0; g < NS; ++g)
+                        if (s_gi[g] < 0) m &= ~(1u << g);
+                }
+            }
+            unsigned b = __ballot_sync(kFull, m != 0);
+            unsigned base = 0;
+            if (lane == 0 && b) base = atomicAdd(&s_n, (unsigned)__popc(b));
+            base = __shfl_sync(kFull, base, 0);
+            if (m) {
+                unsigned at = base + __popc(b & ((1u << lane) - 1u));
+                s_list[at] = (int)(r - t0);
+                s_em[at] = (uint8_t)m;
+            }
+        }
+        __syncthreads();
+        const int nlist = (int)s_n;
         if (!EMIT) {
             unsigned aub[NS], alb[NS], an[NS];
 #pragma unroll
             for (int g = 0; g < NS; ++g) aub[g] = alb[g] = an[g] = 0;
-#pragma unroll
-            for (int k = 0; k < kRPT; ++k) {
-                int64_t r = t0 + threadIdx.x + k * 256;
-                if (r >= t1) break;
-                if (!((c.passmask[r - c.r0] >> s) & 1)) continue;
+#pragma unroll 1
+            for (int i = threadIdx.x; i < nlist; i += 256) {
+                int64_t r = t0 + s_list[i];
                 RecState<FAM, PREC> st, ch;
                 st.load(c.in, r);
                 if (PREC == 1) st.prep32(P, c.lev, s_pg32 + NS * F::NB);
@@ -772,18 +803,11 @@ __global__ void __launch_bounds__(256, 4) k_test2(Chunk c, Chunk c1, const uint8
                 if (v) atomicAdd(c1.cnt + (size_t)ci * NS * 3 + threadIdx.x, v);
             }
         } else {
-            unsigned em[kRPT];
+            // positions in (iteration, warp, lane) order over the compacted list
 #pragma unroll
             for (int k = 0; k < kRPT; ++k) {
-                int64_t r = t0 + threadIdx.x + k * 256;
-                unsigned m = 0;
-                if (r < t1 && ((c.passmask[r - c.r0] >> s) & 1)) {
-                    m = pm2_in[(size_t)(r - c.r0) * NS + s];
-#pragma unroll
-                    for (int g = 0; g < NS; ++g)
-                        if (s_gi[g] < 0) m &= ~(1u << g);
-                }
-                em[k] = m;
+                int i = threadIdx.x + k * 256;
+                unsigned m = i < nlist ? s_em[i] : 0u;
 #pragma unroll
                 for (int g = 0; g < NS; ++g) {
                     unsigned b = __ballot_sync(kFull, (m >> g) & 1);
@@ -803,12 +827,14 @@ __global__ void __launch_bounds__(256, 4) k_test2(Chunk c, Chunk c1, const uint8
                 s_base[g] = (run && s_gi[g] >= 0) ? atomicAdd(&c1.cursor[(size_t)ci * NS + g], run) : 0;
             }
             __syncthreads();
-#pragma unroll
+#pragma unroll 1
             for (int k = 0; k < kRPT; ++k) {
-                unsigned m = em[k];
-                int64_t r = t0 + threadIdx.x + k * 256;
+                int i = threadIdx.x + k * 256;
+                if (k * 256 >= nlist) break;                     // uniform
+                unsigned m = i < nlist ? s_em[i] : 0u;
                 RecState<FAM, PREC> st, ch;
                 if (m) {
+                    int64_t r = t0 + s_list[i];
                     st.load(c.in, r);
                     if (PREC == 1) st.prep32(P, c.lev, s_pg32 + NS * F::NB);
                     derive_child<FAM, PREC>(P, c.lev, st, s_pg32, s_pg64, s, ch, nrechk, c.sc);
