@@ -90,7 +90,7 @@ typedef enum {
     VOTE_OPT_TWO_LEVEL = 9    /* expand two levels per read of a chunk's records when
                                  its children would hold more than this many times
                                  its records (their records are then never written
-                                 to memory); 0 = never; default 2 */
+                                 to memory); 0 = never (default)                     */
 } vote_option;
 
 /* Kernel classes reported by vote_get_kernel_times. */

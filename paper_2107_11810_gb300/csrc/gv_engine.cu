@@ -72,7 +72,7 @@ struct vote_ctx {
     int64_t chunk_records = 1 << 25;
     uint32_t initial_lb = 0;
     int kernel_timing = 0;
-    double two_level = 2.0;
+    double two_level = 0.0;
     static const int kEv = 24;
     cudaEvent_t ev[kEv] = {};
     int ev_n = 0;              // events recorded since the last collection
