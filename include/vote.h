@@ -182,6 +182,32 @@ vote_status vote_get_kernel_times(vote_ctx *ctx, double *ms, int64_t *launches, 
  * level l, for l in [0, L) (host arrays of at least L entries). */
 vote_status vote_get_level_stats(vote_ctx *ctx, int64_t *cells, int64_t *records);
 
+/* UB and LB of one cell, like vote_cell_counts, for callers that cannot allocate
+ * device memory: code running where cudaMalloc is not allowed or not wanted (a
+ * host that pre-plans all GPU memory, a real-time loop with a fixed memory
+ * budget, a plugin inside another framework's allocator).  There is no
+ * counterpart in the paper; it exists for such callers.
+ *
+ * It needs no context and allocates nothing: its scratch (level constants, the
+ * root-to-cell path geometry and two counters, VOTE_NOALLOC_SCRATCH_BYTES in all)
+ * is one file-scope __device__ array of the library, which every GPU that loads
+ * the library holds until the process exits.  The caller passes the inputs and
+ * outputs exactly as for vote_cell_counts, plus the CUDA stream to use (NULL:
+ * legacy default stream).
+ *   family, d, k, eps[d], bounds[2d]   as for vote_create;
+ *   surfaces, n, level, coords, ub, lb, reach   as for vote_cell_counts.
+ * Problems with more levels than the array holds (L > 31) return
+ * VOTE_EUNSUPPORTED.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (the counters
+ * are cleared at the start of each call): calls that may overlap on the GPU (on
+ * different streams or host threads) race and must be serialised by the caller.
+ * The call synchronises the stream before returning. */
+#define VOTE_NOALLOC_SCRATCH_BYTES 32768
+vote_status vote_cell_counts_noalloc(int family, int d, int k, const double *eps, const double *bounds,
+                                     const double *surfaces, int64_t n, int level, const int64_t *coords,
+                                     int64_t *ub, int64_t *lb, uint32_t *reach, void *cuda_stream);
+
 /* Message for the last error on this host thread (static storage). */
 const char *vote_last_error(void);
 

@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "gv_kernels.h"
@@ -918,3 +919,82 @@ void vote_destroy(vote_ctx *c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Entry point without allocation (vote_cell_counts_noalloc).  Its scratch is this
+// file-scope device array; host code must not use the symbol as an address (in
+// host code it names a host-side stand-in), so the device address is looked up
+// once per device with cudaGetSymbolAddress and passed to the kernels.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[VOTE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr size_t kNaLevels = 0;
+constexpr size_t kNaPath = kNaLevels + sizeof(Level) * GV_MAXL;
+constexpr size_t kNaScalars = (kNaPath + sizeof(PathStep) * GV_MAXL + 255) / 256 * 256;
+constexpr size_t kNaEnd = kNaScalars + sizeof(Scalars);
+static_assert(kNaEnd <= VOTE_NOALLOC_SCRATCH_BYTES, "no-alloc scratch too small");
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+unsigned char *g_na_ptr[kNaMaxDevices] = {};
+}  // namespace
+
+static vote_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNaMaxDevices) {
+        set_err("device %d out of range", dev);
+        return VOTE_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void *p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));   // once per device, this device current
+        g_na_ptr[dev] = (unsigned char *)p;
+    }
+    *out = g_na_ptr[dev];
+    return VOTE_OK;
+}
+
+extern "C" vote_status vote_cell_counts_noalloc(int family, int d, int k, const double *eps, const double *bounds,
+                                                const double *surfaces, int64_t n, int level,
+                                                const int64_t *coords, int64_t *ub, int64_t *lb, uint32_t *reach,
+                                                void *cuda_stream) {
+    if (!eps || !bounds || !coords || !ub || !lb || n < 0 || (n > 0 && !surfaces)) {
+        set_err("invalid arguments");
+        return VOTE_EINVAL;
+    }
+    vote_ctx tmp;                        // host-side constants only (no device memory)
+    TRY(problem_init(&tmp, family, d, k, eps, bounds));
+    const Problem &P = tmp.P;
+    if (P.L > GV_MAXL - 1) {
+        set_err("%d levels exceed the no-alloc scratch (%d)", P.L, GV_MAXL - 1);
+        return VOTE_EUNSUPPORTED;
+    }
+    if (level < 0 || level > P.L) { set_err("level %d outside [0, %d]", level, P.L); return VOTE_EINVAL; }
+    uint64_t key = 0;
+    for (int j = 0; j < P.d; ++j) {
+        int e = level < P.Lj[j] ? level : P.Lj[j];
+        if (coords[j] < 0 || coords[j] >= ((int64_t)1 << e)) { set_err("coordinate %d out of range", j); return VOTE_EINVAL; }
+        key |= (uint64_t)coords[j] << (P.coord_shift[j] + P.Lj[j] - e);
+    }
+    if (n == 0) { *ub = 0; *lb = 0; return VOTE_OK; }
+    unsigned char *base = nullptr;
+    TRY(noalloc_scratch(&base));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    Level *levs = (Level *)(base + kNaLevels);
+    PathStep *path = (PathStep *)(base + kNaPath);
+    Scalars *sc = (Scalars *)(base + kNaScalars);
+    if (P.L > 0) CK(cudaMemcpyAsync(levs, tmp.lev, sizeof(Level) * P.L, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(sc, 0, sizeof(Scalars), st));        // the counters must start at zero
+    if (level > 0) launch_path_geo(P, levs, level, key, path, st);
+    launch_replay(P, levs, path, level, surfaces, n, reach, sc, st);
+    CK(cudaGetLastError());
+    unsigned long long cnt[2] = {0, 0};
+    CK(cudaMemcpyAsync(cnt, &sc->replay_ub, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *ub = (int64_t)cnt[0];
+    *lb = (int64_t)cnt[1];
+    return VOTE_OK;
+}

@@ -30,7 +30,7 @@ STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: 
 NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4}
 EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
            "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_get_kernel_times",
-           "vote_get_level_stats",
+           "vote_get_level_stats", "vote_cell_counts_noalloc",
            "vote_last_error", "vote_destroy"]
 
 
@@ -71,6 +71,7 @@ def load(path: str | None = None):
             lib.vote_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
             lib.vote_get_kernel_times.argtypes = [P, P, P, P]
             lib.vote_get_level_stats.argtypes = [P, P, P]
+            lib.vote_cell_counts_noalloc.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P]
             lib.vote_last_error.restype = ctypes.c_char_p
             lib.vote_last_error.argtypes = []
             lib.vote_destroy.argtypes = [P]
@@ -234,6 +235,26 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def cell_counts_noalloc(family: int, eps, bounds, surfaces, level: int, coords, reach=None, stream=None):
+    """UB and LB of one cell through the entry point that allocates no device memory
+    (its scratch is a fixed array inside the library).  ``surfaces``: CUDA float64
+    [P, n]; ``reach``: optional CUDA int32 tensor of (n+31)//32 words to receive the
+    reach mask.  Calls that may overlap on the GPU must be serialised by the caller."""
+    lib = load()
+    d, k = FAMILY_DK[family]
+    e = np.ascontiguousarray(eps, dtype=np.float64).reshape(d)
+    b = np.ascontiguousarray(bounds, dtype=np.float64).reshape(2 * d)
+    c = np.ascontiguousarray(coords, dtype=np.int64).reshape(d)
+    ub = np.zeros(1, np.int64)
+    lb = np.zeros(1, np.int64)
+    handle = None
+    if stream is not None:
+        handle = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.vote_cell_counts_noalloc(family, d, k, _ptr(e), _ptr(b), _ptr(surfaces), surfaces.shape[1],
+                                        int(level), _ptr(c), _ptr(ub), _ptr(lb), _ptr(reach), handle))
+    return int(ub[0]), int(lb[0])
 
 
 def mask_words_to_numpy(mask) -> np.ndarray:
