@@ -87,6 +87,8 @@ typedef enum {
                                  exceed the true maximum depth; default 0            */
     VOTE_OPT_KERNEL_TIMING = 8, /* 1 = time each kernel class with CUDA events on the
                                  context's stream (see vote_get_kernel_times)        */
+    VOTE_OPT_BATCH_WORKERS = 10, /* host workers (streams) of vote_solve_batched, 1..32,
+                                 default 4                                           */
     VOTE_OPT_TWO_LEVEL = 9    /* expand two levels per read of a chunk's records when
                                  its children would hold more than this many times
                                  its records (their records are then never written
@@ -151,6 +153,22 @@ vote_status vote_solve(vote_ctx *ctx, const double *surfaces, int64_t n, double 
 vote_status vote_solve_host(vote_ctx *ctx, const double *surfaces, int64_t n, double *best_point,
                             int64_t *best_leaf, int64_t *depth, uint32_t *inlier_mask);
 
+/* Solve B independent problems of this context's family, eps and bounds.
+ *   surfaces    device: problem b's surfaces are the FP64 structure-of-arrays
+ *               block [P][n_b] starting at element P * offsets[b];
+ *   offsets     host [B+1], offsets[0] = 0, n_b = offsets[b+1] - offsets[b];
+ *   best_points host [B*d];  best_leaves host [B*d] or NULL;  depths host [B];
+ *   masks       device or NULL: problem b's mask words start at word
+ *               sum_{b'<b} ceil(n_b'/32);
+ *   latency_ms  host [B] or NULL: completion time of each problem, in ms from
+ *               the start of the call.
+ * Problems are taken from a shared queue by VOTE_OPT_BATCH_WORKERS host workers,
+ * each with its own stream and working memory, so small problems overlap on the
+ * GPU.  Each problem's results equal those of vote_solve on it alone. */
+vote_status vote_solve_batched(vote_ctx *ctx, const double *surfaces, const int64_t *offsets, int B,
+                               double *best_points, int64_t *best_leaves, int64_t *depths, uint32_t *masks,
+                               double *latency_ms);
+
 /* Upper and lower bound of one cell, by replaying every surface from the root
  * along the path to the cell (the counts Algorithm 2 assigns to that cell,
  * independent of pruning).
@@ -159,6 +177,33 @@ vote_status vote_solve_host(vote_ctx *ctx, const double *surfaces, int64_t n, do
  *             [(n+31)/32] or NULL (bit set per surface reaching the cell). */
 vote_status vote_cell_counts(vote_ctx *ctx, const double *surfaces, int64_t n, int level,
                              const int64_t *coords, int64_t *ub, int64_t *lb, uint32_t *reach);
+
+/* Soft inlier score used to refine the voting result (not part of the paper's
+ * voting itself; Sec. 4.2 hands the approximate pose to "a more accurate
+ * method"):
+ *     S(p) = sum_i w_i exp(-u_i^2 / 2),   u_i^2 = sum_j (r_ij / tol_j)^2,
+ * r_ij the vertical residual of surface i at point p in dependent coordinate j
+ * (Eq. 1, global form), w_i = bit i of mask (NULL: all ones).
+ *   surfaces  device [P][n];  mask device [(n+31)/32] or NULL;  point device [d];
+ *   tol       host [d-k] or NULL (= eps of the dependent coordinates);
+ *   score     device [1] (forward).
+ * Backward: grad_score device [1] (upstream gradient); grad_point device [d] or
+ * NULL receives grad_score * dS/dp; grad_surfaces device [P][n] or NULL receives
+ * grad_score * dS/d(surface parameters).  Residuals are recomputed, not stored.
+ * Reductions are deterministic (fixed grid, ordered final sum). */
+vote_status vote_softscore_fwd(vote_ctx *ctx, const double *surfaces, int64_t n, const uint32_t *mask,
+                               const double *point, const double *tol, double *score);
+vote_status vote_softscore_bwd(vote_ctx *ctx, const double *surfaces, int64_t n, const uint32_t *mask,
+                               const double *point, const double *tol, const double *grad_score,
+                               double *grad_point, double *grad_surfaces);
+
+/* Projected gradient ascent of S inside the box [cell_lo, cell_hi] (host [d]),
+ * preconditioned by the squared box widths, with Armijo backtracking, at most
+ * iters steps.  point_inout host [d] (start, clamped into the box; result);
+ * score_out host or NULL: S at the result.  mask/tol as for vote_softscore_fwd. */
+vote_status vote_refine(vote_ctx *ctx, const double *surfaces, int64_t n, const uint32_t *mask,
+                        const double *cell_lo, const double *cell_hi, const double *tol, int iters,
+                        double *point_inout, double *score_out);
 
 /* Number of levels L and per-coordinate split counts L_j (host [d]). */
 vote_status vote_levels(vote_ctx *ctx, int *L, int *Lj);

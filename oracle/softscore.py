@@ -1,0 +1,42 @@
+"""Oracle of the soft inlier score (test infrastructure only).
+
+Plain PyTorch CPU FP64, the definition written out:
+    S(p) = sum_i w_i exp(-u_i^2 / 2),  u_i^2 = sum_j (r_ij / tol_j)^2,
+with r_ij the vertical residual of surface i at p in dependent coordinate j
+(Eq. 1 of the paper in global form: r = p_dep - F(p_free; t) - g).  Gradients come
+from torch.autograd on these CPU tensors.
+Pins: tests/test_softscore_oracle.py (hand-computed single-surface values, exact
+inliers, central finite differences, the plane double cover).
+"""
+from __future__ import annotations
+
+import torch
+
+LINE2D, PLANE3D_SPH, POSE3DOF = 1, 2, 3
+
+
+def residuals(family: int, params: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
+    """[n, d-k] residuals (CPU float64)."""
+    if family == LINE2D:                       # b = y - x m
+        x, y = params[0], params[1]
+        return (p[1] - (y - x * p[0]))[:, None]
+    if family == PLANE3D_SPH:                  # d = q . (sin th cos ph, sin th sin ph, cos th)
+        qx, qy, qz = params[0], params[1], params[2]
+        nx = torch.sin(p[0]) * torch.cos(p[1])
+        ny = torch.sin(p[0]) * torch.sin(p[1])
+        nz = torch.cos(p[0])
+        return (p[2] - (qx * nx + qy * ny + qz * nz))[:, None]
+    if family == POSE3DOF:                     # x = w1 - (a cos - b sin), y = w2 - (a sin + b cos)
+        w1, w2, a, b = params[0], params[1], params[2], params[3]
+        c, s = torch.cos(p[0]), torch.sin(p[0])
+        rx = p[1] - (w1 - (a * c - b * s))
+        ry = p[2] - (w2 - (a * s + b * c))
+        return torch.stack([rx, ry], dim=1)
+    raise ValueError(family)
+
+
+def softscore(family: int, params: torch.Tensor, p: torch.Tensor, weights: torch.Tensor, tol) -> torch.Tensor:
+    r = residuals(family, params, p)
+    tol = torch.as_tensor(tol, dtype=torch.float64)
+    u2 = ((r / tol) ** 2).sum(dim=1)
+    return (weights * torch.exp(-0.5 * u2)).sum()

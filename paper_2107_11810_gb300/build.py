@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvote.so")
-SOURCES = ["gv_kernels.cu", "gv_engine.cu"]
+SOURCES = ["gv_kernels.cu", "gv_engine.cu", "gv_softscore.cu"]
 HEADERS = ["gv_device.cuh", "gv_kernels.h"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

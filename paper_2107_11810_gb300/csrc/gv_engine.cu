@@ -17,8 +17,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "gv_kernels.h"
 #include "vote.h"
@@ -74,6 +77,10 @@ struct vote_ctx {
     uint32_t initial_lb = 0;
     int kernel_timing = 0;
     double two_level = 0.0;
+    int batch_workers = 4;
+    int family = 0;
+    double eps_in[GV_MAXD] = {}, bounds_in[2 * GV_MAXD] = {};
+    std::vector<vote_ctx *> workers;   // sub-contexts of vote_solve_batched
     static const int kEv = 24;
     cudaEvent_t ev[kEv] = {};
     int ev_n = 0;              // events recorded since the last collection
@@ -88,6 +95,7 @@ struct vote_ctx {
     DevBuf levs_dev, path, scal, alive, geo64, geo32, cnt, passmask, child_idx, cursor, keepflag, recn, bsums;
     DevBuf tr_level, tr_key, tr_ub, tr_lb, surf_tmp, mask_tmp;
     DevBuf alive1, geo64b, geo32b, cntb, pm2, child_idxb, cursorb;
+    DevBuf ss_partial, ss_io;  // soft score: block partials; point [d] + outputs [d] + grad_out [1]
     Scalars *h_sc = nullptr;   // pinned mirror of the device scalars
     uint64_t *h_tmp = nullptr; // pinned slot for single values
     int64_t trace_written = 0;
@@ -701,6 +709,12 @@ vote_status vote_create(int family, int d, int k, const double *eps, const doubl
         return s;
     }
     c->ns = 1 << d;
+    c->family = family;
+    for (int j = 0; j < d; ++j) {
+        c->eps_in[j] = eps[j];
+        c->bounds_in[2 * j] = bounds[2 * j];
+        c->bounds_in[2 * j + 1] = bounds[2 * j + 1];
+    }
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_sc, sizeof(Scalars));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_tmp, 64);
@@ -778,6 +792,10 @@ vote_status vote_set_option(vote_ctx *c, int key, double v) {
         if (!(v >= 0 && v <= 1e6)) break;
         c->two_level = v;
         return VOTE_OK;
+    case VOTE_OPT_BATCH_WORKERS:
+        if (!(v >= 1 && v <= 32)) break;
+        c->batch_workers = (int)v;
+        return VOTE_OK;
     default:
         set_err("unknown option %d", key);
         return VOTE_EINVAL;
@@ -815,6 +833,78 @@ vote_status vote_solve_host(vote_ctx *c, const double *surfaces, int64_t n, doub
     return VOTE_OK;
 }
 
+vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_t *offsets, int B,
+                               double *best_points, int64_t *best_leaves, int64_t *depths, uint32_t *masks,
+                               double *latency_ms) {
+    if (!c || !offsets || B < 0 || !best_points || !depths) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    if (offsets[0] != 0) { set_err("offsets[0] must be 0"); return VOTE_EINVAL; }
+    for (int b = 0; b < B; ++b)
+        if (offsets[b + 1] < offsets[b]) { set_err("offsets must be non-decreasing"); return VOTE_EINVAL; }
+    if (B == 0) return VOTE_OK;
+    if (offsets[B] > 0 && !surfaces) { set_err("null surfaces"); return VOTE_EINVAL; }
+    const int d = c->P.d, np = c->P.np;
+    int nw = c->batch_workers < B ? c->batch_workers : B;
+    CK(cudaSetDevice(c->device));
+    while ((int)c->workers.size() < nw) {     // sub-contexts with their own streams
+        vote_ctx *w = nullptr;
+        TRY(vote_create(c->family, d, c->P.k, c->eps_in, c->bounds_in, &w));
+        cudaStream_t ws;
+        cudaError_t e = cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { vote_destroy(w); set_err("stream creation failed"); return VOTE_ECUDA; }
+        w->stream = ws;
+        c->workers.push_back(w);
+    }
+    for (int i = 0; i < nw; ++i) {
+        vote_ctx *w = c->workers[i];
+        w->precision = c->precision;
+        w->prune = c->prune;
+        w->chunk_records = c->chunk_records;
+        w->two_level = c->two_level;
+        w->fault_alloc_at = 0;
+    }
+    std::vector<int64_t> wordoff(B + 1, 0);
+    for (int b = 0; b < B; ++b) wordoff[b + 1] = wordoff[b] + (offsets[b + 1] - offsets[b] + 31) / 32;
+    CK(cudaStreamSynchronize(c->stream));     // inputs written on the caller's stream are visible
+    std::atomic<int> next(0);
+    std::atomic<int> failed(0);
+    std::vector<vote_status> wst(nw, VOTE_OK);
+    std::vector<std::string> wmsg(nw);
+    auto t0 = std::chrono::steady_clock::now();
+    auto work = [&](int wi) {
+        vote_ctx *w = c->workers[wi];
+        cudaSetDevice(c->device);
+        for (;;) {
+            int b = next.fetch_add(1);
+            if (b >= B || failed.load()) break;
+            int64_t n = offsets[b + 1] - offsets[b];
+            vote_status st = solve_device(w, surfaces + np * offsets[b], n, best_points + (size_t)b * d,
+                                          best_leaves ? best_leaves + (size_t)b * d : nullptr, depths + b,
+                                          masks ? masks + wordoff[b] : nullptr);
+            if (st != VOTE_OK) {
+                wst[wi] = st;
+                wmsg[wi] = g_err;
+                failed.store(1);
+                break;
+            }
+            if (latency_ms)
+                latency_ms[b] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+    };
+    std::vector<std::thread> th;
+    for (int i = 1; i < nw; ++i) th.emplace_back(work, i);
+    work(0);
+    for (auto &t : th) t.join();
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    for (int i = 0; i < nw; ++i) {
+        if (wst[i] != VOTE_OK) {
+            set_err("%s", wmsg[i].c_str());
+            return wst[i];
+        }
+    }
+    c->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return VOTE_OK;
+}
+
 vote_status vote_cell_counts(vote_ctx *c, const double *surfaces, int64_t n, int level, const int64_t *coords,
                              int64_t *ub, int64_t *lb, uint32_t *reach) {
     if (!c || !coords || !ub || !lb || n < 0 || (n > 0 && !surfaces)) { set_err("invalid arguments"); return VOTE_EINVAL; }
@@ -828,6 +918,101 @@ vote_status vote_cell_counts(vote_ctx *c, const double *surfaces, int64_t n, int
     }
     if (n == 0) { *ub = 0; *lb = 0; return VOTE_OK; }
     TRY(replay(c, surfaces, n, level, key, reach, ub, lb));
+    return VOTE_OK;
+}
+
+static vote_status ss_prepare(vote_ctx *c, const double *tol, double *inv_tol2) {
+    const Problem &P = c->P;
+    for (int j = 0; j < P.nd; ++j) {
+        double t = tol ? tol[j] : P.eps[P.k + j];
+        if (!(t > 0.0) || !std::isfinite(t)) { set_err("tol must be finite and > 0"); return VOTE_EINVAL; }
+        inv_tol2[j] = 1.0 / (t * t);
+    }
+    TRY(ensure(c, c->ss_partial, sizeof(double) * softscore_partial_doubles()));
+    TRY(ensure(c, c->ss_io, sizeof(double) * (2 * GV_MAXD + 2)));
+    return VOTE_OK;
+}
+
+vote_status vote_softscore_fwd(vote_ctx *c, const double *surfaces, int64_t n, const uint32_t *mask,
+                               const double *point, const double *tol, double *score) {
+    if (!c || n < 0 || (n > 0 && !surfaces) || !point || !score) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    double inv_tol2[GV_MAXD];
+    TRY(ss_prepare(c, tol, inv_tol2));
+    if (n == 0) { CK(cudaMemsetAsync(score, 0, sizeof(double), c->stream)); return VOTE_OK; }
+    launch_softscore(c->P.fam, false, surfaces, n, mask, point, inv_tol2, c->P.nd, nullptr, nullptr,
+                     (double *)c->ss_partial.p, score, c->stream);
+    CK(cudaGetLastError());
+    return VOTE_OK;
+}
+
+vote_status vote_softscore_bwd(vote_ctx *c, const double *surfaces, int64_t n, const uint32_t *mask,
+                               const double *point, const double *tol, const double *grad_score,
+                               double *grad_point, double *grad_surfaces) {
+    if (!c || n < 0 || (n > 0 && !surfaces) || !point || !grad_score) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    double inv_tol2[GV_MAXD];
+    TRY(ss_prepare(c, tol, inv_tol2));
+    double *gp = grad_point ? grad_point : (double *)c->ss_io.p + GV_MAXD;
+    if (n == 0) { CK(cudaMemsetAsync(gp, 0, sizeof(double) * c->P.d, c->stream)); return VOTE_OK; }
+    launch_softscore(c->P.fam, true, surfaces, n, mask, point, inv_tol2, c->P.nd, grad_score, grad_surfaces,
+                     (double *)c->ss_partial.p, gp, c->stream);
+    CK(cudaGetLastError());
+    return VOTE_OK;
+}
+
+vote_status vote_refine(vote_ctx *c, const double *surfaces, int64_t n, const uint32_t *mask, const double *cell_lo,
+                        const double *cell_hi, const double *tol, int iters, double *point_inout,
+                        double *score_out) {
+    if (!c || n < 0 || (n > 0 && !surfaces) || !cell_lo || !cell_hi || !point_inout || iters < 0) {
+        set_err("invalid arguments");
+        return VOTE_EINVAL;
+    }
+    const int d = c->P.d;
+    for (int j = 0; j < d; ++j)
+        if (!(cell_hi[j] >= cell_lo[j])) { set_err("empty cell in coordinate %d", j); return VOTE_EINVAL; }
+    double inv_tol2[GV_MAXD];
+    TRY(ss_prepare(c, tol, inv_tol2));
+    double *dio = (double *)c->ss_io.p;       // [0, d): point, [d, 2d): outputs, [2 MAXD]: 1.0
+    double host[2 * GV_MAXD + 2];
+    auto eval = [&](const double *pt, bool grad, double *res) -> vote_status {
+        std::memcpy(host, pt, sizeof(double) * d);
+        host[2 * GV_MAXD] = 1.0;
+        CK(cudaMemcpyAsync(dio, host, sizeof(double) * d, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(dio + 2 * GV_MAXD, host + 2 * GV_MAXD, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        launch_softscore(c->P.fam, grad, surfaces, n, mask, dio, inv_tol2, c->P.nd, dio + 2 * GV_MAXD, nullptr,
+                         (double *)c->ss_partial.p, dio + GV_MAXD, c->stream);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(res, dio + GV_MAXD, sizeof(double) * (grad ? d : 1), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return VOTE_OK;
+    };
+    double p[GV_MAXD], q[GV_MAXD], g[GV_MAXD], D[GV_MAXD], S = 0.0, Sq = 0.0;
+    for (int j = 0; j < d; ++j) {
+        p[j] = std::fmin(std::fmax(point_inout[j], cell_lo[j]), cell_hi[j]);
+        D[j] = (cell_hi[j] - cell_lo[j]) * (cell_hi[j] - cell_lo[j]);
+    }
+    if (n > 0) {
+        TRY(eval(p, false, &S));
+        for (int it = 0; it < iters; ++it) {
+            TRY(eval(p, true, g));
+            double gdg = 0.0;
+            for (int j = 0; j < d; ++j) gdg += g[j] * g[j] * D[j];
+            if (!(gdg > 0.0)) break;
+            bool moved = false;
+            for (double t = 1.0 / std::sqrt(gdg); t > 1e-14; t *= 0.5) {
+                for (int j = 0; j < d; ++j) q[j] = std::fmin(std::fmax(p[j] + t * D[j] * g[j], cell_lo[j]), cell_hi[j]);
+                TRY(eval(q, false, &Sq));
+                if (Sq >= S + 1e-4 * t * gdg) {
+                    std::memcpy(p, q, sizeof(double) * d);
+                    S = Sq;
+                    moved = true;
+                    break;
+                }
+            }
+            if (!moved) break;
+        }
+    }
+    std::memcpy(point_inout, p, sizeof(double) * d);
+    if (score_out) *score_out = S;
     return VOTE_OK;
 }
 
@@ -899,6 +1084,12 @@ vote_status vote_get_stats(vote_ctx *c, vote_stats *out) {
 
 void vote_destroy(vote_ctx *c) {
     if (!c) return;
+    for (vote_ctx *w : c->workers) {
+        cudaStream_t ws = w->stream;
+        vote_destroy(w);
+        if (ws) cudaStreamDestroy(ws);
+    }
+    c->workers.clear();
     for (int l = 0; l <= GV_MAXL; ++l) {
         LevelStore &s = c->ls[l];
         for (int j = 0; j < GV_MAXD; ++j) release(c, s.qf[j]);
@@ -908,7 +1099,8 @@ void vote_destroy(vote_ctx *c) {
     DevBuf *bufs[] = {&c->levs_dev, &c->path, &c->scal, &c->alive, &c->geo64, &c->geo32, &c->cnt, &c->passmask,
                       &c->child_idx, &c->cursor, &c->keepflag, &c->recn, &c->bsums, &c->tr_level, &c->tr_key,
                       &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp, &c->alive1, &c->geo64b,
-                      &c->geo32b, &c->cntb, &c->pm2, &c->child_idxb, &c->cursorb};
+                      &c->geo32b, &c->cntb, &c->pm2, &c->child_idxb, &c->cursorb, &c->ss_partial,
+                      &c->ss_io};
     for (DevBuf *b : bufs) release(c, *b);
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < vote_ctx::kEv; ++i)

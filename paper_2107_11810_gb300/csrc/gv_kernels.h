@@ -96,4 +96,12 @@ void launch_path_geo(const Problem &P, const Level *levs_dev, int lam, uint64_t 
 void launch_replay(const Problem &P, const Level *levs_dev, const PathStep *path, int lam, const double *prm,
                    int64_t n, uint32_t *reach, Scalars *sc, cudaStream_t st);
 
+// soft inlier score (gv_softscore.cu): forward writes out[0] = S; backward writes
+// out[0..d) = grad_out * dS/dp and, if grad_prm, grad_out * dS/dparams [P][n].
+// partial: softscore_partial_doubles() doubles of scratch.
+void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uint32_t *mask, const double *p,
+                      const double *inv_tol2, int nd, const double *grad_out, double *grad_prm, double *partial,
+                      double *out, cudaStream_t st);
+int softscore_partial_doubles();
+
 }  // namespace gv

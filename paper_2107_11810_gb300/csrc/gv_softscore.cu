@@ -1,0 +1,187 @@
+// gv_softscore.cu -- soft inlier score S(p) = sum_i w_i exp(-u_i^2 / 2),
+// u_i^2 = sum_j (r_ij / tol_j)^2, r_ij the vertical residual of surface i at p in
+// dependent coordinate j (Eq. 1 in global form), w_i = bit i of the inlier mask.
+// Forward, backward (d S / d p and d S / d surface parameters, recomputing the
+// residuals instead of storing them) and a projected gradient ascent that keeps p
+// inside a cell.  This refines the voting result the way Sec. 4.2 suggests a
+// "more accurate method" take over from the approximate pose.
+//
+// Reductions are deterministic: per-block partial sums in a fixed grid, then one
+// block adds the partials in order.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "gv_kernels.h"
+
+namespace gv {
+
+constexpr int kSsBlocks = 1024;
+constexpr int kSsThreads = 256;
+
+// Residuals r[j], d r / d p (dp[j][d]) and d r / d params (dq[j][P]) of surface i at p.
+template <int FAM> struct SoftFam;
+
+template <> struct SoftFam<FAM_LINE2D> {       // r = b - (y - x m)
+    static constexpr int D = 2, ND = 1, NP = 2;
+    __device__ static void eval(const double *prm, int64_t n, int64_t i, const double *p, double *r, double *dp,
+                                double *dq) {
+        double x = prm[i], y = prm[n + i];
+        r[0] = p[1] - (y - x * p[0]);
+        dp[0] = x; dp[1] = 1.0;
+        dq[0] = p[0]; dq[1] = -1.0;
+    }
+};
+
+template <> struct SoftFam<FAM_PLANE3D_SPH> {  // r = d - q . n(theta, phi)
+    static constexpr int D = 3, ND = 1, NP = 3;
+    __device__ static void eval(const double *prm, int64_t n, int64_t i, const double *p, double *r, double *dp,
+                                double *dq) {
+        double qx = prm[i], qy = prm[n + i], qz = prm[2 * n + i];
+        double st, ct, sp, cp;
+        sincos(p[0], &st, &ct);
+        sincos(p[1], &sp, &cp);
+        double nx = st * cp, ny = st * sp, nz = ct;
+        r[0] = p[2] - (qx * nx + qy * ny + qz * nz);
+        dp[0] = -(qx * ct * cp + qy * ct * sp - qz * st);
+        dp[1] = -(-qx * st * sp + qy * st * cp);
+        dp[2] = 1.0;
+        dq[0] = -nx; dq[1] = -ny; dq[2] = -nz;
+    }
+};
+
+template <> struct SoftFam<FAM_POSE3DOF> {     // r_x = x - (w1 - (a c - b s)), r_y = y - (w2 - (a s + b c))
+    static constexpr int D = 3, ND = 2, NP = 4;
+    __device__ static void eval(const double *prm, int64_t n, int64_t i, const double *p, double *r, double *dp,
+                                double *dq) {
+        double w1 = prm[i], w2 = prm[n + i], a = prm[2 * n + i], b = prm[3 * n + i];
+        double s, c;
+        sincos(p[0], &s, &c);
+        r[0] = p[1] - (w1 - (a * c - b * s));
+        r[1] = p[2] - (w2 - (a * s + b * c));
+        dp[0] = -a * s - b * c; dp[1] = 1.0; dp[2] = 0.0;
+        dp[3] = a * c - b * s;  dp[4] = 0.0; dp[5] = 1.0;
+        dq[0] = -1.0; dq[1] = 0.0; dq[2] = c; dq[3] = -s;
+        dq[4] = 0.0; dq[5] = -1.0; dq[6] = s; dq[7] = c;
+    }
+};
+
+struct SoftArgs {
+    const double *prm;
+    int64_t n;
+    const uint32_t *mask;     // NULL: every weight 1
+    const double *p;          // device [d]
+    double inv_tol2[GV_MAXD]; // 1 / tol_j^2
+    const double *grad_out;   // device [1] (backward)
+    double *grad_prm;         // device [P][n] or NULL (backward)
+    double *partial;          // [kSsBlocks][1 + d]
+};
+
+__device__ __forceinline__ double block_sum(double v, double *sm) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kSsThreads / 32; ++i) t += sm[i];
+    return t;                 // valid in thread 0
+}
+
+template <int FAM, bool BWD>
+__global__ void __launch_bounds__(kSsThreads) k_softscore(SoftArgs a) {
+    using S = SoftFam<FAM>;
+    __shared__ double sm[kSsThreads / 32];
+    double p[S::D];
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) p[j] = a.p[j];
+    double g0 = BWD ? a.grad_out[0] : 0.0;
+    double acc = 0.0, accp[S::D];
+#pragma unroll
+    for (int j = 0; j < S::D; ++j) accp[j] = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        double w = a.mask ? (double)((a.mask[i >> 5] >> (i & 31)) & 1u) : 1.0;
+        double r[S::ND], dp[S::ND * S::D], dq[S::ND * S::NP];
+        S::eval(a.prm, a.n, i, p, r, dp, dq);
+        double u2 = 0.0;
+#pragma unroll
+        for (int j = 0; j < S::ND; ++j) u2 += r[j] * r[j] * a.inv_tol2[j];
+        double k = w * exp(-0.5 * u2);
+        if (!BWD) {
+            acc += k;
+        } else {
+            // dS_i / dr_j = -k r_j / tol_j^2
+            double gq[S::NP];
+#pragma unroll
+            for (int m = 0; m < S::NP; ++m) gq[m] = 0.0;
+#pragma unroll
+            for (int j = 0; j < S::ND; ++j) {
+                double dr = -g0 * k * r[j] * a.inv_tol2[j];
+#pragma unroll
+                for (int q = 0; q < S::D; ++q) accp[q] += dr * dp[j * S::D + q];
+#pragma unroll
+                for (int m = 0; m < S::NP; ++m) gq[m] += dr * dq[j * S::NP + m];
+            }
+            if (a.grad_prm)
+#pragma unroll
+                for (int m = 0; m < S::NP; ++m) a.grad_prm[m * a.n + i] = gq[m];
+        }
+    }
+    if (!BWD) {
+        double t = block_sum(acc, sm);
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = t;
+    } else {
+#pragma unroll
+        for (int q = 0; q < S::D; ++q) {
+            double t = block_sum(accp[q], sm);
+            if (threadIdx.x == 0) a.partial[blockIdx.x * S::D + q] = t;
+        }
+    }
+}
+
+// out[q] = sum over blocks of partial[b * width + q], in block order
+__global__ void k_softscore_final(const double *partial, int nb, int width, double *out) {
+    int q = threadIdx.x;
+    if (q >= width) return;
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += partial[b * width + q];
+    out[q] = t;
+}
+
+static int ss_blocks(int64_t n) {
+    int64_t b = (n + kSsThreads - 1) / kSsThreads;
+    return (int)(b < 1 ? 1 : (b > kSsBlocks ? kSsBlocks : b));
+}
+
+void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uint32_t *mask, const double *p,
+                      const double *inv_tol2, int nd, const double *grad_out, double *grad_prm, double *partial,
+                      double *out, cudaStream_t st) {
+    SoftArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.prm = prm; a.n = n; a.mask = mask; a.p = p; a.grad_out = grad_out; a.grad_prm = grad_prm;
+    a.partial = partial;
+    for (int j = 0; j < nd; ++j) a.inv_tol2[j] = inv_tol2[j];
+    int nb = ss_blocks(n);
+    int d = fam == FAM_LINE2D ? 2 : 3;
+    switch (fam) {
+    case FAM_LINE2D:
+        if (bwd) k_softscore<FAM_LINE2D, true><<<nb, kSsThreads, 0, st>>>(a);
+        else k_softscore<FAM_LINE2D, false><<<nb, kSsThreads, 0, st>>>(a);
+        break;
+    case FAM_PLANE3D_SPH:
+        if (bwd) k_softscore<FAM_PLANE3D_SPH, true><<<nb, kSsThreads, 0, st>>>(a);
+        else k_softscore<FAM_PLANE3D_SPH, false><<<nb, kSsThreads, 0, st>>>(a);
+        break;
+    case FAM_POSE3DOF:
+        if (bwd) k_softscore<FAM_POSE3DOF, true><<<nb, kSsThreads, 0, st>>>(a);
+        else k_softscore<FAM_POSE3DOF, false><<<nb, kSsThreads, 0, st>>>(a);
+        break;
+    }
+    k_softscore_final<<<1, 32, 0, st>>>(partial, nb, bwd ? d : 1, out);
+}
+
+int softscore_partial_doubles() { return kSsBlocks * GV_MAXD; }
+
+}  // namespace gv

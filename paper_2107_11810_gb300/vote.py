@@ -23,14 +23,15 @@ _lib = None
 
 VOTE_OPT_PRECISION, VOTE_OPT_PRUNE, VOTE_OPT_CHUNK_RECORDS = 1, 2, 3
 VOTE_OPT_TRACE_CAP, VOTE_OPT_GROUP, VOTE_OPT_FAULT_ALLOC_AT = 4, 5, 6
-VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING, VOTE_OPT_TWO_LEVEL = 7, 8, 9
+VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING, VOTE_OPT_TWO_LEVEL, VOTE_OPT_BATCH_WORKERS = 7, 8, 9, 10
 KERNEL_CLASSES = ["lift", "cell_geo", "test_count", "test_emit", "children", "replay", "group", "spare"]
 STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
           5: "VOTE_ETIMEOUT", 6: "VOTE_EUNSUPPORTED", 7: "VOTE_EINTERNAL"}
 NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4}
 EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
            "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_get_kernel_times",
-           "vote_get_level_stats", "vote_cell_counts_noalloc",
+           "vote_get_level_stats", "vote_cell_counts_noalloc", "vote_softscore_fwd", "vote_softscore_bwd",
+           "vote_refine", "vote_solve_batched",
            "vote_last_error", "vote_destroy"]
 
 
@@ -72,6 +73,10 @@ def load(path: str | None = None):
             lib.vote_get_kernel_times.argtypes = [P, P, P, P]
             lib.vote_get_level_stats.argtypes = [P, P, P]
             lib.vote_cell_counts_noalloc.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P]
+            lib.vote_softscore_fwd.argtypes = [P, P, i64, P, P, P, P]
+            lib.vote_softscore_bwd.argtypes = [P, P, i64, P, P, P, P, P, P]
+            lib.vote_refine.argtypes = [P, P, i64, P, P, P, P, i32, P, P]
+            lib.vote_solve_batched.argtypes = [P, P, P, i32, P, P, P, P, P]
             lib.vote_last_error.restype = ctypes.c_char_p
             lib.vote_last_error.argtypes = []
             lib.vote_destroy.argtypes = [P]
@@ -114,6 +119,7 @@ class Solver:
         b = np.ascontiguousarray(bounds, dtype=np.float64).reshape(2 * self.d)
         h = ctypes.c_void_p()
         _check(self.lib.vote_create(family, self.d, self.k, _ptr(e), _ptr(b), ctypes.byref(h)))
+        self.eps, self.bounds = e, b
         self.h = h
         self.set_option(VOTE_OPT_PRECISION, precision)
         self.set_option(VOTE_OPT_PRUNE, 1 if prune else 0)
@@ -225,6 +231,52 @@ class Solver:
         _check(self.lib.vote_get_stats(self.h, ctypes.byref(s)))
         return s.as_dict()
 
+    def solve_batched(self, blocks, want_mask: bool = True):
+        """Solve independent problems.  ``blocks``: CUDA float64 tensor holding the
+        problems' [P, n_b] blocks back to back (see pack_batch) and ``offsets``.
+        Returns dict of best_points [B, d], best_leaves, depths [B], masks (CUDA
+        int32 words, problem b at word_offsets[b]), latency_ms [B]."""
+        import torch
+        data, offsets = blocks
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        B = len(offs) - 1
+        ns = np.diff(offs)
+        wo = np.concatenate([[0], np.cumsum((ns + 31) // 32)]).astype(np.int64)
+        bp = np.zeros((max(B, 1), self.d))
+        bl = np.zeros((max(B, 1), self.d), np.int64)
+        dep = np.zeros(max(B, 1), np.int64)
+        lat = np.zeros(max(B, 1))
+        masks = torch.zeros(max(int(wo[-1]), 1), dtype=torch.int32, device=data.device) if want_mask else None
+        _check(self.lib.vote_solve_batched(self.h, _ptr(data), _ptr(offs), B, _ptr(bp), _ptr(bl), _ptr(dep),
+                                           _ptr(masks), _ptr(lat)))
+        return dict(best_points=bp[:B], best_leaves=bl[:B], depths=dep[:B], masks=masks, word_offsets=wo,
+                    latency_ms=lat[:B])
+
+    def refine(self, surfaces, mask, cell_lo, cell_hi, point, tol=None, iters: int = 50):
+        """Projected gradient ascent of the soft inlier score inside a cell; returns
+        (point, score)."""
+        self._check_surfaces(surfaces)
+        n = surfaces.shape[1]
+        lo = np.ascontiguousarray(cell_lo, dtype=np.float64).reshape(self.d)
+        hi = np.ascontiguousarray(cell_hi, dtype=np.float64).reshape(self.d)
+        pt = np.array(point, dtype=np.float64).reshape(self.d)
+        tl = None if tol is None else np.ascontiguousarray(tol, dtype=np.float64).reshape(self.d - self.k)
+        sc = np.zeros(1)
+        _check(self.lib.vote_refine(self.h, _ptr(surfaces), n, _ptr(mask), _ptr(lo), _ptr(hi), _ptr(tl), int(iters),
+                                    _ptr(pt), _ptr(sc)))
+        return pt, float(sc[0])
+
+    def leaf_box(self, leaf):
+        """(lo, hi) of a leaf cell given its integer coordinates."""
+        L, Lj = self.levels()
+        lo = np.zeros(self.d)
+        hi = np.zeros(self.d)
+        for j in range(self.d):
+            w = (self.bounds[2 * j + 1] - self.bounds[2 * j]) / 2.0 ** int(Lj[j])
+            lo[j] = self.bounds[2 * j] + w * int(leaf[j])
+            hi[j] = lo[j] + w
+        return lo, hi
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.vote_destroy(self.h)
@@ -235,6 +287,15 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def pack_batch(param_list):
+    """Concatenate [P, n_b] float64 arrays into the batched layout: a flat array with
+    problem b's [P, n_b] block at element P * offsets[b]; returns (flat, offsets)."""
+    offs = np.concatenate([[0], np.cumsum([p.shape[1] for p in param_list])]).astype(np.int64)
+    flat = np.concatenate([np.ascontiguousarray(p, dtype=np.float64).ravel() for p in param_list]) \
+        if param_list else np.zeros(0)
+    return flat, offs
 
 
 def cell_counts_noalloc(family: int, eps, bounds, surfaces, level: int, coords, reach=None, stream=None):

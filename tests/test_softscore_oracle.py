@@ -1,0 +1,81 @@
+"""Pins of the soft-score oracle (CPU)."""
+import math
+
+import numpy as np
+import torch
+
+from oracle import softscore as ss
+from paper_2107_11810_gb300 import inputs
+
+
+def test_single_line_hand_value():
+    # point (x, y) = (0.5, 0.25); at (m, b) = (0.5, 0.1) the dual-line residual is
+    # b - (y - x m) = 0.1 - 0 = 0.1; with tol 0.1, u = 1 and S = exp(-1/2)
+    prm = torch.tensor([[0.5], [0.25]], dtype=torch.float64)
+    p = torch.tensor([0.5, 0.1], dtype=torch.float64)
+    s = ss.softscore(ss.LINE2D, prm, p, torch.ones(1, dtype=torch.float64), [0.1])
+    assert abs(float(s) - math.exp(-0.5)) < 1e-15
+
+
+def test_single_pose_hand_value():
+    # camera at (10, 20), yaw 0.3; the surface of a point seen at (a, b) = (3, 4)
+    # passes exactly through the camera position at that yaw: r = 0, S = 1;
+    # moving x by tol gives u = 1
+    yaw, cx, cy, a, b = 0.3, 10.0, 20.0, 3.0, 4.0
+    w1 = cx + (a * math.cos(yaw) - b * math.sin(yaw))
+    w2 = cy + (a * math.sin(yaw) + b * math.cos(yaw))
+    prm = torch.tensor([[w1], [w2], [a], [b]], dtype=torch.float64)
+    w = torch.ones(1, dtype=torch.float64)
+    s0 = ss.softscore(ss.POSE3DOF, prm, torch.tensor([yaw, cx, cy], dtype=torch.float64), w, [0.25, 0.25])
+    s1 = ss.softscore(ss.POSE3DOF, prm, torch.tensor([yaw, cx + 0.25, cy], dtype=torch.float64), w, [0.25, 0.25])
+    assert abs(float(s0) - 1.0) < 1e-12
+    assert abs(float(s1) - math.exp(-0.5)) < 1e-12
+
+
+def test_exact_inliers_sum_of_weights_and_plane_double_cover():
+    rng = np.random.default_rng(3)
+    th, ph = 0.7, 2.1
+    n = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    d = 0.3
+    # points exactly on the plane n . q = d
+    q = rng.uniform(-1, 1, size=(40, 3))
+    q -= np.outer(q @ n - d, n)
+    prm = torch.from_numpy(q.T.copy())
+    w = torch.from_numpy(rng.integers(0, 2, 40).astype(np.float64))
+    p = torch.tensor([th, ph, d], dtype=torch.float64)
+    s = ss.softscore(ss.PLANE3D_SPH, prm, p, w, [0.01])
+    assert abs(float(s) - float(w.sum())) < 1e-9
+    # (theta, phi, d) and (pi - theta, phi + pi, -d) are the same plane
+    q2 = rng.uniform(0, 1, size=(30, 3))
+    prm2 = torch.from_numpy(q2.T.copy())
+    w2 = torch.ones(30, dtype=torch.float64)
+    a = ss.softscore(ss.PLANE3D_SPH, prm2, p, w2, [0.2])
+    b = ss.softscore(ss.PLANE3D_SPH, prm2, torch.tensor([math.pi - th, ph + math.pi, -d], dtype=torch.float64), w2,
+                     [0.2])
+    assert abs(float(a) - float(b)) < 1e-12
+
+
+def test_oracle_gradients_match_central_differences():
+    for fam, mk, tol in [(ss.LINE2D, lambda: inputs.line2d(n=200, seed=4), [0.05]),
+                         (ss.PLANE3D_SPH, lambda: inputs.plane3d(n=200, seed=5), [0.05]),
+                         (ss.POSE3DOF, lambda: inputs.pose3dof(n=200, seed=6), [2.0, 2.0])]:
+        prob = mk()
+        prm = torch.from_numpy(prob.params.copy()).requires_grad_(True)
+        p = torch.tensor(prob.truth, dtype=torch.float64) + 0.003
+        p.requires_grad_(True)
+        w = torch.ones(prob.n, dtype=torch.float64)
+        s = ss.softscore(fam, prm, p, w, tol)
+        gp, gq = torch.autograd.grad(s, [p, prm])
+        h = 1e-6
+        for j in range(p.numel()):
+            e = torch.zeros_like(p)
+            e[j] = h
+            with torch.no_grad():
+                fd = (ss.softscore(fam, prm, p + e, w, tol) - ss.softscore(fam, prm, p - e, w, tol)) / (2 * h)
+            assert abs(float(fd) - float(gp[j])) <= 1e-6 * max(1.0, abs(float(fd)))
+        for (m, i) in [(0, 0), (prm.shape[0] - 1, 7)]:
+            e = torch.zeros_like(prm)
+            e[m, i] = h
+            with torch.no_grad():
+                fd = (ss.softscore(fam, prm + e, p, w, tol) - ss.softscore(fam, prm - e, p, w, tol)) / (2 * h)
+            assert abs(float(fd) - float(gq[m, i])) <= 1e-6 * max(1.0, abs(float(fd)))
