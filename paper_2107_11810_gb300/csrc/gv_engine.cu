@@ -96,8 +96,12 @@ struct vote_ctx {
     DevBuf tr_level, tr_key, tr_ub, tr_lb, surf_tmp, mask_tmp;
     DevBuf alive1, geo64b, geo32b, cntb, pm2, child_idxb, cursorb;
     DevBuf ss_partial, ss_io;  // soft score: block partials; point [d] + outputs [d] + grad_out [1]
+    DevBuf g_table, g_owner, g_newpos, g_ccount, g_ccur, g_qf[GV_MAXD], g_qt[GV_MAXT], g_mult, g_cell;
+    int64_t grouped_away = 0;  // records merged away by grouping in the last solve
     Scalars *h_sc = nullptr;   // pinned mirror of the device scalars
     uint64_t *h_tmp = nullptr; // pinned slot for single values
+    // device slot for single values: 64 bytes after the scalars block
+    void *h_tmp_dev() { return (char *)scal.p + ((sizeof(Scalars) + 63) / 64) * 64; }
     int64_t trace_written = 0;
     bool trace_overflow = false;
     vote_stats stats;
@@ -489,6 +493,47 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     CK(cudaMemsetAsync(c->cursor.p, 0, nch * 4, c->stream));
     CK(cudaMemsetAsync(&dsc(c)->n_cells, 0, 16, c->stream));
 
+    RecView in = rec_view(c, l);
+    int64_t g_r0 = r0, g_r1 = r1;
+    if (c->group && nr > 1) {
+        // canonization's grouping: merge records with equal (cell, q_f, q_t)
+        size_t cap = 1;
+        while (cap < (size_t)nr * 2) cap <<= 1;
+        TRY(ensure(c, c->g_table, cap * 4));
+        TRY(ensure(c, c->g_owner, (size_t)nr * 4));
+        TRY(ensure(c, c->g_newpos, (size_t)nr * 4));
+        TRY(ensure(c, c->g_ccount, (size_t)nc * 4));
+        TRY(ensure(c, c->g_ccur, (size_t)nc * 4));
+        for (int j = 0; j < P.nd; ++j) TRY(ensure(c, c->g_qf[j], (size_t)nr * 4));
+        for (int m = 0; m < P.le; ++m) TRY(ensure(c, c->g_qt[m], (size_t)nr * 4));
+        TRY(ensure(c, c->g_mult, (size_t)nr * 4));
+        TRY(ensure(c, c->g_cell, (size_t)nr * 4));
+        CK(cudaMemsetAsync(c->g_table.p, 0, cap * 4, c->stream));
+        CK(cudaMemsetAsync(c->g_ccount.p, 0, (size_t)nc * 4, c->stream));
+        CK(cudaMemsetAsync(c->g_ccur.p, 0, (size_t)nc * 4, c->stream));
+        RecView gv;
+        std::memset(&gv, 0, sizeof(gv));
+        for (int j = 0; j < P.nd; ++j) gv.qf[j] = (int32_t *)c->g_qf[j].p;
+        for (int m = 0; m < P.le; ++m) gv.qt[m] = (int32_t *)c->g_qt[m].p;
+        gv.mult = (uint32_t *)c->g_mult.p;
+        gv.cell = (uint32_t *)c->g_cell.p;
+        ev_mark(c, -1);
+        launch_group(P, in, r0, nr, c0, nc, (uint32_t *)c->g_table.p, (uint32_t)(cap - 1), (uint32_t *)c->g_owner.p,
+                     (uint32_t *)c->g_ccount.p, (uint32_t *)c->g_ccur.p, (uint32_t *)c->g_newpos.p,
+                     (unsigned long long *)c->h_tmp_dev(), gv, dsc(c), c->stream);
+        ev_mark(c, VOTE_K_GROUP);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(c->h_tmp, c->h_tmp_dev(), 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        int64_t ng = (int64_t)*c->h_tmp;
+        c->stats.launches += 4;
+        c->kbytes[VOTE_K_GROUP] += (double)nr * (4 * (P.nd + P.le + 2)) * 2;
+        c->grouped_away += nr - ng;
+        in = gv;
+        g_r0 = 0;
+        g_r1 = ng;
+        if (nr > 0) TRY(ensure(c, c->passmask, (size_t)ng));
+    }
     Chunk ch;
     std::memset(&ch, 0, sizeof(ch));
     ch.P = P;
@@ -496,9 +541,9 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     ch.cells = cell_view(c, l);
     ch.c0 = c0;
     ch.nc = nc;
-    ch.in = rec_view(c, l);
-    ch.r0 = r0;
-    ch.r1 = r1;
+    ch.in = in;
+    ch.r0 = g_r0;
+    ch.r1 = g_r1;
     ch.alive = (uint8_t *)c->alive.p;
     ch.geo64 = (double *)c->geo64.p;
     ch.geo32 = (float *)c->geo32.p;
@@ -522,6 +567,7 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     ch.precision = c->precision;
 
     int rec_bytes = 4 * (P.nd + P.le + 2);
+    nr = g_r1 - g_r0;                 // records actually tested (after grouping)
     ev_mark(c, -1);
     launch_cell_geo(ch, c->stream);
     ev_mark(c, VOTE_K_CELL_GEO);
@@ -593,6 +639,7 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
     const Problem &P = c->P;
     std::memset(&c->stats, 0, sizeof(c->stats));
     for (int l = 0; l < GV_MAXL; ++l) c->lv_cells[l] = c->lv_recs[l] = 0;
+    c->grouped_away = 0;
     c->stats.levels = P.L;
     if (n < 0 || !best_point || !depth || (n > 0 && !surfaces)) {
         set_err("invalid arguments");
@@ -723,7 +770,7 @@ vote_status vote_create(int family, int d, int k, const double *eps, const doubl
         delete c;
         return VOTE_ECUDA;
     }
-    s = ensure(c, c->scal, sizeof(Scalars));
+    s = ensure(c, c->scal, ((sizeof(Scalars) + 63) / 64) * 64 + 64);
     if (s == VOTE_OK) s = ensure(c, c->levs_dev, sizeof(Level) * (c->P.L > 0 ? c->P.L : 1));
     if (s == VOTE_OK) s = ensure(c, c->path, sizeof(PathStep) * (c->P.L > 0 ? c->P.L : 1));
     if (s == VOTE_OK && c->P.L > 0) {
@@ -1100,8 +1147,11 @@ void vote_destroy(vote_ctx *c) {
                       &c->child_idx, &c->cursor, &c->keepflag, &c->recn, &c->bsums, &c->tr_level, &c->tr_key,
                       &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp, &c->alive1, &c->geo64b,
                       &c->geo32b, &c->cntb, &c->pm2, &c->child_idxb, &c->cursorb, &c->ss_partial,
-                      &c->ss_io};
+                      &c->ss_io, &c->g_table, &c->g_owner, &c->g_newpos, &c->g_ccount, &c->g_ccur,
+                      &c->g_mult, &c->g_cell};
     for (DevBuf *b : bufs) release(c, *b);
+    for (int j = 0; j < GV_MAXD; ++j) release(c, c->g_qf[j]);
+    for (int m = 0; m < GV_MAXT; ++m) release(c, c->g_qt[m]);
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < vote_ctx::kEv; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);

@@ -1083,6 +1083,101 @@ __global__ void __launch_bounds__(256) k_replay(Problem P, const Level *__restri
 }
 
 // ---------------------------------------------------------------------------
+// A3 grouping: merge records of a chunk with equal (cell, q_f, q_t) (the
+// canonization's grouping, Sec. 3.2).  An open-addressing table of record
+// indices: each record claims its home slot by atomicCAS of (its index + 1); a
+// record that finds the slot taken compares its full key with the owner's
+// (immutable) record and either adopts it or probes on.  Exact: different keys
+// are never merged.  Canonical records are then laid out per cell (scan of
+// per-cell counts) and their multiplicities summed with integer atomics, so the
+// grouped records are deterministic up to their order inside a cell.
+// ---------------------------------------------------------------------------
+template <int ND, int LE>
+__device__ __forceinline__ bool same_key(const RecView &in, int64_t a, int64_t b) {
+    if (in.cell[a] != in.cell[b]) return false;
+#pragma unroll
+    for (int j = 0; j < ND; ++j)
+        if (in.qf[j][a] != in.qf[j][b]) return false;
+#pragma unroll
+    for (int m = 0; m < LE; ++m)
+        if (in.qt[m][a] != in.qt[m][b]) return false;
+    return true;
+}
+
+template <int ND, int LE>
+__device__ __forceinline__ uint64_t key_hash(const RecView &in, int64_t r) {
+    uint64_t h = 0x9E3779B97F4A7C15ull ^ in.cell[r];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) h = (h ^ (uint32_t)in.qf[j][r]) * 0xff51afd7ed558ccdull;
+#pragma unroll
+    for (int m = 0; m < LE; ++m) h = (h ^ (uint32_t)in.qt[m][r]) * 0xc4ceb9fe1a85ec53ull;
+    return h ^ (h >> 29);
+}
+
+template <int FAM>
+__global__ void k_group_insert(RecView in, int64_t r0, int64_t nr, int64_t c0, uint32_t *table, uint32_t tmask,
+                               uint32_t *owner, uint32_t *ccount, Scalars *sc) {
+    using F = Fam<FAM>;
+    int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= nr) return;
+    int64_t r = r0 + x;
+    uint32_t slot = (uint32_t)key_hash<F::ND, F::LE>(in, r) & tmask;
+    for (uint32_t probe = 0; probe <= tmask; ++probe) {
+        uint32_t prev = atomicCAS(&table[slot], 0u, (uint32_t)(x + 1));
+        if (prev == 0u) {                                   // new canonical record
+            owner[x] = (uint32_t)x;
+            atomicAdd(&ccount[in.cell[r] - c0], 1u);
+            return;
+        }
+        if (same_key<F::ND, F::LE>(in, r, r0 + (int64_t)(prev - 1))) {
+            owner[x] = prev - 1;
+            return;
+        }
+        slot = (slot + 1) & tmask;
+    }
+    atomicOr(&sc->err, 4u);                                 // table full (cannot happen at load <= 1/2)
+    owner[x] = (uint32_t)x;
+}
+
+// exclusive scan of n u32 values in place (one block of 256 threads); *total = sum
+__global__ void __launch_bounds__(256) k_scan_u32(uint32_t *a, int64_t n, unsigned long long *total) {
+    unsigned long long carry = 0;
+    for (int64_t base = 0; base < n; base += 256) {
+        int64_t i = base + threadIdx.x;
+        unsigned long long v = i < n ? a[i] : 0u, t;
+        unsigned long long e = block_excl_scan(v, &t);
+        if (i < n) a[i] = (uint32_t)(carry + e);
+        carry += t;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <int FAM>
+__global__ void k_group_place(RecView in, int64_t r0, int64_t nr, int64_t c0, const uint32_t *owner,
+                              const uint32_t *coff, uint32_t *ccur, uint32_t *newpos, RecView out) {
+    using F = Fam<FAM>;
+    int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= nr || owner[x] != (uint32_t)x) return;
+    int64_t r = r0 + x;
+    uint32_t cl = in.cell[r] - (uint32_t)c0;
+    uint32_t pos = coff[cl] + atomicAdd(&ccur[cl], 1u);
+    newpos[x] = pos;
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) out.qf[j][pos] = in.qf[j][r];
+#pragma unroll
+    for (int m = 0; m < F::LE; ++m) out.qt[m][pos] = in.qt[m][r];
+    out.cell[pos] = in.cell[r];
+    out.mult[pos] = 0u;
+}
+
+__global__ void k_group_mult(RecView in, int64_t r0, int64_t nr, const uint32_t *owner, const uint32_t *newpos,
+                             RecView out) {
+    int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (x >= nr) return;
+    atomicAdd(&out.mult[newpos[owner[x]]], in.mult[r0 + x]);
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -1155,6 +1250,17 @@ void launch_child_alloc(const Chunk &c, uint32_t *keepflag, uint32_t *recn, unsi
     k_scan_sums<<<1, 256, 0, st>>>(ba, bb, (int)nb, c.sc);
     if (ns == 4) k_child_write<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else k_child_write<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+}
+
+void launch_group(const Problem &P, RecView in, int64_t r0, int64_t nr, int64_t c0, int nc, uint32_t *table,
+                  uint32_t tmask, uint32_t *owner, uint32_t *ccount, uint32_t *ccur, uint32_t *newpos,
+                  unsigned long long *total, RecView out, Scalars *sc, cudaStream_t st) {
+    if (nr <= 0) return;
+    unsigned g = blocks_for(nr, 256);
+    GV_DISPATCH(P.fam, (k_group_insert<FAMV><<<g, 256, 0, st>>>(in, r0, nr, c0, table, tmask, owner, ccount, sc)));
+    k_scan_u32<<<1, 256, 0, st>>>(ccount, nc, total);
+    GV_DISPATCH(P.fam, (k_group_place<FAMV><<<g, 256, 0, st>>>(in, r0, nr, c0, owner, ccount, ccur, newpos, out)));
+    k_group_mult<<<g, 256, 0, st>>>(in, r0, nr, owner, newpos, out);
 }
 
 void launch_path_geo(const Problem &P, const Level *levs_dev, int lam, uint64_t key, PathStep *path,

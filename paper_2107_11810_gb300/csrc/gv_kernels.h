@@ -96,6 +96,13 @@ void launch_path_geo(const Problem &P, const Level *levs_dev, int lam, uint64_t 
 void launch_replay(const Problem &P, const Level *levs_dev, const PathStep *path, int lam, const double *prm,
                    int64_t n, uint32_t *reach, Scalars *sc, cudaStream_t st);
 
+// grouping of a chunk's records [r0, r0 + nr) (cells [c0, c0 + nc)) into out:
+// table [tmask + 1] zeroed; ccount, ccur [nc] zeroed; owner, newpos [nr];
+// *total = number of canonical records
+void launch_group(const Problem &P, RecView in, int64_t r0, int64_t nr, int64_t c0, int nc, uint32_t *table,
+                  uint32_t tmask, uint32_t *owner, uint32_t *ccount, uint32_t *ccur, uint32_t *newpos,
+                  unsigned long long *total, RecView out, Scalars *sc, cudaStream_t st);
+
 // soft inlier score (gv_softscore.cu): forward writes out[0] = S; backward writes
 // out[0..d) = grad_out * dS/dp and, if grad_prm, grad_out * dS/dparams [P][n].
 // partial: softscore_partial_doubles() doubles of scratch.

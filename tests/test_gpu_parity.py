@@ -164,6 +164,26 @@ def test_two_level_trace_equals_oracle_without_pruning():
     assert dg == do
 
 
+@pytest.mark.parametrize("family", FAMS)
+@pytest.mark.parametrize("two_level", [0.0, 1e-9])
+def test_grouping_parity_and_merging(family, two_level):
+    # grouping merges equal canonical records; results must not change
+    v = vote_mod()
+    p = small(family, 2500, 15)
+    params = np.concatenate([p.params, p.params[:, :700], p.params[:, :300]], axis=1)   # duplicates merge
+    o = oracle.solve(p.family, p.eps, p.bounds, params)
+    s0 = v.Solver(p.family, p.eps, p.bounds, two_level=two_level, chunk_records=4000)
+    s1 = v.Solver(p.family, p.eps, p.bounds, two_level=two_level, chunk_records=4000)
+    s1.set_option(v.VOTE_OPT_GROUP, 1)
+    t = torch.from_numpy(np.ascontiguousarray(params)).cuda()
+    r0, r1 = s0.solve(t), s1.solve(t)
+    for r in (r0, r1):
+        r["mask"] = v.mask_words_to_numpy(r["mask"])
+        assert_same(r, o, params.shape[1])
+    assert s1.stats()["records"] < s0.stats()["records"]
+    assert s1.stats()["tests"] < s0.stats()["tests"]
+
+
 @pytest.mark.parametrize("chunk", [1, 7, 1000])
 def test_chunking_does_not_change_results(chunk):
     p = small(inputs.POSE3DOF, 3000, 8)
