@@ -38,6 +38,9 @@ WORKLOADS = {
                           "eps 0.25 m / 0.5 deg, (yaw,x,y) space"),
     "line2d_n1e4": dict(make=lambda: inputs.line2d(), desc="2D line fitting, 1e4 points, 10% inliers, eps 0.01, "
                         "(m,b) space"),
+    "pose3dof_batch256": dict(make=lambda: inputs.pose3dof_batch(), batched=True,
+                              desc="256 independent 3DoF problems, n log-uniform in [1e3, 1e6], inlier ratio "
+                                   "U[0.5%, 5%]; one vote_solve_batched call per step"),
 }
 # FP32-pipe instructions per (child cell, canonical surface) test, counted from
 # the formulas of each family's residual and comparisons
@@ -179,6 +182,58 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, rank, world, w):
+    """Batched workload: every rank solves its greedy share of the problems with one
+    vote_solve_batched call per step (no collective on the data path)."""
+    import torch
+    from paper_2107_11810_gb300 import shard, vote
+    probs = w["make"]()
+    mine = shard.partition([p.n for p in probs], world)[rank]
+    local = [probs[i] for i in mine]
+    p0 = probs[0]
+    s = vote.Solver(p0.family, p0.eps, p0.bounds, precision=args.precision,
+                    stream=torch.cuda.current_stream())
+    flat, offs = vote.pack_batch([p.params for p in local])
+    data = torch.from_numpy(flat).cuda()
+    for _ in range(args.warmup):
+        res = s.solve_batched((data, offs))
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    times, lats = [], []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = s.solve_batched((data, offs))
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            lats.extend(res["latency_ms"].tolist())
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    pinned = torch.from_numpy(flat).pin_memory()
+    t0 = time.perf_counter()
+    r2 = s.solve_batched((pinned.cuda(non_blocking=True), offs))
+    words = torch.empty(r2["masks"].numel(), dtype=torch.int32).copy_(r2["masks"])
+    e2e_t = time.perf_counter() - t0
+    out = dict(metric="solved problems/sec (batched 3DoF voting, 256 problems)", value=len(probs) * args.steps / total,
+               unit="problems/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+               ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="strong", vs_baseline=None,
+               dtype="f32+f64" if args.precision == 1 else "f64", data="synthetic",
+               config=dict(workload=args.workload, desc=w["desc"], problems=len(probs),
+                           total_n=int(sum(p.n for p in probs)), l2="inputs and working set larger than L2"),
+               latency_ms=dict(p50=float(np.percentile(lats, 50)), p99=float(np.percentile(lats, 99))),
+               gpu_launches=None, clocks=clk.summary(),
+               e2e=dict(value=len(local) / e2e_t, unit="problems/s", h2d_bytes_per_step=int(flat.nbytes),
+                        d2h_bytes_per_step=int(words.numel() * 4)))
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +266,12 @@ def main():
     if world > 1:
         dist.barrier()
     w = WORKLOADS[args.workload]
+    if w.get("batched"):
+        run_batched(args, rank, world, w)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     p = w["make"]()
     stream = torch.cuda.current_stream()
     s = vote.Solver(p.family, p.eps, p.bounds, precision=args.precision, stream=stream,
