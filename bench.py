@@ -115,9 +115,11 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """Per-launch DRAM traffic of a kernel from the committed ncu summary, valid only
-    while the kernel sources are unchanged since the capture."""
+def recorded_traffic(kernel: str, family: str, algorithmic_bytes_per_launch: float):
+    """DRAM traffic per launch of a kernel: the ratio of ncu's dram bytes (read + write)
+    to the launch's algorithmic bytes, measured on a smaller case of the same kernel
+    and committed in profiles/ncu_traffic.txt, times this run's algorithmic bytes per
+    launch.  None once the kernel sources differ from the ones captured."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -125,8 +127,8 @@ def recorded_traffic(kernel: str, workload: str):
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and not line.startswith("#") and parts[0] == kh and parts[1] == kernel \
-                and parts[2] == workload:
-            return float(parts[3])
+                and parts[2] == family:
+            return float(parts[3]) * algorithmic_bytes_per_launch
     return None
 
 
@@ -322,13 +324,20 @@ def main():
         roof = dict(bound="alu", achieved=achieved, peak=alu_peak, unit="TFP32-instr/s",
                     frac=achieved / alu_peak, kernel="k_test<count>",
                     peak_src="152 SMs x 128 FP32 lanes x max SM clock (instructions/s, no FMA doubling)",
-                    traffic=recorded_traffic("k_test_count", args.workload), bytes_per_launch=by / max(nl, 1))
+                    traffic=recorded_traffic("k_test_count", inputs.FAMILY_NAMES[p.family], by / max(nl, 1)),
+                    bytes_per_launch=by / max(nl, 1))
     else:
         achieved = by / max(nl, 1) / avg_s / 1e9
         roof = dict(bound="hbm", achieved=achieved, peak=pk["hbm_gbs"], unit="GB/s",
                     frac=achieved / pk["hbm_gbs"], kernel=f"k_test<{dom[5:]}>", peak_src=pk["src"],
-                    traffic=recorded_traffic("k_" + dom, args.workload), bytes_per_launch=by / max(nl, 1))
+                    traffic=recorded_traffic("k_" + dom, inputs.FAMILY_NAMES[p.family], by / max(nl, 1)),
+                    bytes_per_launch=by / max(nl, 1))
     roof["share_of_step"] = kt[dom][0] / 1000.0 / total * world
+    if kt["test_emit"][1]:
+        e_ms, e_nl, e_by = kt["test_emit"]
+        roof["emit_kernel"] = dict(bound="hbm", achieved=e_by / (e_ms / 1000.0) / 1e9, peak=pk["hbm_gbs"],
+                                   unit="GB/s", frac=e_by / (e_ms / 1000.0) / 1e9 / pk["hbm_gbs"],
+                                   share_of_step=e_ms / 1000.0 / total * world)
     # end to end through the public API with host buffers
     pinned = torch.from_numpy(p.params).pin_memory()
     e2e_times = []

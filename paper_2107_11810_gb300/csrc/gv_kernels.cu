@@ -339,30 +339,30 @@ __device__ __forceinline__ void eval_record(const Problem &P, const Level &lev, 
 #pragma unroll
             for (int s = fs; s < NS; s += NF) {
                 if (s & ~smask) continue;
-                int ub_fail = 0, ub_unsure = 0, lb_fail = 0, lb_unsure = 0;
+                // pass bits from the signs of |f'| - R; a slot is uncertain when a
+                // margin is within the screen's error bound (the UB test's, or the
+                // LB test's when the UB test passes)
+                bool ub = true, lb = true, bu = false, bl = false;
 #pragma unroll
                 for (int j = 0; j < F::ND; ++j) {
                     float a = fabsf(pr[j] - dep_shift32<FAM>(lev, j, s));
                     float du = a - st.R32[j], dl = a - lev.rlbf[j];
-                    ub_fail |= du > st.Eub[j];
-                    ub_unsure |= !(du < -st.Eub[j]);
-                    lb_fail |= dl > st.Elb[j];
-                    lb_unsure |= !(dl < -st.Elb[j]);
+                    ub &= du < 0.0f;
+                    lb &= dl < 0.0f;
+                    bu |= fabsf(du) <= st.Eub[j];
+                    bl |= fabsf(dl) <= st.Elb[j];
                 }
-                if (!ub_fail) {
-                    if (!ub_unsure && (lb_fail || !lb_unsure)) {
-                        ubm |= 1u << s;
-                        lbm |= (lb_fail ? 0u : 1u) << s;
-                    } else {
-                        unsure |= 1u << s;
-                    }
-                }
+                ubm |= (unsigned)ub << s;
+                lbm |= (unsigned)(ub & lb) << s;
+                unsure |= (unsigned)(bu | (ub & bl)) << s;
             }
         }
     }
     if (PREC == 1 && unsure) {
         // the FP32 screen could not decide these children: exact FP64 test (one
         // copy of the code, not unrolled)
+        ubm &= ~unsure;
+        lbm &= ~unsure;
         st.need64(P, lev);
 #pragma unroll 1
         for (unsigned u = unsure; u; u &= u - 1) {
@@ -380,6 +380,35 @@ __device__ __forceinline__ void eval_record(const Problem &P, const Level &lev, 
             ubm |= (unsigned)ub << s;
             lbm |= (unsigned)lb << s;
         }
+    }
+}
+
+// Exact FP64 snap of one child residual, out of line: the FP32 screen needs it
+// rarely, and one shared copy keeps the emit kernels' instruction footprint small.
+// Everything is passed by value (no reference to kernel parameters).
+struct Snap64In {
+    int32_t qf[2], qt[3];
+    double sf[2], st[3], inv[2], sh[2];
+    const double *g64;   // basis changes of the child ([NB] doubles)
+};
+
+template <int FAM>
+__device__ __noinline__ void snap64(Snap64In a, int32_t *qn, Scalars *sc) {
+    using F = Fam<FAM>;
+    double f[2], t[3], pr[2];
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) f[j] = dmul((double)a.qf[j], a.sf[j]);
+#pragma unroll
+    for (int m = 0; m < F::LE; ++m) t[m] = dmul((double)a.qt[m], a.st[m]);
+    F::partial64(f, t, a.g64, pr);
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) {
+        double q = rint(dmul(dsub(pr[j], a.sh[j]), a.inv[j]));
+        if (!(fabs(q) < 1073741824.0)) {
+            atomicOr(&sc->err, 2u);
+            q = 0.0;
+        }
+        qn[j] = (int32_t)q;
     }
 }
 
@@ -407,18 +436,21 @@ __device__ __forceinline__ void child_qf(const Problem &P, const Level &lev, Rec
         if (!done) ++nrechk;
     }
     if (!done) {
-        st.need64(P, lev);
-        double pr[F::ND];
-        F::partial64(st.f64, st.t64, g64 + fs * F::NB, pr);
+        Snap64In a;
 #pragma unroll
         for (int j = 0; j < F::ND; ++j) {
-            double q = rint(dmul(dsub(pr[j], dep_shift64<FAM>(lev, j, s)), P.inv_s_f[j]));
-            if (!(fabs(q) < 1073741824.0)) {
-                atomicOr(&sc->err, 2u);
-                q = 0.0;
-            }
-            qn[j] = (int32_t)q;
+            a.qf[j] = st.qf[j];
+            a.sf[j] = P.s_f[j];
+            a.inv[j] = P.inv_s_f[j];
+            a.sh[j] = dep_shift64<FAM>(lev, j, s);
         }
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) {
+            a.qt[m] = st.qt[m];
+            a.st[m] = lev.s_t[m];
+        }
+        a.g64 = g64 + fs * F::NB;
+        snap64<FAM>(a, qn, sc);
     }
 }
 

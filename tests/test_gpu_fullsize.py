@@ -1,0 +1,86 @@
+"""Full-size workloads in the launch configuration bench.py times.
+
+- 3DoF camera voting, 1e6 matches: the oracle solves it completely; bit-exact.
+- 3D plane fitting, 1e6 points: the oracle cannot run the whole search (~1e13
+  tests), so sampled outputs it can compute one by one are compared: the best
+  leaf's count and inlier set by replaying every surface from the root, and
+  random cells at several levels; plus the planted-plane lower bound.
+- Batched 3DoF: the first problems completely, every problem's best leaf by replay.
+"""
+import numpy as np
+import pytest
+
+import brute
+import oracle
+from paper_2107_11810_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_11810_gb300 import build
+    build.build()
+
+
+def test_pose3dof_1e6_bit_exact_against_the_oracle():
+    from paper_2107_11810_gb300 import vote
+    p = inputs.pose3dof()
+    s = vote.Solver(p.family, p.eps, p.bounds, stream=torch.cuda.current_stream())
+    r = s.solve(torch.from_numpy(p.params).cuda())
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    assert r["depth"] == o["depth"]
+    assert np.array_equal(r["best_leaf"], o["best_leaf"])
+    assert np.array_equal(r["best_point"], o["best_point"])
+    assert np.array_equal(vote.mask_words_to_numpy(r["mask"]), o["mask"])
+
+
+def test_plane3d_1e6_sampled_outputs_equal_the_oracle():
+    from paper_2107_11810_gb300 import vote
+    p = inputs.plane3d()
+    s = vote.Solver(p.family, p.eps, p.bounds, stream=torch.cuda.current_stream())   # bench configuration
+    t = torch.from_numpy(p.params).cuda()
+    r = s.solve(t)
+    L, Lj = s.levels()
+    # the best leaf: count and inlier set by replay of every surface (oracle)
+    ub, lb, reach = oracle.cell_counts(p.family, p.eps, p.bounds, p.params, L, r["best_leaf"], want_reach=True)
+    assert ub == r["depth"]
+    assert np.array_equal(vote.mask_words_to_numpy(r["mask"]), reach)
+    lv = oracle.levels(p.family, p.eps, p.bounds)
+    W = p.bounds[1::2] - p.bounds[0::2]
+    assert np.array_equal(r["best_point"], p.bounds[0::2] + (2 * r["best_leaf"] + 1) * (W / 2.0 ** (lv["Lj"] + 1)))
+    # planted plane: the reported depth is at least the depth at the truth
+    assert r["depth"] >= brute.depth(p.family, p.params, p.eps[2:], p.truth[None])[0]
+    # random cells at several levels: GPU replay == oracle replay
+    rng = np.random.default_rng(7)
+    for level in (1, 4, 8, L):
+        coords = [int(rng.integers(0, 2 ** min(level, int(Lj[j])))) for j in range(3)]
+        assert s.cell_counts(t, level, coords) == oracle.cell_counts(p.family, p.eps, p.bounds, p.params, level,
+                                                                     coords)
+
+
+def test_batched_workload_sampled_outputs_equal_the_oracle():
+    from paper_2107_11810_gb300 import vote
+    probs = inputs.pose3dof_batch()
+    p0 = probs[0]
+    s = vote.Solver(p0.family, p0.eps, p0.bounds)
+    flat, offs = vote.pack_batch([p.params for p in probs])
+    res = s.solve_batched((torch.from_numpy(flat).cuda(), offs))
+    masks = vote.mask_words_to_numpy(res["masks"])
+    small = sorted(range(len(probs)), key=lambda i: probs[i].n)[:6]
+    for b in small:                                   # complete solves of the smallest problems
+        p = probs[b]
+        o = oracle.solve(p.family, p.eps, p.bounds, p.params)
+        assert res["depths"][b] == o["depth"]
+        assert np.array_equal(res["best_leaves"][b], o["best_leaf"])
+    for b in range(0, len(probs), 32):               # best leaf of every 32nd problem by replay
+        p = probs[b]
+        L = oracle.levels(p.family, p.eps, p.bounds)["L"]
+        ub, _, reach = oracle.cell_counts(p.family, p.eps, p.bounds, p.params, L, res["best_leaves"][b],
+                                          want_reach=True)
+        assert ub == res["depths"][b]
+        w0 = res["word_offsets"][b]
+        assert np.array_equal(masks[w0:w0 + (p.n + 31) // 32], reach)
