@@ -57,6 +57,36 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _declare(lib):
+    P = ctypes.c_void_p
+    i64, i32 = ctypes.c_int64, ctypes.c_int
+    lib.gvo_vsin.restype = ctypes.c_double
+    lib.gvo_vsin.argtypes = [ctypes.c_double]
+    lib.gvo_vcos.restype = ctypes.c_double
+    lib.gvo_vcos.argtypes = [ctypes.c_double]
+    lib.gvo_levels.restype = i32
+    lib.gvo_levels.argtypes = [i32, i32, i32, P, P, P, P, P, P, P]
+    lib.gvo_root_records.restype = i32
+    lib.gvo_root_records.argtypes = [i32, i32, i32, P, P, P, i64, P, P]
+    lib.gvo_solve.restype = i32
+    lib.gvo_solve.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P, i64, P, P, P, P, P, P]
+    lib.gvo_cell_counts.restype = i32
+    lib.gvo_cell_counts.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P]
+    return lib
+
+
+def load_variant(source: str, tag: str):
+    """Compile a modified copy of the oracle source (used by the mutation tests to
+    check that the pins catch planted mistakes) and return the loaded library."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src = os.path.join(_BUILD, f"variant_{tag}.c")
+    lib = os.path.join(_BUILD, f"libgvoracle_{tag}.so")
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.run(["gcc", *_CFLAGS, "-o", lib, src, "-lm"], check=True)
+    return _declare(ctypes.CDLL(lib))
+
+
 def _load():
     global _lib
     with _lock:
@@ -103,13 +133,18 @@ def vcos(x: float) -> float:
     return _load().gvo_vcos(float(x))
 
 
-def levels(family, eps, bounds):
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def levels(family, eps, bounds, lib=None):
     """Level structure: dict with L, Lj[d], h[L+1, d], s_f[d-k], s_t[L, le], A[L+1, d-k]."""
     d, k, le, _ = FAMILY_SHAPE[family]
     eps = np.ascontiguousarray(eps, dtype=np.float64)
     bounds = np.ascontiguousarray(bounds, dtype=np.float64)
     Lj = np.zeros(d, np.int32)
-    lib = _load()
+    lib = lib or _load()
     L = lib.gvo_levels(family, d, k, _ptr(eps), _ptr(bounds), _ptr(Lj), None, None, None, None)
     if L < 0:
         raise ValueError("invalid problem")
@@ -131,7 +166,7 @@ def root_records(family, eps, bounds, params):
     return f, t
 
 
-def solve(family, eps, bounds, params, flags=0, trace_cap=0, members=False):
+def solve(family, eps, bounds, params, flags=0, trace_cap=0, members=False, lib=None):
     """Run SurfaceConsensus.  Returns a dict with best_point[d], best_leaf[d],
     depth, mask (uint32 words), stats (tests, cells, leaves, L), and optionally
     the trace (level, coords, ub, lb of every tested child) and the best leaf's
@@ -149,7 +184,7 @@ def solve(family, eps, bounds, params, flags=0, trace_cap=0, members=False):
     tb = np.zeros(max(trace_cap, 1), np.int64)
     tn = np.zeros(1, np.int64)
     mem = np.full(max(n, 1), -1, np.int64) if members else None
-    rc = _load().gvo_solve(family, d, k, _ptr(eps), _ptr(bounds), _ptr(params), n, flags,
+    rc = (lib or _load()).gvo_solve(family, d, k, _ptr(eps), _ptr(bounds), _ptr(params), n, flags,
                            _ptr(best_point), _ptr(best_leaf), _ptr(depth), _ptr(mask), _ptr(stats),
                            trace_cap, _ptr(tl), _ptr(tc), _ptr(tu), _ptr(tb), _ptr(tn), _ptr(mem))
     if rc:

@@ -1,0 +1,97 @@
+"""Planted mistakes in the oracle (on the CPU) must be caught by the pins.
+
+Limit of these pins: a mistake that only tightens a conservative margin (for
+example dropping the canonization error A from the UB radius, or shrinking one
+Lipschitz term that the others dominate) changes a result only for surfaces
+within that margin of a decision, which random instances rarely produce; the
+level-structure pin still checks A itself.
+
+Each mutant is a copy of oracle/gv_oracle.c with one plausible mistake -- a
+dropped term, a wrong sign, a wrong index, a transposed operand -- compiled
+separately.  For each, at least one pin of tests/test_oracle_pins.py fails:
+the reported depth drops below the brute-force depth at some point (lower
+side), or exceeds the depth at the relaxed radius / counts a surface outside it
+(upper side).
+"""
+import numpy as np
+import pytest
+
+import brute
+import oracle
+from paper_2107_11810_gb300 import inputs
+
+MUTANTS = {
+    "plane_sign": ("t[1] * g->dpsi[1]) + t[2] * g->dpsi[2]", "t[1] * g->dpsi[1]) - t[2] * g->dpsi[2]"),
+    "pose_index": ("fo[1] = (f[1] - (t[0] * g->dpsi[1] + t[1] * g->dpsi[0]))",
+                   "fo[1] = (f[1] - (t[0] * g->dpsi[0] + t[1] * g->dpsi[1]))"),
+    "line_residual_sign": ("fo[0] = (f[0] - t[0] * g->dpsi[0]) - g->shift[1];",
+                           "fo[0] = (f[0] + t[0] * g->dpsi[0]) - g->shift[1];"),
+    "canon_error_not_accumulated": ("p->A[l + 1][j] = p->A[l][j] + delta;", "p->A[l + 1][j] = delta;"),
+    "snap_step_too_coarse": ("p->s_t[l][m] = pow2_floor(epsp_min / ((double)(le + 1) * sigma[m]));",
+                             "p->s_t[l][m] = pow2_floor(64.0 * epsp_min / ((double)(le + 1) * sigma[m]));"),
+    "radius_parent_width": ("R = R + lam[j * p->k + i] * p->h[l + 1][i];", "R = R + lam[j * p->k + i] * p->h[l + 1][i] * 0.25;"),
+    "child_shift_sign": ("g->shift[j] = bit ? p->h[l + 1][j] : -p->h[l + 1][j];",
+                         "g->shift[j] = bit ? -p->h[l + 1][j] : p->h[l + 1][j];"),
+    "pose_basis_swap": ("psi[0] = gvo_vcos(yaw);\n        psi[1] = gvo_vsin(yaw);",
+                        "psi[0] = gvo_vsin(yaw);\n        psi[1] = gvo_vcos(yaw);"),
+}
+
+CASES = {
+    inputs.LINE2D: lambda s: inputs.line2d(n=300, inlier_frac=0.3, eps=0.02, seed=s),
+    inputs.PLANE3D_SPH: lambda s: inputs.plane3d(n=120, inlier_frac=0.3, eps=0.08, sigma=0.002, seed=s),
+    inputs.POSE3DOF: lambda s: inputs.pose3dof(n=200, inlier_frac=0.3, eps_xy=2.0, eps_yaw_deg=4.0,
+                                               noise_deg=0.05, seed=s),
+}
+
+
+def pins_hold(lib, fam, seed):
+    """The level-structure, lower- and upper-side pins on one instance; False if any
+    fails."""
+    p = CASES[fam](seed)
+    lv = oracle.levels(p.family, p.eps, p.bounds, lib=lib)
+    L = lv["L"]
+    # level structure: canonization error accumulates (strictly increasing) and stays
+    # below eps/2; the essential-parameter steps respect their bound
+    if not (np.all(np.diff(lv["A"], axis=0) > 0) and np.all(lv["A"][L] <= p.eps[p.k:] / 2 + 1e-12)):
+        return False
+    r = oracle.solve(p.family, p.eps, p.bounds, p.params, lib=lib)
+    lo, W = p.bounds[0::2], p.bounds[1::2] - p.bounds[0::2]
+    dep = p.eps[p.k:]
+    rng = np.random.default_rng(seed)
+    pts = np.concatenate([lo + W * rng.uniform(size=(3000, p.d)), p.truth[None]])
+    grid = brute.leaf_centers(lo, W, lv["Lj"])
+    best = max(int(brute.depth(p.family, p.params, dep, c).max()) for c in np.array_split(grid, max(1, len(grid) // 4096)))
+    if r["depth"] < max(best, int(brute.depth(p.family, p.params, dep, pts).max())):
+        return False
+    L, hL = lv["L"], lv["h"][lv["L"]]
+    if p.family == inputs.LINE2D:
+        lam = np.abs(p.params[0]).max() + lv["s_t"][-1].max()
+    elif p.family == inputs.PLANE3D_SPH:
+        lam = np.linalg.norm(p.params, axis=0).max() + 2 * lv["s_t"][-1].max()
+    else:
+        lam = np.hypot(p.params[2], p.params[3]).max() + 2 * lv["s_t"][-1].max()
+    ep = dep + hL[p.k:] + lam * hL[: p.k].sum() + 2 * lv["A"][L] + 1e-9
+    if r["depth"] > brute.depth(p.family, p.params, ep, r["best_point"][None])[0]:
+        return False
+    members = oracle.mask_to_indices(r["mask"], p.n)
+    if len(members) != r["depth"]:
+        return False
+    res = brute.vertical_residuals(p.family, p.params[:, members], r["best_point"])[0]
+    return bool(np.all(np.abs(res) <= ep))
+
+
+def test_unmodified_oracle_passes_the_pins():
+    src = oracle.source()
+    lib = oracle.load_variant(src, "identity")
+    for fam in CASES:
+        assert pins_hold(lib, fam, 1)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name):
+    old, new = MUTANTS[name]
+    src = oracle.source()
+    assert src.count(old) == 1, name
+    lib = oracle.load_variant(src.replace(old, new), name)
+    caught = any(not pins_hold(lib, fam, seed) for fam in CASES for seed in (1, 2, 3))
+    assert caught, f"mutant {name} survived the pins"
