@@ -468,6 +468,7 @@ __device__ __forceinline__ void write_child(const Chunk &c, const RecState<FAM, 
 
 constexpr int kRPT = 4;              // records per thread in one tile
 constexpr int kTile = 256 * kRPT;    // records per block
+constexpr int kSpanCells = 64;       // tiles spanning at most this many cells count in shared memory
 
 // Proximity test of a chunk's records against all children of their cells.
 // Count pass (EMIT = false): per child UB = sum of mult over UB-passing records,
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
     __shared__ unsigned s_red[8][3 * NS];
     __shared__ int s_ci[NS];
     __shared__ unsigned long long s_base[NS];
+    __shared__ unsigned s_span[kSpanCells * NS * 3];
     const int64_t t0 = c.r0 + (int64_t)blockIdx.x * kTile;
     const int64_t t1 = t0 + kTile < c.r1 ? t0 + kTile : c.r1;
     const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
@@ -605,8 +607,92 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
                 }
             }
         }
+    } else if (clast - cfirst < kSpanCells) {
+        // ------------------ a few cells: shared-memory counters -------------------
+        const int span = clast - cfirst + 1;
+        for (int i = threadIdx.x; i < span * NS * 3; i += blockDim.x) s_span[i] = 0u;
+        __syncthreads();
+        if (!EMIT) {
+#pragma unroll 1
+            for (int k = 0; k < kRPT; ++k) {
+                int64_t r = t0 + threadIdx.x + k * 256;
+                if (r >= t1) break;
+                int cl = (int)((int64_t)c.in.cell[r] - c.c0);
+                if (!c.alive[cl]) continue;
+                RecState<FAM, PREC> st;
+                st.load(c.in, r);
+                if (PREC == 1) st.prep32(P, lev, c.geo32 + ((size_t)cl * (NS + 1) + NS) * F::NB);
+                else st.need64(P, lev);
+                unsigned ubm, lbm;
+                eval_record<FAM, PREC>(P, lev, st, c.geo32 + (size_t)cl * (NS + 1) * F::NB,
+                                       c.geo64 + (size_t)cl * NS * F::NB, ubm, lbm, nrechk);
+                c.passmask[r - c.r0] = (uint8_t)ubm;
+                unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
+                for (int s = 0; s < NS; ++s) {
+                    if (s & ~smask) continue;
+                    ++ntest;
+                    if ((ubm >> s) & 1) {
+                        atomicAdd(cnt + 3 * s, st.mult);
+                        atomicAdd(cnt + 3 * s + 2, 1u);
+                    }
+                    if ((lbm >> s) & 1) atomicAdd(cnt + 3 * s + 1, st.mult);
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < span * NS * 3; i += blockDim.x)
+                if (s_span[i]) atomicAdd(c.cnt + (size_t)cfirst * NS * 3 + i, s_span[i]);
+        } else {
+            // count this block's records per (cell, child), reserve each child's range
+            // with one global atomic, then place records by shared-memory ranks
+            unsigned em[kRPT];
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {
+                int64_t r = t0 + threadIdx.x + k * 256;
+                unsigned m = 0;
+                if (r < t1) {
+                    int cl = (int)((int64_t)c.in.cell[r] - c.c0);
+                    if (c.alive[cl]) {
+                        m = c.passmask[r - c.r0];
+                        for (int s = 0; s < NS; ++s)
+                            if (((m >> s) & 1) && c.child_idx[(size_t)cl * NS + s] < 0) m &= ~(1u << s);
+                        unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
+                        for (int s = 0; s < NS; ++s)
+                            if ((m >> s) & 1) atomicAdd(cnt + 3 * s, 1u);
+                    }
+                }
+                em[k] = m;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < span * NS; i += blockDim.x) {
+                unsigned v = s_span[3 * i];
+                if (v) s_span[3 * i + 1] = atomicAdd(&c.cursor[(size_t)cfirst * NS + i], v);
+                s_span[3 * i + 2] = 0u;
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int k = 0; k < kRPT; ++k) {
+                unsigned m = em[k];
+                if (!m) continue;
+                int64_t r = t0 + threadIdx.x + k * 256;
+                int cl = (int)((int64_t)c.in.cell[r] - c.c0);
+                const float *g32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
+                const double *g64 = c.geo64 + (size_t)cl * NS * F::NB;
+                RecState<FAM, PREC> st;
+                st.load(c.in, r);
+                if (PREC == 1) st.prep32(P, lev, g32 + NS * F::NB);
+                unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
+                for (int s = 0; s < NS; ++s) {
+                    if (!((m >> s) & 1)) continue;
+                    unsigned pos = cnt[3 * s + 1] + atomicAdd(cnt + 3 * s + 2, 1u);
+                    int32_t qn[F::ND];
+                    child_qf<FAM, PREC>(P, lev, st, g32, g64, s, qn, nrechk, c.sc);
+                    int ci = c.child_idx[(size_t)cl * NS + s];
+                    write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos);
+                }
+            }
+        }
     } else {
-        // --------------------------- several cells ----------------------------
+        // --------------------------- many cells ----------------------------
 #pragma unroll 1
         for (int k = 0; k < kRPT; ++k) {
             int64_t r = t0 + threadIdx.x + k * 256;
