@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 
 from paper_2107_11810_gb300 import inputs  # noqa: E402
 
+METRIC = "solved problems/sec and surface-cell tests/sec: FP32+recheck vs plain FP64 path"
+
 WORKLOADS = {
     "plane3d_n1e6": dict(make=lambda: inputs.plane3d(), desc="3D plane fitting, 1e6 points in the unit cube, "
                          "2% inliers (sigma 0.001), eps_d=0.005, eps_angle=eps/sqrt3, (theta,phi,d) space"),
@@ -171,7 +173,7 @@ def run_reference(args, rank, world):
     tps = tests / statistics.mean(times)
     # scale: problems/s = oracle tests/s / tests one full-size problem needs
     value = tps / gpu_tests if gpu_tests else None
-    line = dict(metric="solved problems/sec (3D plane fitting, 1e6 points); surface-cell tests/sec",
+    line = dict(metric=METRIC,
                 value=value, unit="problems/s", impl="reference", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1000 * statistics.mean(times), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
@@ -222,7 +224,7 @@ def run_batched(args, rank, world, w):
     r2 = s.solve_batched((pinned.cuda(non_blocking=True), offs))
     words = torch.empty(r2["masks"].numel(), dtype=torch.int32).copy_(r2["masks"])
     e2e_t = time.perf_counter() - t0
-    out = dict(metric="solved problems/sec (batched 3DoF voting, 256 problems)", value=len(probs) * args.steps / total,
+    out = dict(metric=METRIC, value=len(probs) * args.steps / total,
                unit="problems/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="strong", vs_baseline=None,
                dtype="f32+f64" if args.precision == 1 else "f64", data="synthetic",
@@ -349,8 +351,7 @@ def main():
     assert rh["depth"] == depth
     e2e = dict(value=1.0 / statistics.mean(e2e_times), unit="problems/s",
                h2d_bytes_per_step=int(p.params.nbytes), d2h_bytes_per_step=int(((p.n + 31) // 32) * 4))
-    out = dict(metric="solved problems/sec (3D plane fitting, 1e6 points); surface-cell tests/sec",
-               value=value, unit="problems/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+    out = dict(metric=METRIC, value=value, unit="problems/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                dtype="f32+f64" if args.precision == 1 else "f64", data="synthetic",
                config=dict(workload=args.workload, desc=w["desc"], n=p.n, l2="flushed between timed steps",

@@ -672,18 +672,28 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
 #pragma unroll 1
             for (int k = 0; k < kRPT; ++k) {
                 unsigned m = em[k];
-                if (!m) continue;
+                if (!__any_sync(kFull, m != 0)) continue;          // uniform
                 int64_t r = t0 + threadIdx.x + k * 256;
-                int cl = (int)((int64_t)c.in.cell[r] - c.c0);
+                int cl = m ? (int)((int64_t)c.in.cell[r] - c.c0) : 0;
                 const float *g32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
                 const double *g64 = c.geo64 + (size_t)cl * NS * F::NB;
                 RecState<FAM, PREC> st;
-                st.load(c.in, r);
-                if (PREC == 1) st.prep32(P, lev, g32 + NS * F::NB);
+                if (m) {
+                    st.load(c.in, r);
+                    if (PREC == 1) st.prep32(P, lev, g32 + NS * F::NB);
+                }
                 unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
                 for (int s = 0; s < NS; ++s) {
-                    if (!((m >> s) & 1)) continue;
-                    unsigned pos = cnt[3 * s + 1] + atomicAdd(cnt + 3 * s + 2, 1u);
+                    bool want = (m >> s) & 1;
+                    // lanes writing to the same child form a group: one shared atomic
+                    // per group, contiguous positions inside it
+                    unsigned grp = __match_any_sync(kFull, want ? cl * NS + s : -1);
+                    int leader = __ffs(grp) - 1;
+                    unsigned base = 0;
+                    if (want && lane == leader) base = atomicAdd(cnt + 3 * s + 2, (unsigned)__popc(grp));
+                    base = __shfl_sync(kFull, base, leader);
+                    if (!want) continue;
+                    unsigned pos = cnt[3 * s + 1] + base + __popc(grp & ((1u << lane) - 1u));
                     int32_t qn[F::ND];
                     child_qf<FAM, PREC>(P, lev, st, g32, g64, s, qn, nrechk, c.sc);
                     int ci = c.child_idx[(size_t)cl * NS + s];
