@@ -466,7 +466,14 @@ __device__ __forceinline__ void write_child(const Chunk &c, const RecState<FAM, 
     c.out.cell[at] = (uint32_t)ci;
 }
 
-constexpr int kRPT = 4;              // records per thread in one tile
+#ifndef GV_KRPT
+#define GV_KRPT 4
+#endif
+#ifndef GV_MINBLOCKS
+#define GV_MINBLOCKS 4
+#endif
+constexpr int kRPT = GV_KRPT;        // records per thread in one tile (count pass, two-level)
+constexpr int kRPTEmit = 2;          // records per thread in one tile (emit pass)
 constexpr int kTile = 256 * kRPT;    // records per block
 constexpr int kSpanCells = 64;       // tiles spanning at most this many cells count in shared memory
 
@@ -482,9 +489,11 @@ constexpr int kSpanCells = 64;       // tiles spanning at most this many cells c
 // reserves the child ranges with one atomic per child and a block scan.  Tiles
 // spanning several cells fall back to warp-level aggregation.
 template <int FAM, int PREC, bool EMIT>
-__global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
+__global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
     using F = Fam<FAM>;
     constexpr int NS = 1 << F::D;
+    constexpr int RPT = EMIT ? kRPTEmit : kRPT;   // records per thread (tuned per pass)
+    constexpr int TILE = 256 * RPT;
     const Problem &P = c.P;
     const Level &lev = c.lev;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -495,8 +504,8 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
     __shared__ int s_ci[NS];
     __shared__ unsigned long long s_base[NS];
     __shared__ unsigned s_span[kSpanCells * NS * 3];
-    const int64_t t0 = c.r0 + (int64_t)blockIdx.x * kTile;
-    const int64_t t1 = t0 + kTile < c.r1 ? t0 + kTile : c.r1;
+    const int64_t t0 = c.r0 + (int64_t)blockIdx.x * TILE;
+    const int64_t t1 = t0 + TILE < c.r1 ? t0 + TILE : c.r1;
     const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
     const int clast = (int)((int64_t)c.in.cell[t1 - 1] - c.c0);
     unsigned nrechk = 0, ntest = 0;
@@ -514,23 +523,24 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
 #pragma unroll
             for (int s = 0; s < NS; ++s) aub[s] = alb[s] = an[s] = 0;
 #pragma unroll
-            for (int k = 0; k < kRPT; ++k) {
+            for (int k = 0; k < RPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
-                if (r >= t1) break;
-                RecState<FAM, PREC> st;
-                st.load(c.in, r);
-                if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
-                else st.need64(P, lev);
-                unsigned ubm, lbm;
-                eval_record<FAM, PREC>(P, lev, st, s_g32, s_g64, ubm, lbm, nrechk);
-                c.passmask[r - c.r0] = (uint8_t)ubm;
+                if (r < t1) {                      // no break: loads of later records may issue early
+                    RecState<FAM, PREC> st;
+                    st.load(c.in, r);
+                    if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
+                    else st.need64(P, lev);
+                    unsigned ubm, lbm;
+                    eval_record<FAM, PREC>(P, lev, st, s_g32, s_g64, ubm, lbm, nrechk);
+                    c.passmask[r - c.r0] = (uint8_t)ubm;
 #pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    if (s & ~smask) continue;
-                    ++ntest;
-                    aub[s] += ((ubm >> s) & 1) ? st.mult : 0u;
-                    alb[s] += ((lbm >> s) & 1) ? st.mult : 0u;
-                    an[s] += (ubm >> s) & 1;
+                    for (int s = 0; s < NS; ++s) {
+                        if (s & ~smask) continue;
+                        ++ntest;
+                        aub[s] += ((ubm >> s) & 1) ? st.mult : 0u;
+                        alb[s] += ((lbm >> s) & 1) ? st.mult : 0u;
+                        an[s] += (ubm >> s) & 1;
+                    }
                 }
             }
 #pragma unroll
@@ -554,10 +564,10 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
         } else {
             // Positions in (k, warp, lane) order so that each warp's stores for one
             // child are contiguous: per k and slot, warp counts are scanned in smem.
-            __shared__ unsigned s_wcnt[kRPT][8][NS];
-            unsigned em[kRPT];
+            __shared__ unsigned s_wcnt[RPT][8][NS];
+            unsigned em[RPT];
 #pragma unroll
-            for (int k = 0; k < kRPT; ++k) {
+            for (int k = 0; k < RPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
                 unsigned m = 0;
                 if (r < t1) {
@@ -577,7 +587,7 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
             if (threadIdx.x < NS) {
                 int s = threadIdx.x;
                 unsigned run = 0;
-                for (int k = 0; k < kRPT; ++k)
+                for (int k = 0; k < RPT; ++k)
                     for (int w = 0; w < 8; ++w) {
                         unsigned v = s_wcnt[k][w][s];
                         s_wcnt[k][w][s] = run;
@@ -587,7 +597,7 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
             }
             __syncthreads();
 #pragma unroll
-            for (int k = 0; k < kRPT; ++k) {
+            for (int k = 0; k < RPT; ++k) {
                 unsigned m = em[k];
                 int64_t r = t0 + threadIdx.x + k * 256;
                 RecState<FAM, PREC> st;
@@ -614,7 +624,7 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
         __syncthreads();
         if (!EMIT) {
 #pragma unroll 1
-            for (int k = 0; k < kRPT; ++k) {
+            for (int k = 0; k < RPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
                 if (r >= t1) break;
                 int cl = (int)((int64_t)c.in.cell[r] - c.c0);
@@ -644,9 +654,9 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
         } else {
             // count this block's records per (cell, child), reserve each child's range
             // with one global atomic, then place records by shared-memory ranks
-            unsigned em[kRPT];
+            unsigned em[RPT];
 #pragma unroll
-            for (int k = 0; k < kRPT; ++k) {
+            for (int k = 0; k < RPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
                 unsigned m = 0;
                 if (r < t1) {
@@ -670,7 +680,7 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
             }
             __syncthreads();
 #pragma unroll 1
-            for (int k = 0; k < kRPT; ++k) {
+            for (int k = 0; k < RPT; ++k) {
                 unsigned m = em[k];
                 if (!__any_sync(kFull, m != 0)) continue;          // uniform
                 int64_t r = t0 + threadIdx.x + k * 256;
@@ -704,7 +714,7 @@ __global__ void __launch_bounds__(256, 4) k_test(Chunk c) {
     } else {
         // --------------------------- many cells ----------------------------
 #pragma unroll 1
-        for (int k = 0; k < kRPT; ++k) {
+        for (int k = 0; k < RPT; ++k) {
             int64_t r = t0 + threadIdx.x + k * 256;
             bool act = false;
             int cl = 0;
@@ -819,7 +829,7 @@ __device__ __forceinline__ void derive_child(const Problem &P, const Level &lev,
 }
 
 template <int FAM, int PREC, bool EMIT>
-__global__ void __launch_bounds__(256, 4) k_test2(Chunk c, Chunk c1, const uint8_t *__restrict__ pm2_in,
+__global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test2(Chunk c, Chunk c1, const uint8_t *__restrict__ pm2_in,
                                                    uint8_t *pm2_out) {
     using F = Fam<FAM>;
     constexpr int NS = 1 << F::D;
@@ -1332,7 +1342,7 @@ void launch_cell_geo(const Chunk &c, cudaStream_t st) {
 void launch_test(const Chunk &c, bool emit, cudaStream_t st) {
     int64_t nr = c.r1 - c.r0;
     if (nr <= 0) return;
-    unsigned g = blocks_for(nr, kTile);
+    unsigned g = blocks_for(nr, emit ? 256 * kRPTEmit : kTile);
     if (c.precision == 0) {
         if (emit) { GV_DISPATCH(c.P.fam, (k_test<FAMV, 0, true><<<g, 256, 0, st>>>(c))); }
         else      { GV_DISPATCH(c.P.fam, (k_test<FAMV, 0, false><<<g, 256, 0, st>>>(c))); }
