@@ -89,9 +89,7 @@ typedef enum {
                                  context's stream (see vote_get_kernel_times)        */
     VOTE_OPT_BATCH_WORKERS = 10, /* host workers (streams) of vote_solve_batched, 1..32,
                                  default 4                                           */
-    VOTE_OPT_DIVE = 11,       /* 1 = before the sweep, expand one root-to-leaf path
-                                 always taking the child with the largest UB, to
-                                 raise the pruning bound early (default); 0 = off    */
+
     VOTE_OPT_TWO_LEVEL = 9    /* expand two levels per read of a chunk's records when
                                  its children would hold more than this many times
                                  its records (their records are then never written

@@ -78,7 +78,6 @@ struct vote_ctx {
     int kernel_timing = 0;
     double two_level = 0.0;
     int batch_workers = 4;
-    int dive = 1;
     int family = 0;
     double eps_in[GV_MAXD] = {}, bounds_in[2 * GV_MAXD] = {};
     std::vector<vote_ctx *> workers;   // sub-contexts of vote_solve_batched
@@ -451,10 +450,8 @@ static vote_status expand_two(vote_ctx *c, int l, Chunk &ch, int64_t nr, int64_t
     return VOTE_OK;
 }
 
-// Expand a chunk of level-l cells.  Normally the chunk is taken from the top of the
-// level's stack and popped; with only >= 0 the single cell `only` is expanded in
-// place (greedy dive), and its UB is set to 0 so the regular traversal skips it.
-static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
+// Expand a chunk of level-l cells taken from the top of the level's stack.
+static vote_status expand_chunk(vote_ctx *c, int l) {
     const Problem &P = c->P;
     LevelStore &S = c->ls[l];
     const int ns = c->ns;
@@ -462,25 +459,18 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     for (int s = 0; s < ns; ++s)
         if (!(s & ~c->lev[l].split_mask)) ++nvalid;
     // chunk: cells [c0, ncells) from the top of the stack, about chunk_records records
-    int64_t c1 = only >= 0 ? only + 1 : S.ncells, r1 = S.nrecs;
+    int64_t c1 = S.ncells, r1 = S.nrecs;
     int64_t avg = S.nrecs / (S.ncells > 0 ? S.ncells : 1);
     int64_t K = c->chunk_records / (avg > 0 ? avg : 1);
     if (K < 1) K = 1;
     if (K > (1 << 22)) K = 1 << 22;
     int64_t c0, r0;
-    if (only >= 0) K = 1;
     for (;;) {
         c0 = c1 - K > 0 ? c1 - K : 0;
         CK(cudaMemcpyAsync(c->h_tmp, (uint64_t *)S.rbeg.p + c0, 8, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         ev_collect(c);
         r0 = (int64_t)*c->h_tmp;
-        if (only >= 0) {
-            uint32_t cnt = 0;
-            CK(cudaMemcpy(&cnt, (uint32_t *)S.rcnt.p + only, 4, cudaMemcpyDeviceToHost));
-            r1 = r0 + cnt;
-            break;
-        }
         if (r1 - r0 <= 2 * c->chunk_records || K == 1) break;
         K = K / 2;
     }
@@ -597,14 +587,8 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     c->stats.records += nr;
     c->lv_cells[l] += nc;
     c->lv_recs[l] += nr;
-    if (only >= 0) {
-        uint32_t zero = 0;                       // expanded: the traversal skips it
-        CK(cudaMemcpyAsync((uint32_t *)S.ub.p + only, &zero, 4, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-    } else {
-        S.ncells = c0;
-        S.nrecs = r0;
-    }
+    S.ncells = c0;
+    S.nrecs = r0;
     if (lev.leaf_children) {
         c->stats.leaves += (int64_t)nc * nvalid;
         return VOTE_OK;
@@ -699,22 +683,6 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         if (c->h_sc->err) {
             set_err("surface parameters are not finite or out of the representable range");
             return VOTE_EINVAL;
-        }
-        if (c->dive) {
-            // greedy dive: from the root, expand only the child with the largest UB,
-            // down to the leaves, to raise the pruning bound before the sweep
-            int64_t cell = 0;
-            for (int l = 0; l < P.L; ++l) {
-                TRY(expand_chunk(c, l, cell));
-                if (l + 1 >= P.L) break;
-                int64_t m = c->ls[l + 1].ncells;
-                if (m <= 0) break;
-                std::vector<uint32_t> ub((size_t)m);
-                CK(cudaMemcpy(ub.data(), c->ls[l + 1].ub.p, 4 * (size_t)m, cudaMemcpyDeviceToHost));
-                cell = 0;
-                for (int64_t i = 1; i < m; ++i)
-                    if (ub[i] > ub[cell]) cell = i;
-            }
         }
         for (;;) {
             int l = -1;
@@ -876,10 +844,7 @@ vote_status vote_set_option(vote_ctx *c, int key, double v) {
         if (!(v >= 1 && v <= 32)) break;
         c->batch_workers = (int)v;
         return VOTE_OK;
-    case VOTE_OPT_DIVE:
-        if (v != 0 && v != 1) break;
-        c->dive = (int)v;
-        return VOTE_OK;
+
     default:
         set_err("unknown option %d", key);
         return VOTE_EINVAL;
@@ -944,7 +909,6 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
         w->prune = c->prune;
         w->chunk_records = c->chunk_records;
         w->two_level = c->two_level;
-        w->dive = c->dive;
         w->fault_alloc_at = 0;
     }
     std::vector<int64_t> wordoff(B + 1, 0);

@@ -473,7 +473,10 @@ __device__ __forceinline__ void write_child(const Chunk &c, const RecState<FAM, 
 #define GV_MINBLOCKS 4
 #endif
 constexpr int kRPT = GV_KRPT;        // records per thread in one tile (count pass, two-level)
-constexpr int kRPTEmit = 2;          // records per thread in one tile (emit pass)
+#ifndef GV_KRPT_EMIT
+#define GV_KRPT_EMIT 2
+#endif
+constexpr int kRPTEmit = GV_KRPT_EMIT;  // records per thread in one tile (emit pass)
 constexpr int kTile = 256 * kRPT;    // records per block
 constexpr int kSpanCells = 64;       // tiles spanning at most this many cells count in shared memory
 

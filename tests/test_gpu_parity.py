@@ -185,14 +185,12 @@ def test_grouping_parity_and_merging(family, two_level):
 
 
 @pytest.mark.parametrize("chunk", [1, 7, 1000])
-@pytest.mark.parametrize("dive", [0, 1])
-def test_chunking_and_dive_do_not_change_results(chunk, dive):
+def test_chunking_does_not_change_results(chunk):
     v = vote_mod()
     for fam in FAMS:
         p = small(fam, 3000, 8)
         o = oracle.solve(p.family, p.eps, p.bounds, p.params)
         s = v.Solver(p.family, p.eps, p.bounds, chunk_records=chunk)
-        s.set_option(v.VOTE_OPT_DIVE, dive)
         g = s.solve(dev(p))
         g["mask"] = v.mask_words_to_numpy(g["mask"])
         assert_same(g, o, p.n)
