@@ -59,9 +59,7 @@ struct DevBuf {
 
 struct LevelStore {
     DevBuf qf[GV_MAXD], qt[GV_MAXT], mult, cell;
-    size_t rec_cap = 0;
     DevBuf key, rbeg, rcnt, ub;
-    size_t cell_cap = 0;
     int64_t ncells = 0, nrecs = 0;
 };
 
@@ -287,21 +285,22 @@ static void release(vote_ctx *c, DevBuf &b) {
     b.bytes = 0;
 }
 
+// Every array is checked against its own allocated size (ensure returns at once
+// when it is large enough), so no separate capacity figure can drift from the
+// allocations.
 static vote_status ensure_level(vote_ctx *c, int l, size_t recs, size_t cells) {
     LevelStore &s = c->ls[l];
-    if (recs > s.rec_cap) {
+    if (recs > 0) {
         for (int j = 0; j < c->P.nd; ++j) TRY(ensure(c, s.qf[j], recs * 4));
         for (int m = 0; m < c->P.le; ++m) TRY(ensure(c, s.qt[m], recs * 4));
         TRY(ensure(c, s.mult, recs * 4));
         TRY(ensure(c, s.cell, recs * 4));
-        s.rec_cap = recs + recs / 4;
     }
-    if (cells > s.cell_cap) {
+    if (cells > 0) {
         TRY(ensure(c, s.key, cells * 8));
         TRY(ensure(c, s.rbeg, cells * 8));
         TRY(ensure(c, s.rcnt, cells * 4));
         TRY(ensure(c, s.ub, cells * 4));
-        s.cell_cap = cells + cells / 4;
     }
     return VOTE_OK;
 }
