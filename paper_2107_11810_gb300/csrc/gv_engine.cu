@@ -76,6 +76,7 @@ struct vote_ctx {
     int kernel_timing = 0;
     double two_level = 0.0;
     int batch_workers = 4;
+    int dive = 1;
     int family = 0;
     double eps_in[GV_MAXD] = {}, bounds_in[2 * GV_MAXD] = {};
     std::vector<vote_ctx *> workers;   // sub-contexts of vote_solve_batched
@@ -449,8 +450,11 @@ static vote_status expand_two(vote_ctx *c, int l, Chunk &ch, int64_t nr, int64_t
     return VOTE_OK;
 }
 
-// Expand a chunk of level-l cells taken from the top of the level's stack.
-static vote_status expand_chunk(vote_ctx *c, int l) {
+// Expand a chunk of level-l cells taken from the top of the level's stack.  With
+// only >= 0, the single cell `only` is expanded where it sits instead (greedy
+// dive); its UB is then set to 0, so the sweep later finds it below every
+// threshold and gives it no children.
+static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     const Problem &P = c->P;
     LevelStore &S = c->ls[l];
     const int ns = c->ns;
@@ -458,18 +462,24 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     for (int s = 0; s < ns; ++s)
         if (!(s & ~c->lev[l].split_mask)) ++nvalid;
     // chunk: cells [c0, ncells) from the top of the stack, about chunk_records records
-    int64_t c1 = S.ncells, r1 = S.nrecs;
+    int64_t c1 = only >= 0 ? only + 1 : S.ncells, r1 = S.nrecs;
     int64_t avg = S.nrecs / (S.ncells > 0 ? S.ncells : 1);
     int64_t K = c->chunk_records / (avg > 0 ? avg : 1);
-    if (K < 1) K = 1;
+    if (K < 1 || only >= 0) K = 1;
     if (K > (1 << 22)) K = 1 << 22;
     int64_t c0, r0;
     for (;;) {
         c0 = c1 - K > 0 ? c1 - K : 0;
         CK(cudaMemcpyAsync(c->h_tmp, (uint64_t *)S.rbeg.p + c0, 8, cudaMemcpyDeviceToHost, c->stream));
+        if (only >= 0)
+            CK(cudaMemcpyAsync(c->h_tmp + 1, (uint32_t *)S.rcnt.p + only, 4, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         ev_collect(c);
-        r0 = (int64_t)*c->h_tmp;
+        r0 = (int64_t)c->h_tmp[0];
+        if (only >= 0) {
+            r1 = r0 + (int64_t)(uint32_t)c->h_tmp[1];
+            break;
+        }
         if (r1 - r0 <= 2 * c->chunk_records || K == 1) break;
         K = K / 2;
     }
@@ -586,8 +596,12 @@ static vote_status expand_chunk(vote_ctx *c, int l) {
     c->stats.records += nr;
     c->lv_cells[l] += nc;
     c->lv_recs[l] += nr;
-    S.ncells = c0;
-    S.nrecs = r0;
+    if (only >= 0) {
+        CK(cudaMemsetAsync((uint32_t *)S.ub.p + only, 0, 4, c->stream));
+    } else {
+        S.ncells = c0;
+        S.nrecs = r0;
+    }
     if (lev.leaf_children) {
         c->stats.leaves += (int64_t)nc * nvalid;
         return VOTE_OK;
@@ -682,6 +696,28 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         if (c->h_sc->err) {
             set_err("surface parameters are not finite or out of the representable range");
             return VOTE_EINVAL;
+        }
+        if (c->dive) {
+            // greedy dive: from the root, expand only the child with the largest UB
+            // (the first on ties) down to the leaves, so the sweep starts with a
+            // leaf's count as its pruning bound
+            int64_t cell = 0;
+            for (int l = 0; l < P.L; ++l) {
+                TRY(expand_chunk(c, l, cell));
+                int64_t m = l + 1 < P.L ? c->ls[l + 1].ncells : 0;
+                if (m <= 0) break;
+                uint32_t best = 0;
+                cell = -1;
+                for (int64_t i0 = 0; i0 < m; i0 += 16) {      // 16 UBs fit the pinned slot
+                    int64_t k = m - i0 < 16 ? m - i0 : 16;
+                    CK(cudaMemcpyAsync(c->h_tmp, (uint32_t *)c->ls[l + 1].ub.p + i0, 4 * (size_t)k,
+                                       cudaMemcpyDeviceToHost, c->stream));
+                    CK(cudaStreamSynchronize(c->stream));
+                    const uint32_t *ub = (const uint32_t *)c->h_tmp;
+                    for (int64_t i = 0; i < k; ++i)
+                        if (cell < 0 || ub[i] > best) best = ub[i], cell = i0 + i;
+                }
+            }
         }
         for (;;) {
             int l = -1;
@@ -843,6 +879,10 @@ vote_status vote_set_option(vote_ctx *c, int key, double v) {
         if (!(v >= 1 && v <= 32)) break;
         c->batch_workers = (int)v;
         return VOTE_OK;
+    case VOTE_OPT_DIVE:
+        if (v != 0 && v != 1) break;
+        c->dive = (int)v;
+        return VOTE_OK;
 
     default:
         set_err("unknown option %d", key);
@@ -908,6 +948,7 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
         w->prune = c->prune;
         w->chunk_records = c->chunk_records;
         w->two_level = c->two_level;
+        w->dive = c->dive;
         w->fault_alloc_at = 0;
     }
     std::vector<int64_t> wordoff(B + 1, 0);

@@ -24,6 +24,7 @@ _lib = None
 VOTE_OPT_PRECISION, VOTE_OPT_PRUNE, VOTE_OPT_CHUNK_RECORDS = 1, 2, 3
 VOTE_OPT_TRACE_CAP, VOTE_OPT_GROUP, VOTE_OPT_FAULT_ALLOC_AT = 4, 5, 6
 VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING, VOTE_OPT_TWO_LEVEL, VOTE_OPT_BATCH_WORKERS = 7, 8, 9, 10
+VOTE_OPT_DIVE = 11
 KERNEL_CLASSES = ["lift", "cell_geo", "test_count", "test_emit", "children", "replay", "group", "spare"]
 STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
           5: "VOTE_ETIMEOUT", 6: "VOTE_EUNSUPPORTED", 7: "VOTE_EINTERNAL"}

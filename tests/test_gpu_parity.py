@@ -108,6 +108,7 @@ def test_full_trace_without_pruning_equals_oracle(family):
     key = lambda l, c: (int(l), tuple(int(x) for x in c))
     dg = {key(l, c): (int(u), int(b)) for l, c, u, b in zip(tg["level"], tg["coords"], tg["ub"], tg["lb"])}
     do = {key(l, c): (int(u), int(b)) for l, c, u, b in zip(to["level"], to["coords"], to["ub"], to["lb"])}
+    assert len(tg["level"]) == len(dg)          # no cell tested twice (the dive's cells included)
     assert dg == do
     assert_same(g, o, p.n)
 
@@ -184,13 +185,15 @@ def test_grouping_parity_and_merging(family, two_level):
     assert s1.stats()["tests"] < s0.stats()["tests"]
 
 
-@pytest.mark.parametrize("chunk", [1, 7, 1000])
-def test_chunking_does_not_change_results(chunk):
+@pytest.mark.parametrize("chunk", [1, 2, 7, 1000])
+@pytest.mark.parametrize("dive", [0, 1])
+def test_chunking_and_dive_do_not_change_results(chunk, dive):
     v = vote_mod()
     for fam in FAMS:
         p = small(fam, 3000, 8)
         o = oracle.solve(p.family, p.eps, p.bounds, p.params)
         s = v.Solver(p.family, p.eps, p.bounds, chunk_records=chunk)
+        s.set_option(v.VOTE_OPT_DIVE, dive)
         g = s.solve(dev(p))
         g["mask"] = v.mask_words_to_numpy(g["mask"])
         assert_same(g, o, p.n)
