@@ -198,6 +198,20 @@ __device__ __forceinline__ int test64(const Level &lev, const double *f, const d
     return ub | (lb << 1);
 }
 
+// Bits 0-3 of x moved to bits 0, 8, 16, 24 (the four shifted copies of x do not
+// overlap, so the product has no carries).
+__device__ __forceinline__ unsigned spread4(unsigned x) { return (x * 0x00204081u) & 0x01010101u; }
+
+// Child slots that exist at this level (slots that split only unsplit coordinates do not).
+template <int NS>
+__device__ __forceinline__ unsigned valid_slots(int smask) {
+    unsigned v = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+        if (!(s & ~smask)) v |= 1u << s;
+    return v;
+}
+
 // Block-wide exclusive scan of one 64-bit value per thread (blockDim = 256).
 __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long *total) {
     __shared__ unsigned long long warp_tot[8];
@@ -507,6 +521,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
     __shared__ int s_ci[NS];
     __shared__ unsigned long long s_base[NS];
     __shared__ unsigned s_span[kSpanCells * NS * 3];
+    __shared__ unsigned s_xw[2 * NS];
     const int64_t t0 = c.r0 + (int64_t)blockIdx.x * TILE;
     const int64_t t1 = t0 + TILE < c.r1 ? t0 + TILE : c.r1;
     const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
@@ -520,11 +535,19 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
             s_g32[i] = c.geo32[(size_t)cl * (NS + 1) * F::NB + i];
         for (int i = threadIdx.x; i < NS * F::NB; i += blockDim.x) s_g64[i] = c.geo64[(size_t)cl * NS * F::NB + i];
         if (EMIT && threadIdx.x < NS) s_ci[threadIdx.x] = c.child_idx[(size_t)cl * NS + threadIdx.x];
+        if (!EMIT && threadIdx.x < 2 * NS) s_xw[threadIdx.x] = 0u;
         __syncthreads();
         if (!EMIT) {
-            unsigned aub[NS], alb[NS], an[NS];
+            // Per-slot pass counts packed one byte per slot (slots 0-3 in pu[0]/pl[0],
+            // 4-7 in pu[1]/pl[1]): a thread adds at most RPT per byte and a warp at most
+            // 32 * RPT < 256, so no byte carries into the next.  The weight of a record
+            // beyond 1 (multiplicity after grouping) goes to shared counters.
+            static_assert(32 * RPT < 256, "packed per-slot counters would overflow a byte");
+            constexpr int NW = NS > 4 ? 2 : 1;
+            unsigned pu[NW], pl[NW];
 #pragma unroll
-            for (int s = 0; s < NS; ++s) aub[s] = alb[s] = an[s] = 0;
+            for (int w = 0; w < NW; ++w) pu[w] = pl[w] = 0u;
+            unsigned nrec = 0;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
@@ -536,25 +559,32 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                     unsigned ubm, lbm;
                     eval_record<FAM, PREC>(P, lev, st, s_g32, s_g64, ubm, lbm, nrechk);
                     c.passmask[r - c.r0] = (uint8_t)ubm;
+                    ++nrec;
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) {
-                        if (s & ~smask) continue;
-                        ++ntest;
-                        aub[s] += ((ubm >> s) & 1) ? st.mult : 0u;
-                        alb[s] += ((lbm >> s) & 1) ? st.mult : 0u;
-                        an[s] += (ubm >> s) & 1;
+                    for (int w = 0; w < NW; ++w) {
+                        pu[w] += spread4((ubm >> (4 * w)) & 15u);
+                        pl[w] += spread4((lbm >> (4 * w)) & 15u);
+                    }
+                    if (st.mult != 1u) {
+                        unsigned x = st.mult - 1u;
+                        for (unsigned b = ubm; b; b &= b - 1) atomicAdd(&s_xw[2 * (__ffs(b) - 1)], x);
+                        for (unsigned b = lbm; b; b &= b - 1) atomicAdd(&s_xw[2 * (__ffs(b) - 1) + 1], x);
                     }
                 }
             }
+            ntest = nrec * (unsigned)__popc(valid_slots<NS>(smask));
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                unsigned a = __reduce_add_sync(kFull, aub[s]);
-                unsigned b = __reduce_add_sync(kFull, alb[s]);
-                unsigned d = __reduce_add_sync(kFull, an[s]);
+            for (int w = 0; w < NW; ++w) {
+                unsigned a = __reduce_add_sync(kFull, pu[w]);
+                unsigned b = __reduce_add_sync(kFull, pl[w]);
                 if (lane == 0) {
-                    s_red[warp][3 * s] = a;
-                    s_red[warp][3 * s + 1] = b;
-                    s_red[warp][3 * s + 2] = d;
+#pragma unroll
+                    for (int q = 0; q < 4 && 4 * w + q < NS; ++q) {
+                        unsigned na = (a >> (8 * q)) & 255u, nb = (b >> (8 * q)) & 255u;
+                        s_red[warp][3 * (4 * w + q)] = na;
+                        s_red[warp][3 * (4 * w + q) + 1] = nb;
+                        s_red[warp][3 * (4 * w + q) + 2] = na;
+                    }
                 }
             }
             __syncthreads();
@@ -562,6 +592,8 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                 unsigned v = 0;
 #pragma unroll
                 for (int w = 0; w < 8; ++w) v += s_red[w][threadIdx.x];
+                int s = threadIdx.x / 3, f = threadIdx.x % 3;
+                if (f < 2) v += s_xw[2 * s + f];   // UB and LB sums are weighted by multiplicity
                 if (v) atomicAdd(c.cnt + (size_t)cl * NS * 3 + threadIdx.x, v);
             }
         } else {
