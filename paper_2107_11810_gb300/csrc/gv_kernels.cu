@@ -202,6 +202,19 @@ __device__ __forceinline__ int test64(const Level &lev, const double *f, const d
 // overlap, so the product has no carries).
 __device__ __forceinline__ unsigned spread4(unsigned x) { return (x * 0x00204081u) & 0x01010101u; }
 
+// Lanes of a warp hold consecutive records and a cell's records are contiguous, so
+// the lanes of one cell form one run of lanes.  Returns the calling lane's run (key:
+// the lane's cell, or -1 for a lane without a record).
+__device__ __forceinline__ unsigned run_mask(int key, int lane) {
+    int prev = __shfl_up_sync(kFull, key, 1);
+    unsigned heads = __ballot_sync(kFull, lane == 0 || prev != key);
+    unsigned upto = lane == 31 ? kFull : ((2u << lane) - 1u);     // lanes 0..lane
+    int start = 31 - __clz(heads & upto);
+    unsigned after = heads & ~upto;
+    unsigned below_end = after ? ((1u << (__ffs(after) - 1)) - 1u) : kFull;
+    return below_end & ~((1u << start) - 1u);
+}
+
 // Child slots that exist at this level (slots that split only unsplit coordinates do not).
 template <int NS>
 __device__ __forceinline__ unsigned valid_slots(int smask) {
@@ -640,8 +653,10 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                     st.load(c.in, r);
                     if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
                 }
-#pragma unroll
-                for (int s = 0; s < NS; ++s) {
+                // only the slots some lane of the warp writes; one copy of the body
+#pragma unroll 1
+                for (unsigned u = __reduce_or_sync(kFull, m); u; u &= u - 1) {
+                    const int s = __ffs(u) - 1;
                     unsigned b = __ballot_sync(kFull, (m >> s) & 1);
                     if (!((m >> s) & 1)) continue;
                     unsigned pos = (unsigned)s_base[s] + s_wcnt[k][warp][s] + __popc(b & ((1u << lane) - 1u));
@@ -690,12 +705,15 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
             // count this block's records per (cell, child), reserve each child's range
             // with one global atomic, then place records by shared-memory ranks
             unsigned em[RPT];
+            int ck[RPT];
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
                 unsigned m = 0;
+                ck[k] = -1;
                 if (r < t1) {
                     int cl = (int)((int64_t)c.in.cell[r] - c.c0);
+                    ck[k] = cl;
                     if (c.alive[cl]) {
                         m = c.passmask[r - c.r0];
                         for (int s = 0; s < NS; ++s)
@@ -717,9 +735,11 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
 #pragma unroll 1
             for (int k = 0; k < RPT; ++k) {
                 unsigned m = em[k];
-                if (!__any_sync(kFull, m != 0)) continue;          // uniform
+                unsigned wm = __reduce_or_sync(kFull, m);
+                if (!wm) continue;                                  // uniform
                 int64_t r = t0 + threadIdx.x + k * 256;
-                int cl = m ? (int)((int64_t)c.in.cell[r] - c.c0) : 0;
+                const unsigned run = run_mask(ck[k], lane);
+                int cl = ck[k] < 0 ? cfirst : ck[k];
                 const float *g32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
                 const double *g64 = c.geo64 + (size_t)cl * NS * F::NB;
                 RecState<FAM, PREC> st;
@@ -728,15 +748,17 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                     if (PREC == 1) st.prep32(P, lev, g32 + NS * F::NB);
                 }
                 unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
-                for (int s = 0; s < NS; ++s) {
+#pragma unroll 1
+                for (unsigned u = wm; u; u &= u - 1) {
+                    const int s = __ffs(u) - 1;
                     bool want = (m >> s) & 1;
-                    // lanes writing to the same child form a group: one shared atomic
-                    // per group, contiguous positions inside it
-                    unsigned grp = __match_any_sync(kFull, want ? cl * NS + s : -1);
+                    // lanes of one cell writing to the same child form a group: one
+                    // shared atomic per group, contiguous positions inside it
+                    unsigned grp = __ballot_sync(kFull, want) & run;
                     int leader = __ffs(grp) - 1;
                     unsigned base = 0;
                     if (want && lane == leader) base = atomicAdd(cnt + 3 * s + 2, (unsigned)__popc(grp));
-                    base = __shfl_sync(kFull, base, leader);
+                    base = __shfl_sync(kFull, base, want ? leader : lane);
                     if (!want) continue;
                     unsigned pos = cnt[3 * s + 1] + base + __popc(grp & ((1u << lane) - 1u));
                     int32_t qn[F::ND];
@@ -801,29 +823,24 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                 }
             } else {
                 unsigned ubm = act ? c.passmask[r - c.r0] : 0u;
-                bool uniform = __all_sync(kFull, !(act && ubm) || cl == cl0);
-#pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    if (s & ~smask) continue;
-                    bool want = act && ((ubm >> s) & 1);
+                const unsigned run = run_mask(r < t1 ? cl : -1, lane);
+#pragma unroll 1
+                for (unsigned u = __reduce_or_sync(kFull, ubm); u; u &= u - 1) {
+                    const int s = __ffs(u) - 1;
+                    bool want = (ubm >> s) & 1;
                     int ci = -1;
                     if (want) {
                         ci = c.child_idx[(size_t)cl * NS + s];
                         want = ci >= 0;
                     }
-                    unsigned bal = __ballot_sync(kFull, want);
-                    if (!bal) continue;
-                    unsigned pos = 0;
-                    if (uniform) {
-                        int ldr = __ffs(bal) - 1;
-                        unsigned base = 0;
-                        if (lane == ldr) base = atomicAdd(&c.cursor[(size_t)cl0 * NS + s], (unsigned)__popc(bal));
-                        base = __shfl_sync(kFull, base, ldr);
-                        pos = base + __popc(bal & ((1u << lane) - 1u));
-                    } else if (want) {
-                        pos = atomicAdd(&c.cursor[(size_t)cl * NS + s], 1u);
-                    }
+                    // one global atomic per (cell, child) group of lanes
+                    unsigned grp = __ballot_sync(kFull, want) & run;
+                    int ldr = __ffs(grp) - 1;
+                    unsigned base = 0;
+                    if (want && lane == ldr) base = atomicAdd(&c.cursor[(size_t)cl * NS + s], (unsigned)__popc(grp));
+                    base = __shfl_sync(kFull, base, want ? ldr : lane);
                     if (!want) continue;
+                    unsigned pos = base + __popc(grp & ((1u << lane) - 1u));
                     int32_t qn[F::ND];
                     child_qf<FAM, PREC>(P, lev, st, g32, g64, s, qn, nrechk, c.sc);
                     write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos);
