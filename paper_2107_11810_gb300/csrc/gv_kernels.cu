@@ -537,6 +537,23 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
     __shared__ unsigned s_xw[2 * NS];
     const int64_t t0 = c.r0 + (int64_t)blockIdx.x * TILE;
     const int64_t t1 = t0 + TILE < c.r1 ? t0 + TILE : c.r1;
+    // count pass: this thread's records are loaded first, so that their latency
+    // overlaps the tile's classification and the staging of the cell's geometry
+    int32_t pqf[EMIT ? 1 : RPT][F::ND], pqt[EMIT ? 1 : RPT][F::LE];
+    uint32_t pmult[EMIT ? 1 : RPT];
+    if (!EMIT) {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            int64_t r = t0 + threadIdx.x + k * 256;
+            if (r < t1) {
+#pragma unroll
+                for (int j = 0; j < F::ND; ++j) pqf[k][j] = c.in.qf[j][r];
+#pragma unroll
+                for (int m = 0; m < F::LE; ++m) pqt[k][m] = c.in.qt[m][r];
+                pmult[k] = c.in.mult[r];
+            }
+        }
+    }
     const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
     const int clast = (int)((int64_t)c.in.cell[t1 - 1] - c.c0);
     unsigned nrechk = 0, ntest = 0;
@@ -564,9 +581,9 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 int64_t r = t0 + threadIdx.x + k * 256;
-                if (r < t1) {                      // no break: loads of later records may issue early
+                if (r < t1) {
                     RecState<FAM, PREC> st;
-                    st.load(c.in, r);
+                    st.set(pqf[k], pqt[k], pmult[k]);
                     if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
                     else st.need64(P, lev);
                     unsigned ubm, lbm;
