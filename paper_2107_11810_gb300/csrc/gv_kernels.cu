@@ -537,21 +537,22 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
     __shared__ unsigned s_xw[2 * NS];
     const int64_t t0 = c.r0 + (int64_t)blockIdx.x * TILE;
     const int64_t t1 = t0 + TILE < c.r1 ? t0 + TILE : c.r1;
-    // count pass: this thread's records are loaded first, so that their latency
-    // overlaps the tile's classification and the staging of the cell's geometry
-    int32_t pqf[EMIT ? 1 : RPT][F::ND], pqt[EMIT ? 1 : RPT][F::LE];
-    uint32_t pmult[EMIT ? 1 : RPT];
-    if (!EMIT) {
+    // This thread's records (and, in the emit pass, their pass masks) are loaded
+    // first, so that their latency overlaps the tile's classification and the
+    // staging of the cell's geometry.
+    int32_t pqf[RPT][F::ND], pqt[RPT][F::LE];
+    uint32_t pmult[RPT], ppm[RPT];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
-            int64_t r = t0 + threadIdx.x + k * 256;
-            if (r < t1) {
+    for (int k = 0; k < RPT; ++k) {
+        int64_t r = t0 + threadIdx.x + k * 256;
+        ppm[k] = 0;
+        if (r < t1) {
 #pragma unroll
-                for (int j = 0; j < F::ND; ++j) pqf[k][j] = c.in.qf[j][r];
+            for (int j = 0; j < F::ND; ++j) pqf[k][j] = c.in.qf[j][r];
 #pragma unroll
-                for (int m = 0; m < F::LE; ++m) pqt[k][m] = c.in.qt[m][r];
-                pmult[k] = c.in.mult[r];
-            }
+            for (int m = 0; m < F::LE; ++m) pqt[k][m] = c.in.qt[m][r];
+            pmult[k] = c.in.mult[r];
+            if (EMIT) ppm[k] = c.passmask[r - c.r0];
         }
     }
     const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
@@ -636,7 +637,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                 int64_t r = t0 + threadIdx.x + k * 256;
                 unsigned m = 0;
                 if (r < t1) {
-                    m = c.passmask[r - c.r0];
+                    m = ppm[k];
 #pragma unroll
                     for (int s = 0; s < NS; ++s)
                         if (s_ci[s] < 0) m &= ~(1u << s);
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                 int64_t r = t0 + threadIdx.x + k * 256;
                 RecState<FAM, PREC> st;
                 if (m) {
-                    st.load(c.in, r);
+                    st.set(pqf[k], pqt[k], pmult[k]);
                     if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
                 }
                 // only the slots some lane of the warp writes; one copy of the body
@@ -732,7 +733,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                     int cl = (int)((int64_t)c.in.cell[r] - c.c0);
                     ck[k] = cl;
                     if (c.alive[cl]) {
-                        m = c.passmask[r - c.r0];
+                        m = ppm[k];
                         for (int s = 0; s < NS; ++s)
                             if (((m >> s) & 1) && c.child_idx[(size_t)cl * NS + s] < 0) m &= ~(1u << s);
                         unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
@@ -749,19 +750,18 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
                 s_span[3 * i + 2] = 0u;
             }
             __syncthreads();
-#pragma unroll 1
+#pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 unsigned m = em[k];
                 unsigned wm = __reduce_or_sync(kFull, m);
                 if (!wm) continue;                                  // uniform
-                int64_t r = t0 + threadIdx.x + k * 256;
                 const unsigned run = run_mask(ck[k], lane);
                 int cl = ck[k] < 0 ? cfirst : ck[k];
                 const float *g32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
                 const double *g64 = c.geo64 + (size_t)cl * NS * F::NB;
                 RecState<FAM, PREC> st;
                 if (m) {
-                    st.load(c.in, r);
+                    st.set(pqf[k], pqt[k], pmult[k]);
                     if (PREC == 1) st.prep32(P, lev, g32 + NS * F::NB);
                 }
                 unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
