@@ -294,7 +294,7 @@ static vote_status ensure_level(vote_ctx *c, int l, size_t recs, size_t cells) {
     if (recs > 0) {
         for (int j = 0; j < c->P.nd; ++j) TRY(ensure(c, s.qf[j], recs * 4));
         for (int m = 0; m < c->P.le; ++m) TRY(ensure(c, s.qt[m], recs * 4));
-        TRY(ensure(c, s.mult, recs * 4));
+        if (c->group) TRY(ensure(c, s.mult, recs * 4));   // without grouping every mult is 1
         TRY(ensure(c, s.cell, recs * 4));
     }
     if (cells > 0) {
@@ -311,7 +311,7 @@ static RecView rec_view(vote_ctx *c, int l) {
     std::memset(&v, 0, sizeof(v));
     for (int j = 0; j < c->P.nd; ++j) v.qf[j] = (int32_t *)c->ls[l].qf[j].p;
     for (int m = 0; m < c->P.le; ++m) v.qt[m] = (int32_t *)c->ls[l].qt[m].p;
-    v.mult = (uint32_t *)c->ls[l].mult.p;
+    v.mult = c->group ? (uint32_t *)c->ls[l].mult.p : nullptr;
     v.cell = (uint32_t *)c->ls[l].cell.p;
     return v;
 }
@@ -419,7 +419,7 @@ static vote_status expand_two(vote_ctx *c, int l, Chunk &ch, int64_t nr, int64_t
                        c->stream);
     ev_mark(c, VOTE_K_CHILDREN);
     CK(cudaGetLastError());
-    int rec_bytes = 4 * (P.nd + P.le + 2);
+    int rec_bytes = 4 * (P.nd + P.le + 1 + (c->group ? 1 : 0));
     c->kbytes[VOTE_K_TEST_COUNT] += (double)nr * (rec_bytes + 1 + ns);
     c->stats.launches += lev1.leaf_children ? 4 : 6;
     c->stats.cells += nc1;
@@ -576,7 +576,7 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     ch.prune = c->prune;
     ch.precision = c->precision;
 
-    int rec_bytes = 4 * (P.nd + P.le + 2);
+    int rec_bytes = 4 * (P.nd + P.le + 1 + (c->group ? 1 : 0));
     nr = g_r1 - g_r0;                 // records actually tested (after grouping)
     ev_mark(c, -1);
     launch_cell_geo(ch, c->stream);
@@ -692,7 +692,7 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         c->ls[0].nrecs = n;
         TRY(read_scalars(c));
         ev_collect(c);
-        c->kbytes[VOTE_K_LIFT] += (double)n * (8 * P.np + 4 * (P.nd + P.le + 2));
+        c->kbytes[VOTE_K_LIFT] += (double)n * (8 * P.np + 4 * (P.nd + P.le + 1 + (c->group ? 1 : 0)));
         if (c->h_sc->err) {
             set_err("surface parameters are not finite or out of the representable range");
             return VOTE_EINVAL;
@@ -949,6 +949,7 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
         w->chunk_records = c->chunk_records;
         w->two_level = c->two_level;
         w->dive = c->dive;
+        w->group = c->group;
         w->fault_alloc_at = 0;
     }
     std::vector<int64_t> wordoff(B + 1, 0);

@@ -63,7 +63,7 @@ __global__ void k_lift(Problem P, Level lev0, const double *__restrict__ prm, in
         bad |= !(fabs(q) < 1073741824.0);
         out.qt[m][i] = bad ? 0 : (int32_t)q;
     }
-    out.mult[i] = 1u;
+    if (out.mult) out.mult[i] = 1u;
     out.cell[i] = 0u;
     if (bad) atomicOr(&sc->err, 1u);
 }
@@ -105,40 +105,52 @@ __device__ __forceinline__ void parent_psi(const Problem &P, const Level &lev, u
     if (!F::LINEAR_BASIS) F::basis(cpar, psi);
 }
 
+// One thread per (cell, free-coordinate child slot fs); the 2^k threads of a cell
+// are consecutive lanes and combine their max |dpsi| by shuffles.
 template <int FAM>
 __global__ void k_cell_geo(Chunk c) {
     using F = Fam<FAM>;
     constexpr int NS = 1 << F::D;
     constexpr int NF = 1 << F::K;
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= c.nc) return;
+    static_assert(32 % NF == 0, "a cell's threads must lie in one warp");
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cell = gid / NF, fs = gid % NF;
+    const bool in = cell < c.nc;
     const Problem &P = c.P;
     const Level &lev = c.lev;
-    unsigned thr = prune_threshold(P, c.sc, c.prune);
-    c.alive[cell] = c.cells.ub[c.c0 + cell] >= thr ? 1 : 0;
-    uint64_t key = c.cells.key[c.c0 + cell];
-    double psi_par[F::NB];
-    parent_psi<FAM>(P, lev, key, psi_par);
     float mx[F::NB];
 #pragma unroll
     for (int m = 0; m < F::NB; ++m) mx[m] = 0.0f;
-    for (int fs = 0; fs < NF; ++fs) {
-        if (fs & ~lev.split_mask & (NF - 1)) continue;
-        double dpsi[F::NB];
-        child_dpsi<FAM>(P, lev, key, fs, psi_par, dpsi);
-        for (int s = fs; s < NS; s += NF) {          // dependent-coordinate bits share psi
-            if (s & ~lev.split_mask) continue;
-#pragma unroll
-            for (int m = 0; m < F::NB; ++m) {
-                c.geo64[((size_t)cell * NS + s) * F::NB + m] = dpsi[m];
-                c.geo32[((size_t)cell * (NS + 1) + s) * F::NB + m] = (float)dpsi[m];
-            }
+    if (in) {
+        if (fs == 0) {
+            unsigned thr = prune_threshold(P, c.sc, c.prune);
+            c.alive[cell] = c.cells.ub[c.c0 + cell] >= thr ? 1 : 0;
         }
+        if (!(fs & ~lev.split_mask & (NF - 1))) {
+            uint64_t key = c.cells.key[c.c0 + cell];
+            double psi_par[F::NB];
+            parent_psi<FAM>(P, lev, key, psi_par);
+            double dpsi[F::NB];
+            child_dpsi<FAM>(P, lev, key, fs, psi_par, dpsi);
+            for (int s = fs; s < NS; s += NF) {          // dependent-coordinate bits share psi
+                if (s & ~lev.split_mask) continue;
 #pragma unroll
-        for (int m = 0; m < F::NB; ++m) mx[m] = fmaxf(mx[m], fabsf((float)dpsi[m]));
+                for (int m = 0; m < F::NB; ++m) {
+                    c.geo64[((size_t)cell * NS + s) * F::NB + m] = dpsi[m];
+                    c.geo32[((size_t)cell * (NS + 1) + s) * F::NB + m] = (float)dpsi[m];
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < F::NB; ++m) mx[m] = fabsf((float)dpsi[m]);
+        }
     }
 #pragma unroll
-    for (int m = 0; m < F::NB; ++m) c.geo32[((size_t)cell * (NS + 1) + NS) * F::NB + m] = mx[m];
+    for (int o = 1; o < NF; o <<= 1)
+#pragma unroll
+        for (int m = 0; m < F::NB; ++m) mx[m] = fmaxf(mx[m], __shfl_xor_sync(kFull, mx[m], o));
+    if (in && fs == 0)
+#pragma unroll
+        for (int m = 0; m < F::NB; ++m) c.geo32[((size_t)cell * (NS + 1) + NS) * F::NB + m] = mx[m];
 }
 
 // ---------------------------------------------------------------------------
@@ -269,7 +281,7 @@ struct RecState {
         for (int j = 0; j < F::ND; ++j) qf[j] = in.qf[j][r];
 #pragma unroll
         for (int m = 0; m < F::LE; ++m) qt[m] = in.qt[m][r];
-        mult = in.mult[r];
+        mult = in.mult ? in.mult[r] : 1u;
         have64 = false;
     }
     __device__ __forceinline__ void set(const int32_t *qf_, const int32_t *qt_, uint32_t mult_) {
@@ -489,7 +501,7 @@ __device__ __forceinline__ void write_child(const Chunk &c, const RecState<FAM, 
     for (int j = 0; j < F::ND; ++j) c.out.qf[j][at] = qn[j];
 #pragma unroll
     for (int m = 0; m < F::LE; ++m) c.out.qt[m][at] = c.lev.st_ratio_log2[m] ? resnap_half(st.qt[m]) : st.qt[m];
-    c.out.mult[at] = st.mult;
+    if (c.out.mult) c.out.mult[at] = st.mult;
     c.out.cell[at] = (uint32_t)ci;
 }
 
@@ -551,7 +563,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
             for (int j = 0; j < F::ND; ++j) pqf[k][j] = c.in.qf[j][r];
 #pragma unroll
             for (int m = 0; m < F::LE; ++m) pqt[k][m] = c.in.qt[m][r];
-            pmult[k] = c.in.mult[r];
+            pmult[k] = c.in.mult ? c.in.mult[r] : 1u;
             if (EMIT) ppm[k] = c.passmask[r - c.r0];
         }
     }
@@ -1405,7 +1417,7 @@ void launch_lift(const Problem &P, const Level &lev0, const double *prm, int64_t
 
 void launch_cell_geo(const Chunk &c, cudaStream_t st) {
     if (c.nc <= 0) return;
-    GV_DISPATCH(c.P.fam, (k_cell_geo<FAMV><<<blocks_for(c.nc, 128), 128, 0, st>>>(c)));
+    GV_DISPATCH(c.P.fam, (k_cell_geo<FAMV><<<blocks_for((int64_t)c.nc << Fam<FAMV>::K, 64), 64, 0, st>>>(c)));
 }
 
 void launch_test(const Chunk &c, bool emit, cudaStream_t st) {

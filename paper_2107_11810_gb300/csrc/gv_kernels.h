@@ -10,7 +10,8 @@ namespace gv {
 // Records of one level, structure of arrays.  A record is one canonical surface
 // in one cell: q_f (free parameter, multiple of s_f), q_t (essential parameters,
 // multiples of the level's s_t), mult (originals merged into it), cell (index of
-// its cell in the level's cell arrays).
+// its cell in the level's cell arrays).  mult is NULL when every multiplicity
+// is 1 (no grouping): it is then neither stored nor read.
 struct RecView {
     int32_t *qf[GV_MAXD];
     int32_t *qt[GV_MAXT];
