@@ -89,11 +89,12 @@ typedef enum {
                                  context's stream (see vote_get_kernel_times)        */
     VOTE_OPT_BATCH_WORKERS = 10, /* host workers (streams) of vote_solve_batched, 1..32,
                                  default 4                                           */
-    VOTE_OPT_DIVE = 11,       /* 1 (default): before the sweep, expand one root-to-leaf
-                                 path that always takes the child with the largest
-                                 UB, so pruning starts from a leaf's count; 0: off.
-                                 Results do not depend on it (Sec. 3.3: any valid
-                                 bound may prune)                                    */
+    VOTE_OPT_DIVE = 11,       /* 1: before the sweep, expand one root-to-leaf path
+                                 that always takes the child with the largest UB, so
+                                 pruning starts from a leaf's count; 0: off; 2
+                                 (default): on for n >= 131072 surfaces.  Results do
+                                 not depend on it (Sec. 3.3: any valid bound may
+                                 prune)                                              */
     VOTE_OPT_TWO_LEVEL = 9    /* expand two levels per read of a chunk's records when
                                  its children would hold more than this many times
                                  its records (their records are then never written

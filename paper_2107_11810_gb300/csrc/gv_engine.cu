@@ -76,7 +76,7 @@ struct vote_ctx {
     int kernel_timing = 0;
     double two_level = 0.0;
     int batch_workers = 4;
-    int dive = 1;
+    int dive = 2;              // greedy dive: 0 off, 1 on, 2 on for n >= kDiveMinN
     int family = 0;
     double eps_in[GV_MAXD] = {}, bounds_in[2 * GV_MAXD] = {};
     std::vector<vote_ctx *> workers;   // sub-contexts of vote_solve_batched
@@ -647,6 +647,10 @@ static vote_status replay(vote_ctx *c, const double *surfaces, int64_t n, int la
     return VOTE_OK;
 }
 
+// Below this many surfaces the dive's per-level host round trips cost more than the
+// pruning they buy (the whole search is then a few chunks).
+static const int64_t kDiveMinN = 1 << 17;
+
 static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, double *best_point,
                                 int64_t *best_leaf, int64_t *depth, uint32_t *mask) {
     auto t0 = std::chrono::steady_clock::now();
@@ -697,7 +701,7 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
             set_err("surface parameters are not finite or out of the representable range");
             return VOTE_EINVAL;
         }
-        if (c->dive) {
+        if (c->dive == 1 || (c->dive == 2 && n >= kDiveMinN)) {
             // greedy dive: from the root, expand only the child with the largest UB
             // (the first on ties) down to the leaves, so the sweep starts with a
             // leaf's count as its pruning bound
@@ -880,7 +884,7 @@ vote_status vote_set_option(vote_ctx *c, int key, double v) {
         c->batch_workers = (int)v;
         return VOTE_OK;
     case VOTE_OPT_DIVE:
-        if (v != 0 && v != 1) break;
+        if (v != 0 && v != 1 && v != 2) break;
         c->dive = (int)v;
         return VOTE_OK;
 
