@@ -105,3 +105,41 @@ def test_exact_recursion_sees_merges():
            for l, c, u, b in zip(to["level"], to["coords"], to["ub"], to["lb"])}
     assert got == trace
     assert o["depth"] == best["ub"] >= 14          # the 7 duplicated surfaces count twice
+
+
+# Planted mistakes that only move a margin or a tie: the brute-force pins can miss
+# them (they change results only near a decision), the exact per-cell comparison
+# must not.  The level constants and root records still come from the unmodified
+# oracle, so only the recursion is under test.
+EXACT_MUTANTS = {
+    "ub_radius_without_A": ("R = R + p->A[l + 1][j];", "R = R + 0.0 * p->A[l + 1][j];"),
+    "lb_radius_without_A": ("double rl = p->eps[jj] - p->A[l + 1][j];", "double rl = p->eps[jj];"),
+    "snap_t_half_away": ("double q = rint(r->t[m] / p->s_t[l][m]);", "double q = round(r->t[m] / p->s_t[l][m]);"),
+    "merge_keeps_one_mult": ("for (int64_t x = a; x < b; ++x) mult += recs[idx[x]].mult;",
+                             "mult = recs[idx[a]].mult;"),
+}
+
+
+def _oracle_trace(p, lib):
+    o = oracle.solve(p.family, p.eps, p.bounds, p.params, flags=oracle.NO_PRUNE, trace_cap=2_000_000, lib=lib)
+    to = o["trace"]
+    return {(int(l), tuple(int(x) for x in c)): (int(u), int(b))
+            for l, c, u, b in zip(to["level"], to["coords"], to["ub"], to["lb"])}
+
+
+@pytest.mark.parametrize("name", sorted(EXACT_MUTANTS))
+def test_exact_pin_catches_margin_and_tie_mistakes(name):
+    old, new = EXACT_MUTANTS[name]
+    src = oracle.source()
+    assert src.count(old) == 1, name
+    lib = oracle.load_variant(src.replace(old, new), "exact_" + name)
+    caught = False
+    for n, seed in ((40, 31), (50, 32)):
+        p = inputs.line2d(n=n, inlier_frac=0.3, eps=0.02, seed=seed)
+        if name == "merge_keeps_one_mult":
+            p = dataclasses.replace(p, params=np.concatenate([p.params, p.params[:, :9]], axis=1))
+        trace, _ = exact_search(p)
+        if _oracle_trace(p, lib) != trace:
+            caught = True
+            break
+    assert caught, f"mutant {name} survived the exact pin"

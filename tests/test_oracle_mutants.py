@@ -4,7 +4,9 @@ Limit of these pins: a mistake that only tightens a conservative margin (for
 example dropping the canonization error A from the UB radius, or shrinking one
 Lipschitz term that the others dominate) changes a result only for surfaces
 within that margin of a decision, which random instances rarely produce; the
-level-structure pin still checks A itself.
+level-structure pin still checks A itself, and for lines the exact-rational pin
+(tests/test_oracle_exact_line.py) catches such margin and rounding-tie mistakes
+cell by cell.
 
 Each mutant is a copy of oracle/gv_oracle.c with one plausible mistake -- a
 dropped term, a wrong sign, a wrong index, a transposed operand -- compiled
