@@ -205,7 +205,7 @@ def run_batched(args, rank, world, w):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    times, lats = [], []
+    times, lats, launches = [], [], 0
     with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
         for _ in range(args.steps):
             torch.cuda.synchronize()
@@ -214,6 +214,7 @@ def run_batched(args, rank, world, w):
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             lats.extend(res["latency_ms"].tolist())
+            launches += int(s.stats()["launches"])
     total = sum(times)
     if world > 1:
         t = torch.tensor([total], dtype=torch.float64, device="cuda")
@@ -231,7 +232,7 @@ def run_batched(args, rank, world, w):
                config=dict(workload=args.workload, desc=w["desc"], problems=len(probs),
                            total_n=int(sum(p.n for p in probs)), l2="inputs and working set larger than L2"),
                latency_ms=dict(p50=float(np.percentile(lats, 50)), p99=float(np.percentile(lats, 99))),
-               gpu_launches=None, clocks=clk.summary(),
+               gpu_launches=launches, clocks=clk.summary(),
                e2e=dict(value=len(local) / e2e_t, unit="problems/s", h2d_bytes_per_step=int(flat.nbytes),
                         d2h_bytes_per_step=int(words.numel() * 4)))
     if rank == 0:

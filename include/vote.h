@@ -220,7 +220,8 @@ vote_status vote_levels(vote_ctx *ctx, int *L, int *Lj);
 vote_status vote_get_trace(vote_ctx *ctx, int64_t cap, int32_t *level, int64_t *coords,
                            int64_t *ub, int64_t *lb, int64_t *count);
 
-/* Counters of the last solve. */
+/* Counters of the last solve; after vote_solve_batched, totals over the whole
+ * batch (levels and peak_records: the largest over its problems). */
 vote_status vote_get_stats(vote_ctx *ctx, vote_stats *out);
 
 /* Per kernel class (VOTE_K_*): summed device milliseconds, launches and

@@ -963,6 +963,8 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
     std::atomic<int> failed(0);
     std::vector<vote_status> wst(nw, VOTE_OK);
     std::vector<std::string> wmsg(nw);
+    std::vector<vote_stats> wsum((size_t)nw);   // per worker: totals over its problems
+    for (auto &x : wsum) std::memset(&x, 0, sizeof(x));
     auto t0 = std::chrono::steady_clock::now();
     auto work = [&](int wi) {
         vote_ctx *w = c->workers[wi];
@@ -982,6 +984,17 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
             }
             if (latency_ms)
                 latency_ms[b] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            vote_stats &a = wsum[wi];
+            const vote_stats &e = w->stats;
+            a.levels = e.levels > a.levels ? e.levels : a.levels;
+            a.cells += e.cells;
+            a.records += e.records;
+            a.tests += e.tests;
+            a.rechecks += e.rechecks;
+            a.chunks += e.chunks;
+            a.leaves += e.leaves;
+            a.peak_records = e.peak_records > a.peak_records ? e.peak_records : a.peak_records;
+            a.launches += e.launches;
         }
     };
     std::vector<std::thread> th;
@@ -994,6 +1007,18 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
             set_err("%s", wmsg[i].c_str());
             return wst[i];
         }
+    }
+    for (int i = 0; i < nw; ++i) {                  // statistics of the whole batch
+        const vote_stats &a = wsum[i];
+        c->stats.levels = a.levels > c->stats.levels ? a.levels : c->stats.levels;
+        c->stats.cells += a.cells;
+        c->stats.records += a.records;
+        c->stats.tests += a.tests;
+        c->stats.rechecks += a.rechecks;
+        c->stats.chunks += a.chunks;
+        c->stats.leaves += a.leaves;
+        c->stats.peak_records = a.peak_records > c->stats.peak_records ? a.peak_records : c->stats.peak_records;
+        c->stats.launches += a.launches;
     }
     c->stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return VOTE_OK;

@@ -36,6 +36,15 @@ def test_batched_equals_single_solves_and_oracle(workers):
         w0, nw = res["word_offsets"][b], (p.n + 31) // 32
         assert np.array_equal(masks[w0:w0 + nw], o["mask"])
     assert np.all(res["latency_ms"] > 0)
+    # the batch's counters are the totals of the problems' own solves
+    s1 = vote.Solver(p0.family, p0.eps, p0.bounds)
+    tests = launches = 0
+    for p in probs:
+        s1.solve(torch.from_numpy(np.ascontiguousarray(p.params)).cuda())
+        tests += s1.stats()["tests"]
+        launches += s1.stats()["launches"]
+    st = s.stats()
+    assert st["tests"] == tests and st["launches"] == launches > 0
 
 
 def test_batched_rejects_bad_offsets():
