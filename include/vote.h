@@ -74,7 +74,11 @@ typedef enum {
     VOTE_OPT_PRECISION = 1,   /* 0 = plain FP64 predicate; 1 = FP32 screen with FP64
                                  recheck of the borderline band (default 1)          */
     VOTE_OPT_PRUNE = 2,       /* 1 = prune cells with UB < best LB (default); 0 = off */
-    VOTE_OPT_CHUNK_RECORDS = 3, /* records processed per expansion step (default 2^23) */
+    VOTE_OPT_CHUNK_RECORDS = 3, /* records processed per expansion step; default 2^27
+                                 for planes (their pruning hardly depends on the
+                                 step size, so larger steps only save per-step
+                                 overhead), 2^25 for the other families (finer
+                                 depth-first steps keep their pruning effective)    */
     VOTE_OPT_TRACE_CAP = 4,   /* >0: record (level, coords, UB, LB) of every tested
                                  child, up to this many entries (debug; default 0)   */
     VOTE_OPT_GROUP = 5,       /* merging of identical canonical surfaces:
