@@ -396,7 +396,7 @@ def main():
 
 # tests per full problem measured by the GPU path (used to scale the reference
 # arm's oracle sample to problems/s); refreshed from bench runs
-REF_TESTS = {"plane3d_n1e6": 1.0475601933066e13, "pose3dof_n1e6": 3.030014590e9, "line2d_n1e4": 8.324422e6}
+REF_TESTS = {"plane3d_n1e6": 1.0476383009996e13, "pose3dof_n1e6": 3.030014590e9, "line2d_n1e4": 8.324422e6}
 
 if __name__ == "__main__":
     main()
