@@ -23,6 +23,7 @@ CANDIDATES = [
     dict(chunk_records=1 << 23, two_level=0.0),
     dict(chunk_records=1 << 25, two_level=0.0),
     dict(chunk_records=1 << 26, two_level=0.0),
+    dict(chunk_records=1 << 27, two_level=0.0),
     dict(chunk_records=1 << 25, two_level=2.0),
 ]
 

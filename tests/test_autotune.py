@@ -30,7 +30,7 @@ def test_buckets_and_keys():
 def test_tune_picks_fastest_and_caches(tmp_path):
     path = str(tmp_path / "cache.json")
     s = FakeSolver()
-    cost = {1 << 23: 3.0, 1 << 25: 1.0, 1 << 26: 2.0}
+    cost = {1 << 23: 3.0, 1 << 25: 1.0, 1 << 26: 2.0, 1 << 27: 2.5}
 
     def timer(solver, x):
         return cost[solver.opts[3]] + (0.5 if solver.opts[9] else 0.0)
