@@ -18,6 +18,10 @@ Functions and the passages they follow:
     error (Sec. 3.2, "Canonization" and the eps-update discussion).
   * :func:`vsin` / :func:`vcos` -- the sine/cosine used for cell-centre basis
     values (Taylor series with Cody-Waite reduction).
+  * :func:`sigma`, :func:`lipschitz`, :func:`path_records` -- the margin functions
+    behind the canonization error bound and the surface-box test (Sec. 3.2), and
+    the canonical records of one surface along a root-to-cell path, exported so
+    that tests can check them against the surface equations.
 
 Pins (tests/test_oracle_*.py): brute-force depth on dense grids, the exact
 arrangement maximum for lines, planted inliers, the approximation guarantee,
@@ -72,6 +76,12 @@ def _declare(lib):
     lib.gvo_solve.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P, i64, P, P, P, P, P, P]
     lib.gvo_cell_counts.restype = i32
     lib.gvo_cell_counts.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P]
+    lib.gvo_sigma.restype = i32
+    lib.gvo_sigma.argtypes = [i32, i32, i32, P, P]
+    lib.gvo_lipschitz.restype = i32
+    lib.gvo_lipschitz.argtypes = [i32, i32, i32, P, P]
+    lib.gvo_path_records.restype = i32
+    lib.gvo_path_records.argtypes = [i32, i32, i32, P, P, P, i64, i64, i32, P, P, P]
     return lib
 
 
@@ -91,23 +101,7 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            i64, i32 = ctypes.c_int64, ctypes.c_int
-            lib.gvo_vsin.restype = ctypes.c_double
-            lib.gvo_vsin.argtypes = [ctypes.c_double]
-            lib.gvo_vcos.restype = ctypes.c_double
-            lib.gvo_vcos.argtypes = [ctypes.c_double]
-            lib.gvo_levels.restype = i32
-            lib.gvo_levels.argtypes = [i32, i32, i32, P, P, P, P, P, P, P]
-            lib.gvo_root_records.restype = i32
-            lib.gvo_root_records.argtypes = [i32, i32, i32, P, P, P, i64, P, P]
-            lib.gvo_solve.restype = i32
-            lib.gvo_solve.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P,
-                                      i64, P, P, P, P, P, P]
-            lib.gvo_cell_counts.restype = i32
-            lib.gvo_cell_counts.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P]
-            _lib = lib
+            _lib = _declare(ctypes.CDLL(build()))
     return _lib
 
 
@@ -218,3 +212,42 @@ def cell_counts(family, eps, bounds, params, level, coords, want_reach=False):
 def mask_to_indices(mask: np.ndarray, n: int) -> np.ndarray:
     bits = np.unpackbits(mask.view(np.uint8), bitorder="little")[:n]
     return np.nonzero(bits)[0]
+
+
+def sigma(family, h, lib=None):
+    """sigma_m: the oracle's bound on the change of basis function m across a cell
+    of half-widths h[d] (it sets the essential-parameter snap steps and the
+    canonization error bound, Sec. 3.2)."""
+    d, k, le, _ = FAMILY_SHAPE[family]
+    h = np.ascontiguousarray(h, dtype=np.float64).reshape(d)
+    out = np.zeros(le)
+    if (lib or _load()).gvo_sigma(family, d, k, _ptr(h), _ptr(out)):
+        raise ValueError("invalid family")
+    return out
+
+
+def lipschitz(family, t, lib=None):
+    """Lambda[j, i]: the oracle's bound on |dF_j/dx_i| for essential parameters t
+    (the free-coordinate term of the surface-box test, Sec. 3.2)."""
+    d, k, le, _ = FAMILY_SHAPE[family]
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(le)
+    out = np.zeros((d - k) * k)
+    if (lib or _load()).gvo_lipschitz(family, d, k, _ptr(t), _ptr(out)):
+        raise ValueError("invalid family")
+    return out.reshape(d - k, k)
+
+
+def path_records(family, eps, bounds, params, i, level, coords, lib=None):
+    """Canonical record (f[d-k], t[le]) of original surface i after the snap at each
+    level of the path from the root to cell (level, coords), as long as the record
+    reaches that level's cell.  Returns (f[m, d-k], t[m, le]), m <= level."""
+    d, k, le, eps, bounds, params = _prep(family, eps, bounds, params)
+    n = params.shape[1]
+    coords = np.ascontiguousarray(coords, dtype=np.int64).reshape(d)
+    f = np.zeros((max(level, 1), d - k))
+    t = np.zeros((max(level, 1), le))
+    m = (lib or _load()).gvo_path_records(family, d, k, _ptr(eps), _ptr(bounds), _ptr(params), n, int(i),
+                                           int(level), _ptr(coords), _ptr(f), _ptr(t))
+    if m < 0:
+        raise ValueError("invalid input")
+    return f[:m], t[:m]

@@ -765,3 +765,68 @@ int gvo_cell_counts(int fam, int d, int k, const double *eps, const double *boun
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Margin functions and canonical records along a path, exported so that the */
+/* tests can check the bounds they rest on against the surface equations.    */
+/* ------------------------------------------------------------------------- */
+
+/* sigma[le]: the bound family_sigma gives for a cell of half-widths h[d]. */
+int gvo_sigma(int fam, int d, int k, const double *h, double *sigma)
+{
+    gvo_problem p;
+    memset(&p, 0, sizeof(p));
+    if (family_shape(fam, d, k, &p.le, &p.np)) return 1;
+    p.fam = fam; p.d = d; p.k = k; p.nd = d - k;
+    family_sigma(&p, h, sigma);
+    return 0;
+}
+
+/* lam[(d-k)*k]: the Lipschitz bounds family_lipschitz gives for the essential
+ * parameters t[le] (dependent coordinate j, free coordinate i at j*k + i). */
+int gvo_lipschitz(int fam, int d, int k, const double *t, double *lam)
+{
+    gvo_problem p;
+    memset(&p, 0, sizeof(p));
+    if (family_shape(fam, d, k, &p.le, &p.np)) return 1;
+    p.fam = fam; p.d = d; p.k = k; p.nd = d - k;
+    family_lipschitz(&p, t, lam);
+    return 0;
+}
+
+/* The canonical record of original surface i at every level of the path from the
+ * root to the cell (level lam, coords ct), as replay_one forms it: f[l*(d-k)+j]
+ * and t[l*le+m] after the snap at level l.  Returns the number of levels at which
+ * the record exists (it reached the level-l cell of the path), or -1 on invalid
+ * input. */
+int gvo_path_records(int fam, int d, int k, const double *eps, const double *bounds, const double *params,
+                     int64_t n, int64_t i, int lam, const int64_t *ct, double *f, double *t)
+{
+    gvo_problem p;
+    if (problem_init(&p, fam, d, k, eps, bounds) || check_inputs(&p, params, n)) return -1;
+    if (i < 0 || i >= n || lam < 0 || lam > p.L) return -1;
+    for (int j = 0; j < d; ++j)
+        if (ct[j] < 0 || ct[j] >= ((int64_t)1 << splits(&p, lam, j))) return -1;
+    gvo_rec r;
+    int64_t key[GVO_MAXD + GVO_MAXT];
+    family_lift(&p, params, n, i, &r);
+    for (int l = 0; l < lam; ++l) {
+        int64_t ci[GVO_MAXD];
+        int b = 0;
+        for (int j = 0; j < p.d; ++j) {
+            ci[j] = ct[j] >> (splits(&p, lam, j) - splits(&p, l, j));
+            if (l < p.Lj[j]) b |= (int)((ct[j] >> (splits(&p, lam, j) - splits(&p, l + 1, j))) & 1) << j;
+        }
+        snap_record(&p, l, &r, key);
+        for (int j = 0; j < p.nd; ++j) f[l * p.nd + j] = r.f[j];
+        for (int m = 0; m < p.le; ++m) t[l * p.le + m] = r.t[m];
+        double psi[GVO_MAXT];
+        family_basis(&p, l, ci, psi);
+        gvo_child g;
+        child_geometry(&p, l, ci, psi, b, &g);
+        double fo[GVO_MAXD];
+        if (!(proximity_test(&p, l, &r, &g, fo) & 1)) return l + 1;
+        for (int j = 0; j < p.nd; ++j) r.f[j] = fo[j];
+    }
+    return lam;
+}

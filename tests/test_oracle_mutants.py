@@ -1,12 +1,12 @@
 """Planted mistakes in the oracle (on the CPU) must be caught by the pins.
 
-Limit of these pins: a mistake that only tightens a conservative margin (for
-example dropping the canonization error A from the UB radius, or shrinking one
-Lipschitz term that the others dominate) changes a result only for surfaces
-within that margin of a decision, which random instances rarely produce; the
-level-structure pin still checks A itself, and for lines the exact-rational pin
-(tests/test_oracle_exact_line.py) catches such margin and rounding-tie mistakes
-cell by cell.
+A mistake that only tightens a conservative margin (for example dropping the
+canonization error A from the UB radius, or shrinking one Lipschitz term that
+the others dominate) changes a result only for surfaces within that margin of a
+decision, which random instances rarely produce.  Such mistakes are caught by
+the margin pins (tests/margins.py: sigma, Lambda and the accumulated error A
+checked against the surface equations on the workloads' level structures) and,
+for lines, by the exact-rational pin (tests/test_oracle_exact_line.py).
 
 Each mutant is a copy of oracle/gv_oracle.c with one plausible mistake -- a
 dropped term, a wrong sign, a wrong index, a transposed operand -- compiled
@@ -19,6 +19,7 @@ import numpy as np
 import pytest
 
 import brute
+import margins
 import oracle
 from paper_2107_11810_gb300 import inputs
 
@@ -36,6 +37,17 @@ MUTANTS = {
                          "g->shift[j] = bit ? -p->h[l + 1][j] : p->h[l + 1][j];"),
     "pose_basis_swap": ("psi[0] = gvo_vcos(yaw);\n        psi[1] = gvo_vsin(yaw);",
                         "psi[0] = gvo_vsin(yaw);\n        psi[1] = gvo_vcos(yaw);"),
+    # margin-only mistakes (the brute-force pins alone let these through)
+    "plane_sigma_without_phi": ("sigma[0] = h[0] + h[1];\n        sigma[1] = h[0] + h[1];",
+                                "sigma[0] = h[0];\n        sigma[1] = h[0] + h[1];"),
+    "plane_lipschitz_phi_from_qz": ("lam[1] = sqrt(t[0] * t[0] + t[1] * t[1]);",
+                                    "lam[1] = fabs(t[2]);"),
+    "pose_lipschitz_max_component": ("lam[0] = r;\n        lam[1] = r;",
+                                     "lam[0] = fmax(fabs(t[0]), fabs(t[1]));\n        lam[1] = lam[0];"),
+    "pose_sigma_halved": ("sigma[0] = h[0];\n        sigma[1] = h[0];\n        break;\n    }\n}",
+                          "sigma[0] = 0.5 * h[0];\n        sigma[1] = 0.5 * h[0];\n        break;\n    }\n}"),
+    "error_step_missing_essential_term": ("delta = delta + (p->s_t[l][m] * 0.5) * sigma[m];",
+                                          "delta = delta + (p->s_t[l][m] * 0.25) * sigma[m];"),
 }
 
 CASES = {
@@ -82,11 +94,37 @@ def pins_hold(lib, fam, seed):
     return bool(np.all(np.abs(res) <= ep))
 
 
+MARGIN_CASES = {
+    inputs.LINE2D: lambda: inputs.line2d(n=200, seed=inputs.SEED_BASE),
+    inputs.PLANE3D_SPH: lambda: inputs.plane3d(n=200, seed=inputs.SEED_BASE + 1),
+    inputs.POSE3DOF: lambda: inputs.pose3dof(n=200, seed=inputs.SEED_BASE + 2),
+}
+MARGIN_T = {
+    inputs.LINE2D: [np.array([1.0]), np.array([0.3])],
+    inputs.PLANE3D_SPH: [np.array(v, float) for v in ([1, 1, 0], [0.2, 0.9, 0.4], [1, 1, 1])],
+    inputs.POSE3DOF: [np.array(v, float) for v in ([50, 50], [-30, 80], [100, 0])],
+}
+
+
+def margins_hold(lib, fam):
+    """The margin pins (sigma, Lambda, accumulated error A) on the workload's level
+    structure, with fewer samples than tests/test_oracle_margins.py; False if any fails."""
+    p = MARGIN_CASES[fam]()
+    if np.any(margins.check_sigma(p, cells_per_level=2, points=20_000, seed=1, lib=lib) > 1.0):
+        return False
+    if np.any(margins.check_lipschitz(p, MARGIN_T[fam], cells_per_level=2, points=5_000, seed=3, lib=lib)
+              > 1.0 + 1e-12):
+        return False
+    reached, worst = margins.check_records(p, surfaces=25, points=1000, seed=4, lib=lib)
+    return reached and worst <= 1.0
+
+
 def test_unmodified_oracle_passes_the_pins():
     src = oracle.source()
     lib = oracle.load_variant(src, "identity")
     for fam in CASES:
         assert pins_hold(lib, fam, 1)
+        assert margins_hold(lib, fam)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -95,5 +133,16 @@ def test_planted_mistake_is_caught(name):
     src = oracle.source()
     assert src.count(old) == 1, name
     lib = oracle.load_variant(src.replace(old, new), name)
-    caught = any(not pins_hold(lib, fam, seed) for fam in CASES for seed in (1, 2, 3))
+    caught = any(not margins_hold(lib, fam) for fam in CASES) or \
+        any(not pins_hold(lib, fam, seed) for fam in CASES for seed in (1, 2, 3))
     assert caught, f"mutant {name} survived the pins"
+
+
+@pytest.mark.parametrize("name", [m for m in sorted(MUTANTS) if m.startswith(("plane_sigma", "plane_lipschitz",
+                                                                               "pose_lipschitz", "pose_sigma",
+                                                                               "error_step"))])
+def test_margin_mistake_is_caught_by_the_margin_pins(name):
+    old, new = MUTANTS[name]
+    src = oracle.source()
+    lib = oracle.load_variant(src.replace(old, new), name)
+    assert any(not margins_hold(lib, fam) for fam in CASES), f"margin mutant {name} survived the margin pins"
