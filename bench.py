@@ -6,9 +6,12 @@ like the paper's workloads; the default is 3D plane fitting with 1,000,000
 points (2 % on a plane, eps = 0.005, (theta, phi, d) space).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                    [--impl gv|reference]
+                    [--impl gv|reference] [--no-fp64] [--no-cpu]
 
-Prints one JSON line (rank 0).  Under torchrun every rank solves its own copy
+After the timed steps, one plain-FP64 solve of the same workload checks that the
+two precision modes give identical results and times it (the metric's
+comparison); the oracle (plain FP64 C on the host cores) is timed on a bounded
+sample.  Prints one JSON line (rank 0).  Under torchrun every rank solves its own copy
 of the problem (independent problems, no collective): weak scaling.
 """
 from __future__ import annotations
@@ -40,6 +43,10 @@ WORKLOADS = {
                           "eps 0.25 m / 0.5 deg, (yaw,x,y) space"),
     "line2d_n1e4": dict(make=lambda: inputs.line2d(), desc="2D line fitting, 1e4 points, 10% inliers, eps 0.01, "
                         "(m,b) space"),
+    "plane3d_n1e5": dict(make=lambda: inputs.plane3d(n=100_000), desc="3D plane fitting, 1e5 points (the plane "
+                         "workload's shape at a tenth of its size; a small target for profiler captures)"),
+    "pose3dof_n3e5": dict(make=lambda: inputs.pose3dof(n=300_000), desc="3DoF camera voting, 3e5 matches (a small "
+                          "target for profiler captures)"),
     "pose3dof_batch256": dict(make=lambda: inputs.pose3dof_batch(), batched=True,
                               desc="256 independent 3DoF problems, n log-uniform in [1e3, 1e6], inlier ratio "
                                    "U[0.5%, 5%]; one vote_solve_batched call per step"),
@@ -135,21 +142,28 @@ def recorded_traffic(kernel: str, family: str, algorithmic_bytes_per_launch: flo
 
 
 def oracle_sample(p, budget_s: float):
-    """The oracle (plain FP64 C, one core) on a bounded sample of the workload: the
-    first n_s surfaces, n_s grown until one solve takes about budget_s/4 seconds.
-    Returns (tests per second, seconds, n_s, tests)."""
+    """The oracle (plain FP64 C) on a bounded sample of the workload: the first n_s
+    surfaces, n_s grown until one single-thread solve takes about budget_s/4
+    seconds; then the same sample on every host core (OpenMP over subtrees).
+    Returns dict(single=(tests/s, s), multi=(tests/s, s, threads), n_s, tests)."""
     import oracle
     n_s = 200
-    last = None
     while True:
         sub = np.ascontiguousarray(p.params[:, :n_s])
         t0 = time.perf_counter()
         r = oracle.solve(p.family, p.eps, p.bounds, sub)
         dt = time.perf_counter() - t0
-        last = (r["stats"][0] / dt, dt, n_s, int(r["stats"][0]))
         if dt > budget_s / 4 or n_s >= p.n:
-            return last
+            break
         n_s = min(p.n, int(n_s * max(1.5, min(8.0, (budget_s / 4) / max(dt, 1e-3)))))
+    tests = int(r["stats"][0])
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    rp = oracle.solve_parallel(p.family, p.eps, p.bounds, sub, threads=cores)
+    dtp = time.perf_counter() - t0
+    assert rp["depth"] == r["depth"]
+    # the parallel run prunes differently; its rate is taken on the serial test count
+    return dict(single=(tests / dt, dt), multi=(tests / dtp, dtp, int(rp["stats"][4])), n_s=n_s, tests=tests)
 
 
 def run_reference(args, rank, world):
@@ -160,15 +174,17 @@ def run_reference(args, rank, world):
     p = w["make"]()
     import oracle
     oracle.build()
-    tps, dt, n_s, tests = oracle_sample(p, 8.0)
+    smp = oracle_sample(p, 8.0)
+    n_s, tests = smp["n_s"], smp["tests"]
+    cores = os.cpu_count() or 1
     gpu_tests = args.ref_tests_per_problem
     sub = np.ascontiguousarray(p.params[:, :n_s])
     for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle.solve(p.family, p.eps, p.bounds, sub)
+        oracle.solve_parallel(p.family, p.eps, p.bounds, sub, threads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = oracle.solve(p.family, p.eps, p.bounds, sub)
+        oracle.solve_parallel(p.family, p.eps, p.bounds, sub, threads=cores)
         times.append(time.perf_counter() - t0)
     tps = tests / statistics.mean(times)
     # scale: problems/s = oracle tests/s / tests one full-size problem needs
@@ -179,9 +195,12 @@ def run_reference(args, rank, world):
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=args.workload, desc=w["desc"]),
                 tests_per_s=tps,
-                cpu_baseline=dict(value=value, unit="problems/s", cores=1, kind="oracle",
-                                  sample=f"oracle solve of the first {n_s} of {p.n} surfaces ({tests} tests); "
-                                         f"problems/s = oracle tests/s / {gpu_tests} tests per full problem"),
+                cpu_baseline=dict(value=value, unit="problems/s", cores=cores, kind="oracle",
+                                  sample=f"oracle (OpenMP over subtrees, {cores} threads) solving the first {n_s} "
+                                         f"of {p.n} surfaces ({tests} tests); problems/s = oracle tests/s / "
+                                         f"{gpu_tests} tests per full problem",
+                                  single_thread=dict(value=smp["single"][0] / gpu_tests if gpu_tests else None,
+                                                     tests_per_s=smp["single"][0], cores=1)),
                 e2e=dict(value=value, unit="problems/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -247,9 +266,9 @@ def main():
     ap.add_argument("--impl", default="gv", choices=["gv", "reference"])
     ap.add_argument("--workload", default="plane3d_n1e6", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--fp64", action="store_true",
-                    help="also time the plain-FP64 predicate path on the same workload and check identical results "
-                         "(FP64 runs at a small fraction of the FP32 rate on GB300: ~400 s for the plane workload)")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the plain-FP64 predicate solve of the same workload that follows the timed steps "
+                         "(the metric's comparison: FP32 screen + FP64 recheck vs plain FP64, identical results)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--ref-tests-per-problem", type=float, default=0.0)
@@ -323,10 +342,12 @@ def main():
     if dom == "test_count" and args.precision == 1:
         instr = INSTR_PER_TEST[p.family] * tests_per_problem * args.steps / max(nl, 1)
         achieved = instr / avg_s / 1e12
-        alu_peak = 152 * 128 * pk["sm_max_mhz"] * 1e6 / 1e12
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        alu_peak = sms * 128 * pk["sm_max_mhz"] * 1e6 / 1e12
         roof = dict(bound="alu", achieved=achieved, peak=alu_peak, unit="TFP32-instr/s",
                     frac=achieved / alu_peak, kernel="k_test<count>",
-                    peak_src="152 SMs x 128 FP32 lanes x max SM clock (instructions/s, no FMA doubling)",
+                    peak_src=f"{sms} SMs (device property) x 128 FP32 lanes x {pk['sm_max_mhz']:.0f} MHz max SM "
+                             f"clock ({pk['src']}); thread instructions/s, no FMA doubling",
                     traffic=recorded_traffic("k_test_count", inputs.FAMILY_NAMES[p.family], by / max(nl, 1)),
                     bytes_per_launch=by / max(nl, 1))
     else:
@@ -361,9 +382,9 @@ def main():
                result=dict(depth=depth, best_leaf=leaf, best_point=r["best_point"].tolist()),
                gpu_launches=launches, roofline=roof, e2e=e2e, clocks=clk.summary(),
                kernel_ms={k: round(v[0] / args.steps, 3) for k, v in kt.items() if v[1]})
-    if not args.fp64:
-        out["fp64_plain"] = dict(skipped="run with --fp64 (one plain-FP64 solve of the same workload)")
-    if args.fp64 and args.precision == 1:
+    if args.no_fp64:
+        out["fp64_plain"] = dict(skipped="--no-fp64")
+    elif args.precision == 1:
         s.set_option(vote.VOTE_OPT_PRECISION, 0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -375,18 +396,26 @@ def main():
         same = (r64["depth"] == depth and r64["best_leaf"].tolist() == leaf and
                 torch.equal(r64["mask"], r["mask"]))
         out["fp64_plain"] = dict(value=1.0 / t64, unit="problems/s", tests_per_s=s.stats()["tests"] / t64,
-                                 identical_results=bool(same), speedup_fp32_screen=value / world * t64)
+                                 seconds=t64, identical_results=bool(same),
+                                 speedup_fp32_screen=value / world * t64,
+                                 note="one plain-FP64 solve of the same workload after the timed steps")
         s.set_option(vote.VOTE_OPT_PRECISION, 1)
     if rank == 0 and not args.no_cpu:
         try:
-            tps, dt, n_s, ot = oracle_sample(p, 16.0)
-            out["cpu_baseline"] = dict(value=tps / tests_per_problem, unit="problems/s", cores=1, kind="oracle",
+            smp = oracle_sample(p, 16.0)
+            tps, dtp, thr = smp["multi"]
+            out["cpu_baseline"] = dict(value=tps / tests_per_problem, unit="problems/s", cores=thr, kind="oracle",
                                        tests_per_s=tps,
-                                       sample=f"oracle solve of the first {n_s} of {p.n} surfaces "
-                                              f"({ot} tests, {dt:.1f} s); problems/s = oracle tests/s / "
-                                              f"{tests_per_problem:.4g} tests per full problem (GPU count)")
+                                       sample=f"oracle solve of the first {smp['n_s']} of {p.n} surfaces "
+                                              f"({smp['tests']} tests; {dtp:.1f} s on {thr} threads, OpenMP over "
+                                              f"subtrees); problems/s = oracle tests/s / {tests_per_problem:.4g} "
+                                              f"tests per full problem (GPU count)",
+                                       single_thread=dict(value=smp["single"][0] / tests_per_problem,
+                                                          tests_per_s=smp["single"][0], seconds=smp["single"][1],
+                                                          cores=1))
         except Exception as e:   # the baseline must not sink the GPU line
-            out["cpu_baseline"] = dict(value=None, unit="problems/s", cores=1, kind="oracle", sample=f"failed: {e}")
+            out["cpu_baseline"] = dict(value=None, unit="problems/s", cores=os.cpu_count(), kind="oracle",
+                                       sample=f"failed: {e}")
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

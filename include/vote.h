@@ -215,6 +215,12 @@ vote_status vote_refine(vote_ctx *ctx, const double *surfaces, int64_t n, const 
                         const double *cell_lo, const double *cell_hi, const double *tol, int iters,
                         double *point_inout, double *score_out);
 
+/* Bounds of a leaf cell: lo[j] = lo_j + leaf[j] * w_j, hi[j] = lo[j] + w_j with w_j the
+ * leaf width in coordinate j (W_j 2^-L_j).  leaf host [d] (integer leaf coordinates, as
+ * vote_solve returns them), lo and hi host [d].  VOTE_EINVAL if a coordinate is out of
+ * range. */
+vote_status vote_leaf_box(vote_ctx *ctx, const int64_t *leaf, double *lo, double *hi);
+
 /* Number of levels L and per-coordinate split counts L_j (host [d]). */
 vote_status vote_levels(vote_ctx *ctx, int *L, int *Lj);
 

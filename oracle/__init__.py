@@ -12,6 +12,8 @@ Functions and the passages they follow:
   * :func:`solve` -- SurfaceConsensus (Algorithm 2) with canonization
     (Sec. 3.2, "Canonization") and bound-based pruning (Sec. 3.3, B&B combined
     with canonization); returns the best leaf, its depth and the inlier mask.
+  * :func:`solve_parallel` -- the same search on several host threads (the
+    multi-core CPU baseline); identical results.
   * :func:`cell_counts` -- upper/lower bound of one cell by replaying every
     original surface from the root (merge tracking, Sec. 3.2).
   * :func:`levels` -- level structure, snap steps and accumulated canonization
@@ -48,7 +50,7 @@ NO_MERGE, NO_PRUNE, REVERSE = 1, 2, 4
 FAMILY_SHAPE = {LINE2D: (2, 1, 1, 2), PLANE3D_SPH: (3, 2, 3, 3), POSE3DOF: (3, 1, 2, 4)}
 """family -> (d, k, number of essential params, number of input params)"""
 
-_CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+_CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11", "-fopenmp"]
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +78,8 @@ def _declare(lib):
     lib.gvo_solve.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P, i64, P, P, P, P, P, P]
     lib.gvo_cell_counts.restype = i32
     lib.gvo_cell_counts.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P]
+    lib.gvo_solve_parallel.restype = i32
+    lib.gvo_solve_parallel.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P]
     lib.gvo_sigma.restype = i32
     lib.gvo_sigma.argtypes = [i32, i32, i32, P, P]
     lib.gvo_lipschitz.restype = i32
@@ -191,6 +195,26 @@ def solve(family, eps, bounds, params, flags=0, trace_cap=0, members=False, lib=
     if members:
         out["members"] = np.sort(mem[: int(depth[0])])
     return out
+
+
+def solve_parallel(family, eps, bounds, params, threads=None, lib=None):
+    """The same search on several host threads (OpenMP over the subtrees below a
+    split level, sharing the best bound between subtrees); depth, best leaf and
+    mask equal :func:`solve`'s.  stats: tests, cells, leaves, L, threads, tasks."""
+    d, k, le, eps, bounds, params = _prep(family, eps, bounds, params)
+    n = params.shape[1]
+    threads = threads or os.cpu_count() or 1
+    best_point = np.zeros(d)
+    best_leaf = np.zeros(d, np.int64)
+    depth = np.zeros(1, np.int64)
+    mask = np.zeros(max((n + 31) // 32, 1), np.uint32)
+    stats = np.zeros(6, np.int64)
+    if (lib or _load()).gvo_solve_parallel(family, d, k, _ptr(eps), _ptr(bounds), _ptr(params), n, int(threads),
+                                            _ptr(best_point), _ptr(best_leaf), _ptr(depth), _ptr(mask),
+                                            _ptr(stats)):
+        raise ValueError("invalid problem")
+    return dict(best_point=best_point, best_leaf=best_leaf, depth=int(depth[0]), mask=mask[: (n + 31) // 32],
+                stats=stats)
 
 
 def cell_counts(family, eps, bounds, params, level, coords, want_reach=False):

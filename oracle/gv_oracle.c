@@ -56,6 +56,9 @@
  * cos, coefficients (-1)^n/n! rounded to double, evaluated by Horner's rule).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -452,8 +455,8 @@ static void snap_record(const gvo_problem *p, int l, gvo_rec *r, int64_t *key)
 /* Canonization with merging of identical rounded surfaces.                   */
 /* ------------------------------------------------------------------------- */
 
-static const int64_t *g_sort_keys;
-static int g_sort_klen;
+static _Thread_local const int64_t *g_sort_keys;   /* per thread: gvo_solve_parallel */
+static _Thread_local int g_sort_klen;
 
 static int cmp_key_index(const void *a, const void *b)
 {
@@ -505,9 +508,20 @@ static int64_t canonize(const gvo_problem *p, int l, gvo_rec *recs, int64_t n, i
 /* Depth-first SurfaceConsensus with bound-based pruning.                      */
 /* ------------------------------------------------------------------------- */
 
+/* A subtree handed to a worker thread by gvo_solve_parallel: one cell and the
+ * records that reach it. */
+typedef struct {
+    int64_t ci[GVO_MAXD];
+    gvo_rec *recs;
+    int64_t n, ub;
+} gvo_task;
+
 typedef struct {
     const gvo_problem *p;
     int flags;
+    int sink_level;        /* > 0: cells of this level become tasks instead of being visited */
+    gvo_task *tasks;
+    int64_t ntasks, cap_tasks;
     int64_t bestLB;
     int have_best;
     int64_t best_ub;
@@ -532,6 +546,20 @@ static void visit(gvo_search *S, int l, const int64_t *ci, gvo_rec *recs, int64_
 {
     const gvo_problem *p = S->p;
     int d = p->d;
+    if (S->sink_level > 0 && l == S->sink_level) {     /* collect the subtree as a task */
+        if (S->ntasks == S->cap_tasks) {
+            S->cap_tasks = S->cap_tasks ? 2 * S->cap_tasks : 64;
+            S->tasks = (gvo_task *)realloc(S->tasks, (size_t)S->cap_tasks * sizeof(gvo_task));
+        }
+        gvo_task *t = &S->tasks[S->ntasks++];
+        memcpy(t->ci, ci, d * sizeof(int64_t));
+        t->recs = (gvo_rec *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gvo_rec));
+        memcpy(t->recs, recs, (size_t)n * sizeof(gvo_rec));
+        t->n = n;
+        t->ub = 0;
+        for (int64_t r = 0; r < n; ++r) t->ub += recs[r].mult;
+        return;
+    }
     if (l == p->L) {                                   /* leaf: Diam(B) <= eps */
         S->leaves++;
         int64_t ub = 0;
@@ -829,4 +857,128 @@ int gvo_path_records(int fam, int d, int k, const double *eps, const double *bou
         for (int j = 0; j < p.nd; ++j) r.f[j] = fo[j];
     }
     return lam;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The same search on several host threads (the multi-core CPU baseline).     */
+/* ------------------------------------------------------------------------- */
+
+/* Runs the levels above a split level exactly as gvo_solve, turns every cell of the
+ * split level that survives into a task, and visits the tasks' subtrees on
+ * nthreads OpenMP threads with the serial visit().  Each task starts from the
+ * best lower bound and best leaf known when it starts and merges its own at the
+ * end; any valid bound may prune (Sec. 3.3), and the argmax keeps the same tie
+ * rule, so depth, best leaf and mask equal gvo_solve's.  stats: tests, cells,
+ * leaves, L, threads used, tasks. */
+int gvo_solve_parallel(int fam, int d, int k, const double *eps, const double *bounds, const double *params,
+                       int64_t n, int nthreads, double *best_point, int64_t *best_leaf, int64_t *depth,
+                       uint32_t *mask, int64_t *stats)
+{
+    gvo_problem p;
+    if (problem_init(&p, fam, d, k, eps, bounds) || check_inputs(&p, params, n)) return 1;
+    if (nthreads < 1) nthreads = 1;
+#ifdef _OPENMP
+    omp_set_num_threads(nthreads);
+#else
+    nthreads = 1;
+#endif
+    /* split level: the first level with at least 16 cells per thread */
+    int split = 0;
+    while (split < p.L) {
+        int bits = 0;
+        for (int j = 0; j < d; ++j) bits += splits(&p, split, j);
+        if (bits >= 30 || ((int64_t)1 << bits) >= 16 * (int64_t)nthreads) break;
+        ++split;
+    }
+    gvo_search top;
+    memset(&top, 0, sizeof(top));
+    top.p = &p;
+    top.sink_level = split;
+    gvo_rec *root = (gvo_rec *)malloc((size_t)(n > 0 ? n : 1) * sizeof(gvo_rec));
+    for (int64_t i = 0; i < n; ++i) family_lift(&p, params, n, i, &root[i]);
+    int64_t zero[GVO_MAXD] = {0};
+    if (split == 0) {
+        top.sink_level = -1;
+        visit(&top, 0, zero, root, n);
+    } else {
+        visit(&top, 0, zero, root, n);
+    }
+    free(root);
+    /* largest upper bounds first: their leaves raise the bound early */
+    for (int64_t x = 1; x < top.ntasks; ++x) {
+        gvo_task v = top.tasks[x];
+        int64_t y = x;
+        while (y > 0 && top.tasks[y - 1].ub < v.ub) { top.tasks[y] = top.tasks[y - 1]; --y; }
+        top.tasks[y] = v;
+    }
+    int64_t tests = top.tests, cells = top.cells, leaves = top.leaves;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : tests, cells, leaves)
+    for (int64_t x = 0; x < top.ntasks; ++x) {
+        gvo_task *t = &top.tasks[x];
+        gvo_search S;
+        memset(&S, 0, sizeof(S));
+        S.p = &p;
+        int64_t thr;
+#pragma omp critical(gvo_best)
+        {
+            S.bestLB = top.bestLB;
+            S.have_best = top.have_best;
+            S.best_ub = top.best_ub;
+            memcpy(S.best_leaf, top.best_leaf, sizeof(S.best_leaf));
+        }
+        thr = S.bestLB;
+        if (S.have_best && S.best_ub > thr) thr = S.best_ub;
+        if (t->ub > 0 && t->ub >= thr) {
+            visit(&S, split, t->ci, t->recs, t->n);
+            tests += S.tests;
+            cells += S.cells;
+            leaves += S.leaves;
+#pragma omp critical(gvo_best)
+            {
+                if (S.bestLB > top.bestLB) top.bestLB = S.bestLB;
+                if (S.have_best && (!top.have_best || S.best_ub > top.best_ub ||
+                                    (S.best_ub == top.best_ub && lex_less(S.best_leaf, top.best_leaf, d)))) {
+                    top.have_best = 1;
+                    top.best_ub = S.best_ub;
+                    memcpy(top.best_leaf, S.best_leaf, sizeof(top.best_leaf));
+                }
+            }
+        }
+        free(t->recs);
+        t->recs = NULL;
+    }
+    free(top.tasks);
+    if (!top.have_best) {
+        top.best_ub = 0;
+        memset(top.best_leaf, 0, sizeof(top.best_leaf));
+    }
+    *depth = top.best_ub;
+    for (int j = 0; j < d; ++j) {
+        best_leaf[j] = top.best_leaf[j];
+        best_point[j] = cell_center(&p, p.L, j, top.best_leaf[j]);
+    }
+    if (mask) {
+        int64_t words = (n + 31) / 32;
+        memset(mask, 0, (size_t)words * sizeof(uint32_t));
+        if (top.best_ub > 0) {
+#pragma omp parallel for schedule(dynamic, 256)
+            for (int64_t w = 0; w < words; ++w) {
+                uint32_t bits = 0;
+                for (int64_t i = 32 * w; i < n && i < 32 * w + 32; ++i) {
+                    int lbp;
+                    if (replay_one(&p, params, n, i, p.L, top.best_leaf, &lbp)) bits |= 1u << (i & 31);
+                }
+                mask[w] = bits;
+            }
+        }
+    }
+    if (stats) {
+        stats[0] = tests;
+        stats[1] = cells;
+        stats[2] = leaves;
+        stats[3] = p.L;
+        stats[4] = nthreads;
+        stats[5] = top.ntasks;
+    }
+    return 0;
 }

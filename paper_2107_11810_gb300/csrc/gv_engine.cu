@@ -933,6 +933,7 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
                                double *best_points, int64_t *best_leaves, int64_t *depths, uint32_t *masks,
                                double *latency_ms) {
     if (!c || !offsets || B < 0 || !best_points || !depths) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    std::memset(&c->stats, 0, sizeof(c->stats));     // this batch's counters, even when it is empty
     if (offsets[0] != 0) { set_err("offsets[0] must be 0"); return VOTE_EINVAL; }
     for (int b = 0; b < B; ++b)
         if (offsets[b + 1] < offsets[b]) { set_err("offsets must be non-decreasing"); return VOTE_EINVAL; }
@@ -1136,6 +1137,18 @@ vote_status vote_refine(vote_ctx *c, const double *surfaces, int64_t n, const ui
     }
     std::memcpy(point_inout, p, sizeof(double) * d);
     if (score_out) *score_out = S;
+    return VOTE_OK;
+}
+
+vote_status vote_leaf_box(vote_ctx *c, const int64_t *leaf, double *lo, double *hi) {
+    if (!c || !leaf || !lo || !hi) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    const Problem &P = c->P;
+    for (int j = 0; j < P.d; ++j) {
+        if (leaf[j] < 0 || leaf[j] >= ((int64_t)1 << P.Lj[j])) { set_err("leaf coordinate %d out of range", j); return VOTE_EINVAL; }
+        double w = 2.0 * c->h_leaf[j];
+        lo[j] = P.lo[j] + (double)leaf[j] * w;
+        hi[j] = lo[j] + w;
+    }
     return VOTE_OK;
 }
 

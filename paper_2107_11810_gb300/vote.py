@@ -32,7 +32,7 @@ NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4}
 EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
            "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_get_kernel_times",
            "vote_get_level_stats", "vote_cell_counts_noalloc", "vote_softscore_fwd", "vote_softscore_bwd",
-           "vote_refine", "vote_solve_batched",
+           "vote_refine", "vote_solve_batched", "vote_leaf_box",
            "vote_last_error", "vote_destroy"]
 
 
@@ -69,6 +69,7 @@ def load(path: str | None = None):
             lib.vote_solve_host.argtypes = [P, P, i64, P, P, P, P]
             lib.vote_cell_counts.argtypes = [P, P, i64, i32, P, P, P, P]
             lib.vote_levels.argtypes = [P, P, P]
+            lib.vote_leaf_box.argtypes = [P, P, P, P]
             lib.vote_get_trace.argtypes = [P, i64, P, P, P, P, P]
             lib.vote_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
             lib.vote_get_kernel_times.argtypes = [P, P, P, P]
@@ -100,6 +101,33 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return ctypes.c_void_p(a.data_ptr())
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def check_surfaces(surfaces, nparam: int):
+    """A device surface array must be a contiguous CUDA float64 tensor [nparam, n]:
+    anything else would hand the library a pointer it reads out of bounds or in
+    the wrong format."""
+    import torch
+    if not isinstance(surfaces, torch.Tensor):
+        raise ValueError("surfaces must be a torch tensor on a CUDA device")
+    if surfaces.ndim != 2 or surfaces.shape[0] != nparam:
+        raise ValueError(f"surfaces must be [{nparam}, n], got {tuple(surfaces.shape)}")
+    if not (surfaces.is_cuda and surfaces.dtype == torch.float64 and surfaces.is_contiguous()):
+        raise ValueError("surfaces must be a contiguous CUDA float64 tensor")
+
+
+def check_words(buf, n: int, device, name: str):
+    """A device bit-mask buffer: CUDA int32 tensor with at least (n + 31) // 32 words,
+    contiguous, on the surfaces' device."""
+    import torch
+    if buf is None:
+        return
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or buf.dtype != torch.int32 or not buf.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA int32 tensor")
+    if buf.numel() < (n + 31) // 32:
+        raise ValueError(f"{name} needs at least {(n + 31) // 32} words, has {buf.numel()}")
+    if buf.device != device:
+        raise ValueError(f"{name} must be on {device}, is on {buf.device}")
 
 
 class Solver:
@@ -147,14 +175,11 @@ class Solver:
         return L.value, Lj
 
     def _check_surfaces(self, surfaces):
-        if tuple(surfaces.shape[:1]) != (self.np,) or surfaces.ndim != 2:
-            raise ValueError(f"surfaces must be [{self.np}, n]")
+        check_surfaces(surfaces, self.np)
 
     def solve(self, surfaces, want_mask: bool = True):
         import torch
         self._check_surfaces(surfaces)
-        if not (surfaces.is_cuda and surfaces.dtype == torch.float64 and surfaces.is_contiguous()):
-            raise ValueError("surfaces must be a contiguous CUDA float64 tensor")
         n = surfaces.shape[1]
         bp = np.zeros(self.d)
         bl = np.zeros(self.d, np.int64)
@@ -168,14 +193,15 @@ class Solver:
 
     def solve_host(self, surfaces, want_mask: bool = True):
         """Host buffers in and out (copies inside the call)."""
-        self._check_surfaces(surfaces)
         if hasattr(surfaces, "data_ptr"):
-            if surfaces.is_cuda or not surfaces.is_contiguous():
-                raise ValueError("surfaces must be a contiguous CPU tensor")
-            n = surfaces.shape[1]
+            import torch
+            if surfaces.is_cuda or not surfaces.is_contiguous() or surfaces.dtype != torch.float64:
+                raise ValueError("surfaces must be a contiguous CPU float64 tensor")
         else:
             surfaces = np.ascontiguousarray(surfaces, dtype=np.float64)
-            n = surfaces.shape[1]
+        if surfaces.ndim != 2 or surfaces.shape[0] != self.np:
+            raise ValueError(f"surfaces must be [{self.np}, n]")
+        n = surfaces.shape[1]
         bp = np.zeros(self.d)
         bl = np.zeros(self.d, np.int64)
         dep = np.zeros(1, np.int64)
@@ -194,6 +220,7 @@ class Solver:
         ub = np.zeros(1, np.int64)
         lb = np.zeros(1, np.int64)
         reach = torch.zeros(max((n + 31) // 32, 1), dtype=torch.int32, device=surfaces.device) if want_reach else None
+        check_words(reach, n, surfaces.device, "reach")
         _check(self.lib.vote_cell_counts(self.h, _ptr(surfaces), n, int(level), _ptr(c), _ptr(ub), _ptr(lb),
                                          _ptr(reach)))
         if want_reach:
@@ -241,6 +268,10 @@ class Solver:
         data, offsets = blocks
         offs = np.ascontiguousarray(offsets, dtype=np.int64)
         B = len(offs) - 1
+        if not (isinstance(data, torch.Tensor) and data.is_cuda and data.dtype == torch.float64
+                and data.is_contiguous() and data.numel() >= self.np * int(offs[-1])):
+            raise ValueError(f"batched surfaces must be a contiguous CUDA float64 tensor of at least "
+                             f"{self.np} x {int(offs[-1])} values")
         ns = np.diff(offs)
         wo = np.concatenate([[0], np.cumsum((ns + 31) // 32)]).astype(np.int64)
         bp = np.zeros((max(B, 1), self.d))
@@ -258,6 +289,7 @@ class Solver:
         (point, score)."""
         self._check_surfaces(surfaces)
         n = surfaces.shape[1]
+        check_words(mask, n, surfaces.device, "mask")
         lo = np.ascontiguousarray(cell_lo, dtype=np.float64).reshape(self.d)
         hi = np.ascontiguousarray(cell_hi, dtype=np.float64).reshape(self.d)
         pt = np.array(point, dtype=np.float64).reshape(self.d)
@@ -268,14 +300,11 @@ class Solver:
         return pt, float(sc[0])
 
     def leaf_box(self, leaf):
-        """(lo, hi) of a leaf cell given its integer coordinates."""
-        L, Lj = self.levels()
+        """(lo, hi) of a leaf cell given its integer coordinates (vote_leaf_box)."""
+        lf = np.ascontiguousarray(leaf, dtype=np.int64).reshape(self.d)
         lo = np.zeros(self.d)
         hi = np.zeros(self.d)
-        for j in range(self.d):
-            w = (self.bounds[2 * j + 1] - self.bounds[2 * j]) / 2.0 ** int(Lj[j])
-            lo[j] = self.bounds[2 * j] + w * int(leaf[j])
-            hi[j] = lo[j] + w
+        _check(self.lib.vote_leaf_box(self.h, _ptr(lf), _ptr(lo), _ptr(hi)))
         return lo, hi
 
     def close(self):
@@ -306,6 +335,8 @@ def cell_counts_noalloc(family: int, eps, bounds, surfaces, level: int, coords, 
     reach mask.  Calls that may overlap on the GPU must be serialised by the caller."""
     lib = load()
     d, k = FAMILY_DK[family]
+    check_surfaces(surfaces, NPARAM[family])
+    check_words(reach, surfaces.shape[1], surfaces.device, "reach")
     e = np.ascontiguousarray(eps, dtype=np.float64).reshape(d)
     b = np.ascontiguousarray(bounds, dtype=np.float64).reshape(2 * d)
     c = np.ascontiguousarray(coords, dtype=np.int64).reshape(d)

@@ -272,3 +272,20 @@ def test_invalid_inputs_rejected():
     bad[0, 3] = np.nan
     with pytest.raises(ValueError):
         oracle.solve(L2, p.eps, p.bounds, bad)
+
+
+# ---------------------------------------------------------------------------
+# the multi-core oracle (CPU baseline) gives the serial oracle's results
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,mk", CASES)
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_parallel_oracle_equals_serial(name, mk, threads):
+    p = mk(6)
+    a = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    b = oracle.solve_parallel(p.family, p.eps, p.bounds, p.params, threads=threads)
+    assert b["depth"] == a["depth"]
+    assert np.array_equal(b["best_leaf"], a["best_leaf"])
+    assert np.array_equal(b["best_point"], a["best_point"])
+    assert np.array_equal(b["mask"], a["mask"])
+    assert b["stats"][4] == threads

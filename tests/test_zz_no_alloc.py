@@ -6,13 +6,15 @@ framework's allocator).  For them the library offers one context-free entry
 point whose scratch is a fixed array inside the library.  This test calls it
 through the C ABI and checks, on two calls in a row, that its per-cell counts and
 reach mask equal those of vote_cell_counts (which uses the context's allocated
-memory).  Counts are integers, so they must be identical.
+memory), and that those equal the oracle's replay.  Counts are integers, so they
+must be identical.
 
 The file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2107_11810_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +50,10 @@ def test_noalloc_cell_counts_match_context_entry_point(family):
     words = (p.n + 31) // 32
     for level, coords in cells:
         ref_ub, ref_lb, ref_reach = s.cell_counts(t, level, coords, want_reach=True)
+        # the context entry point itself equals the oracle's replay (the FP64 definition)
+        oub, olb, oreach = oracle.cell_counts(p.family, p.eps, p.bounds, p.params, level, coords, want_reach=True)
+        assert (ref_ub, ref_lb) == (oub, olb)
+        assert np.array_equal(vote.mask_words_to_numpy(ref_reach), oreach)
         for _ in range(2):                                  # two calls in a row share the scratch
             reach = torch.full((words,), -1, dtype=torch.int32, device="cuda")
             ub, lb = vote.cell_counts_noalloc(p.family, p.eps, p.bounds, t, level, coords, reach=reach)
@@ -67,3 +73,11 @@ def test_noalloc_rejects_bad_arguments():
     assert ei.value.code == 1
     with pytest.raises(vote.VoteError):
         vote.cell_counts_noalloc(p.family, p.eps, p.bounds, t, 1, [5, 0])
+    # wrong buffers are refused before the call: host tensor, float32, short reach
+    with pytest.raises(ValueError):
+        vote.cell_counts_noalloc(p.family, p.eps, p.bounds, t.cpu(), 1, [0, 0])
+    with pytest.raises(ValueError):
+        vote.cell_counts_noalloc(p.family, p.eps, p.bounds, t.float(), 1, [0, 0])
+    with pytest.raises(ValueError):
+        short = torch.zeros((p.n + 31) // 32 - 1, dtype=torch.int32, device="cuda")
+        vote.cell_counts_noalloc(p.family, p.eps, p.bounds, t, 1, [0, 0], reach=short)
