@@ -99,10 +99,6 @@ typedef enum {
                                  (default): on for n >= 131072 surfaces.  Results do
                                  not depend on it (Sec. 3.3: any valid bound may
                                  prune)                                              */
-    VOTE_OPT_TWO_LEVEL = 9    /* expand two levels per read of a chunk's records when
-                                 its children would hold more than this many times
-                                 its records (their records are then never written
-                                 to memory); 0 = never (default)                     */
 } vote_option;
 
 /* Kernel classes reported by vote_get_kernel_times. */
@@ -117,7 +113,10 @@ typedef struct {
     int64_t cells;           /* cells expanded (canonized and tested)            */
     int64_t records;         /* (cell, canonical surface) records tested          */
     int64_t tests;           /* (child cell, canonical surface) predicate calls   */
-    int64_t rechecks;        /* tests decided by the FP64 recheck                 */
+    int64_t rechecks;        /* tests re-evaluated in FP64 because the FP32 screen
+                                could not decide them (whole records: every child
+                                of a record with one uncertain test), plus child
+                                snaps taken in FP64                               */
     int64_t chunks;          /* expansion steps                                   */
     int64_t leaves;          /* leaves evaluated                                  */
     int64_t peak_records;    /* largest record count held at one level            */

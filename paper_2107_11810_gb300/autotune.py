@@ -1,9 +1,9 @@
 """Autotuner for the solver's runtime settings.
 
-The search's launch shapes are fixed per kernel (tiles of 1,024 records, 256
-threads), but how much work one expansion step takes (chunk size), whether two
-levels are expanded per read of a chunk, and how many host workers a batched
-solve uses depend on the family, the problem size and the GPU.  The autotuner
+The search's launch shapes are fixed per kernel (warp tiles of 32 records, blocks
+of 8 warps), but how much work one expansion step takes (chunk size) and how many
+host workers a batched solve uses depend on the family, the problem size and the
+GPU.  The autotuner
 times a few candidate settings on a representative problem, keeps the fastest,
 and caches the choice in a JSON file keyed by (family, d, n bucket, GPU name).
 Results never depend on these settings (they are tested bit-identical), only the
@@ -20,11 +20,10 @@ from . import vote
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gv_gb300_autotune.json")
 CANDIDATES = [
-    dict(chunk_records=1 << 23, two_level=0.0),
-    dict(chunk_records=1 << 25, two_level=0.0),
-    dict(chunk_records=1 << 26, two_level=0.0),
-    dict(chunk_records=1 << 27, two_level=0.0),
-    dict(chunk_records=1 << 25, two_level=2.0),
+    dict(chunk_records=1 << 23),
+    dict(chunk_records=1 << 25),
+    dict(chunk_records=1 << 26),
+    dict(chunk_records=1 << 27),
 ]
 
 
@@ -55,7 +54,6 @@ def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
 
 def apply(solver: "vote.Solver", setting: dict) -> None:
     solver.set_option(vote.VOTE_OPT_CHUNK_RECORDS, setting["chunk_records"])
-    solver.set_option(vote.VOTE_OPT_TWO_LEVEL, setting["two_level"])
     if "batch_workers" in setting:
         solver.set_option(vote.VOTE_OPT_BATCH_WORKERS, setting["batch_workers"])
 

@@ -1,6 +1,6 @@
 """Build libvote.so (the CUDA path) in-tree with nvcc for sm_103a.
 
-Two translation units are compiled in parallel and linked into
+The translation units are compiled in parallel and linked into
 ``paper_2107_11810_gb300/libvote.so``; the objects go to ``_build/``.
 """
 from __future__ import annotations
@@ -14,8 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvote.so")
-SOURCES = ["gv_kernels.cu", "gv_engine.cu", "gv_softscore.cu"]
-HEADERS = ["gv_device.cuh", "gv_kernels.h"]
+SOURCES = ["gv_kernels.cu", "gv_count.cu", "gv_emit.cu", "gv_engine.cu", "gv_softscore.cu"]
+HEADERS = ["gv_device.cuh", "gv_kernels.h", "gv_tile.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -prec-sqrt=false: FP32 sqrtf (only used by the FP32 screen, whose error margin

@@ -3,13 +3,16 @@
 // Surfaces follow Sec. 3, Eq. 1 of Aiger et al. (arXiv 2107.11810):
 // x_j = F_j(x_free; t) + f_j.  A record holds one canonical surface in the frame of
 // its cell: the free parameter as an integer multiple q_f of the snap step s_f
-// (its vertical residual at the cell centre), the essential parameters as integer
-// multiples q_t of the level's step s_t (canonization, Sec. 3.2), and the number of
-// original surfaces it stands for.
+// (its vertical residual at the cell centre) and the essential parameters as
+// integer multiples q_t of the level's step s_t (canonization, Sec. 3.2).
 //
 // Every FP64 operation that decides a count is issued as one explicitly rounded
 // IEEE operation (__dadd_rn, __dmul_rn, ...), in a fixed order, so the compiler
 // cannot fuse or reorder it; the results are bit-identical to the definition.
+// The FP32 screen works in units of the free-parameter step: a record's residual
+// at a child centre is u_j = q_f,j + sum_m q_t,m G_jm - H_j, with G_jm the
+// coefficient of t_m in that residual scaled by s_t,m / s_f,j (exact power-of-two
+// scaling of an FP64 value rounded once to FP32) and H_j the child shift in steps.
 #pragma once
 #include <cstdint>
 
@@ -29,7 +32,6 @@ struct Problem {
     int coord_bits;            // sum of Lj
     double lo[GV_MAXD], W[GV_MAXD], eps[GV_MAXD];
     double s_f[GV_MAXD], inv_s_f[GV_MAXD];  // per dependent coordinate
-    float s_ff[GV_MAXD], inv_s_ff[GV_MAXD];
 };
 
 struct Level {                 // tests of the children of a level-l cell
@@ -44,10 +46,18 @@ struct Level {                 // tests of the children of a level-l cell
     double Rbase[GV_MAXD];     // eps_j + h1_j            (dependent index)
     double A1[GV_MAXD];        // accumulated canonization error at level l+1
     double rlb[GV_MAXD];       // eps_j - A1_j             (lower-bound radius)
-    float h1f[GV_MAXD];        // FP32 copies for the screen
-    float Rbasef[GV_MAXD], A1f[GV_MAXD], rlbf[GV_MAXD], s_tf[GV_MAXT];
+    double gscale[GV_MAXD][GV_MAXT];  // s_t,m / s_f,j (a power of two)
+    // FP32 screen constants, in units of s_f,j (dependent coordinate j)
+    float Hs[GV_MAXD];         // h1 of dependent coordinate j
+    float rc0[GV_MAXD];        // (eps_j + h1_j + A1_j): the radius without its Lipschitz term
+    float lam_c[4];            // family-specific scale of the Lipschitz term (see Fam::radius32)
+    float rho2;                // family-specific ratio of essential steps (planes: (s_t,z / s_t,x)^2)
+    float Lc[GV_MAXD];         // eps_j - A1_j (lower-bound radius)
+    // set per solve, once the input's parameter ranges are known
+    float qt_max[GV_MAXT];     // bound on |q_t,m| of this level's records
+    int q16;                   // this level's records hold 16-bit fields
+    int q16_next;              // the next level's records hold 16-bit fields
 };
-
 // ---------------------------------------------------------------------------
 // Explicitly rounded FP64 operations.
 // ---------------------------------------------------------------------------
@@ -128,9 +138,10 @@ __device__ __forceinline__ uint64_t child_key(const Problem &P, uint64_t key, in
 
 // ---------------------------------------------------------------------------
 // Families.  For each: D, K (free coords), ND (dependent), LE (essential params),
-// NP (input rows), NB (basis values); basis(), lift(), residual64(), lipschitz64(),
-// and the FP32 screen versions residual32(), lipschitz32() with errmag32(), the
-// magnitude sum that bounds the FP32 residual's distance from the FP64 one.
+// NP (input rows), NB (basis values), NFP (record fields, padded to a power of
+// two); basis(), lift(), residual64(), partial64(), lipschitz64() (the exact FP64
+// definition), and for the FP32 screen coef() (coefficient of t_m in dependent
+// residual j for a basis change) and radius32() (the UB radius in steps).
 // ---------------------------------------------------------------------------
 enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3 };
 
@@ -139,7 +150,7 @@ template <int FAM> struct Fam;
 // LINE2D: coords (m, b); b = y - x m.  t = x, psi = m (linear: its change across a
 // child shift is the shift itself).
 template <> struct Fam<FAM_LINE2D> {
-    static constexpr int D = 2, K = 1, ND = 1, LE = 1, NP = 2, NB = 1;
+    static constexpr int D = 2, K = 1, ND = 1, LE = 1, NP = 2, NB = 1, NFP = 2;
     static constexpr bool LINEAR_BASIS = true;
     __device__ static void basis(const double *c, double *psi) { psi[0] = c[0]; }
     __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
@@ -158,25 +169,16 @@ template <> struct Fam<FAM_LINE2D> {
     __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
         p[0] = dsub(f[0], dmul(t[0], dpsi[0]));
     }
-    __device__ static void partial32(const float *f, const float *t, const float *dpsi, float *p) {
-        p[0] = f[0] - t[0] * dpsi[0];
+    __device__ static void coef(const double *dpsi, double *g) { g[0] = -dpsi[0]; }
+    // |t| = s_t |q_t|: radius = rc0 + lam_c[0] |q_t|
+    __device__ static void radius32(const Level &lev, const float *qt, float *R) {
+        R[0] = __fmaf_rn(lev.lam_c[0], fabsf(qt[0]), lev.rc0[0]);
     }
-    // FP32 screen: residual, and the magnitude sum its rounding error scales with
-    // (dpsi_max/sh_max: largest |dpsi| and |shift| over the cell's children)
-    __device__ static void residual32(const float *f, const float *t, const float *dpsi, const float *sh,
-                                      float *fo) {
-        fo[0] = (f[0] - t[0] * dpsi[0]) - sh[1];
-    }
-    __device__ static void errmag32(const float *f, const float *t, const float *dpsi_max, const float *sh_max,
-                                    float *err) {
-        err[0] = fabsf(f[0]) + fabsf(t[0]) * dpsi_max[0] + sh_max[1];
-    }
-    __device__ static void lipschitz32(const float *t, float *lam) { lam[0] = fabsf(t[0]); }
 };
 
 // PLANE3D_SPH: coords (theta, phi, d); d = q . n(theta, phi).  t = q; psi = n.
 template <> struct Fam<FAM_PLANE3D_SPH> {
-    static constexpr int D = 3, K = 2, ND = 1, LE = 3, NP = 3, NB = 3;
+    static constexpr int D = 3, K = 2, ND = 1, LE = 3, NP = 3, NB = 3, NFP = 4;
     static constexpr bool LINEAR_BASIS = false;
     __device__ static void basis(const double *c, double *psi) {
         double st, ct, sp, cp;
@@ -200,35 +202,25 @@ template <> struct Fam<FAM_PLANE3D_SPH> {
     __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
         p[0] = dadd(f[0], dadd(dadd(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1])), dmul(t[2], dpsi[2])));
     }
-    __device__ static void partial32(const float *f, const float *t, const float *dpsi, float *p) {
-        p[0] = f[0] + __fmaf_rn(t[2], dpsi[2], __fmaf_rn(t[1], dpsi[1], t[0] * dpsi[0]));
-    }
     __device__ static void lipschitz64(const double *t, double *lam) {
         double xy = dadd(dmul(t[0], t[0]), dmul(t[1], t[1]));
         lam[0] = dsqrt(dadd(xy, dmul(t[2], t[2])));
         lam[1] = dsqrt(xy);
     }
-    __device__ static void residual32(const float *f, const float *t, const float *dpsi, const float *sh,
-                                      float *fo) {
-        float s = __fmaf_rn(t[2], dpsi[2], __fmaf_rn(t[1], dpsi[1], t[0] * dpsi[0]));
-        fo[0] = (f[0] + s) - sh[2];
-    }
-    __device__ static void errmag32(const float *f, const float *t, const float *dpsi_max, const float *sh_max,
-                                    float *err) {
-        err[0] = fabsf(f[0]) + fabsf(t[0]) * dpsi_max[0] + fabsf(t[1]) * dpsi_max[1] +
-                 fabsf(t[2]) * dpsi_max[2] + sh_max[2];
-    }
-    __device__ static void lipschitz32(const float *t, float *lam) {
-        float xy = t[0] * t[0] + t[1] * t[1];
-        lam[0] = sqrtf(xy + t[2] * t[2]);
-        lam[1] = sqrtf(xy);
+    __device__ static void coef(const double *dpsi, double *g) { g[0] = dpsi[0]; g[1] = dpsi[1]; g[2] = dpsi[2]; }
+    // s_t,x = s_t,y (their sigma bounds are equal) and s_t,z = s_t,x sqrt(rho2):
+    // |q| = s_t,x sqrt(qx^2 + qy^2 + rho2 qz^2), |q_xy| = s_t,x sqrt(qx^2 + qy^2)
+    __device__ static void radius32(const Level &lev, const float *qt, float *R) {
+        float xy = __fmaf_rn(qt[1], qt[1], qt[0] * qt[0]);
+        float all = __fmaf_rn(qt[2] * lev.rho2, qt[2], xy);
+        R[0] = __fmaf_rn(lev.lam_c[0], sqrtf(all), __fmaf_rn(lev.lam_c[1], sqrtf(xy), lev.rc0[0]));
     }
 };
 
 // POSE3DOF: coords (yaw, x, y); x = w1 - (a cos yaw - b sin yaw),
 // y = w2 - (a sin yaw + b cos yaw).  t = (a, b); psi = (cos yaw, sin yaw).
 template <> struct Fam<FAM_POSE3DOF> {
-    static constexpr int D = 3, K = 1, ND = 2, LE = 2, NP = 4, NB = 2;
+    static constexpr int D = 3, K = 1, ND = 2, LE = 2, NP = 4, NB = 2, NFP = 4;
     static constexpr bool LINEAR_BASIS = false;
     __device__ static void basis(const double *c, double *psi) {
         double s, co;
@@ -252,38 +244,35 @@ template <> struct Fam<FAM_POSE3DOF> {
         p[0] = dsub(f[0], dsub(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1])));
         p[1] = dsub(f[1], dadd(dmul(t[0], dpsi[1]), dmul(t[1], dpsi[0])));
     }
-    __device__ static void partial32(const float *f, const float *t, const float *dpsi, float *p) {
-        p[0] = f[0] - __fmaf_rn(t[0], dpsi[0], -(t[1] * dpsi[1]));
-        p[1] = f[1] - __fmaf_rn(t[0], dpsi[1], t[1] * dpsi[0]);
-    }
     __device__ static void lipschitz64(const double *t, double *lam) {
         double r = dsqrt(dadd(dmul(t[0], t[0]), dmul(t[1], t[1])));
         lam[0] = r;
         lam[1] = r;
     }
-    __device__ static void residual32(const float *f, const float *t, const float *dpsi, const float *sh,
-                                      float *fo) {
-        fo[0] = (f[0] - __fmaf_rn(t[0], dpsi[0], -(t[1] * dpsi[1]))) - sh[1];
-        fo[1] = (f[1] - __fmaf_rn(t[0], dpsi[1], t[1] * dpsi[0])) - sh[2];
+    // x residual: -a dcos + b dsin; y residual: -a dsin - b dcos
+    __device__ static void coef(const double *dpsi, double *g) {
+        g[0] = -dpsi[0]; g[1] = dpsi[1];
+        g[2] = -dpsi[1]; g[3] = -dpsi[0];
     }
-    __device__ static void errmag32(const float *f, const float *t, const float *dpsi_max, const float *sh_max,
-                                    float *err) {
-        float m = fabsf(t[0]) * fmaxf(dpsi_max[0], dpsi_max[1]) + fabsf(t[1]) * fmaxf(dpsi_max[0], dpsi_max[1]);
-        err[0] = fabsf(f[0]) + m + sh_max[1];
-        err[1] = fabsf(f[1]) + m + sh_max[2];
-    }
-    __device__ static void lipschitz32(const float *t, float *lam) {
-        float r = sqrtf(t[0] * t[0] + t[1] * t[1]);
-        lam[0] = r;
-        lam[1] = r;
+    // s_t,a = s_t,b: sqrt(a^2 + b^2) = s_t sqrt(qa^2 + qb^2)
+    __device__ static void radius32(const Level &lev, const float *qt, float *R) {
+        float r = sqrtf(__fmaf_rn(qt[1], qt[1], qt[0] * qt[0]));
+        R[0] = __fmaf_rn(lev.lam_c[0], r, lev.rc0[0]);
+        R[1] = __fmaf_rn(lev.lam_c[1], r, lev.rc0[1]);
     }
 };
 
-// Relative error factor of the FP32 screen: every FP32 residual above takes at
-// most 6 rounded steps (conversions included) on terms whose magnitudes sum to
-// err[]; its distance to the FP64 value is below 8 u32 * err (u32 = 2^-24) plus
-// the FP64 value's own error (< 8 u64 * err).  The screen uses 32 u32 * err, a
-// factor-4 margin that also covers the rounding of err itself.
-constexpr float kScreenRel = 32.0f * 5.9604645e-08f;
+// Width of the FP32 screen's band, from the magnitudes of one record (in steps):
+// M_j = |q_f,j| + sum_m |q_t,m| Gmax_jm + |H_j|.  The FP32 residual y takes LE fused
+// multiply-adds, one add and coefficients rounded once from FP64, so
+// |y - y_exact| <= 6 u M_j (u = 2^-24; the FP64 definition's own error is below
+// 2^-48 M_j); the FP32 radius (two approximate square roots of at most 4 ulp, two
+// multiply-adds, constants rounded once) is within 13 u R of the exact radius.
+// A comparison of |y| with R (or with the lower-bound radius) is decided in FP32
+// only when it clears kBandTest (M_j + R); a snap only when y is kBandSnap M_j away
+// from a rounding tie: both about twice the bound.
+constexpr float kU32 = 5.9604645e-08f;
+constexpr float kBandTest = 24.0f * kU32;
+constexpr float kBandSnap = 12.0f * kU32;
 
 }  // namespace gv

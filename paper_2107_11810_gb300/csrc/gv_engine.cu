@@ -11,11 +11,13 @@
 // level, and leaves are reached early, which raises the pruning bound early.  The
 // result does not depend on this order.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <atomic>
 #include <mutex>
@@ -24,6 +26,7 @@
 #include <vector>
 
 #include "gv_kernels.h"
+#include "gv_tile.cuh"
 #include "vote.h"
 
 using namespace gv;
@@ -58,9 +61,9 @@ struct DevBuf {
 };
 
 struct LevelStore {
-    DevBuf qf[GV_MAXD], qt[GV_MAXT], mult, cell;
+    DevBuf rec, mult, tile_cell;       // packed records (whole tiles), multiplicities, owning cell per tile
     DevBuf key, rbeg, rcnt, ub;
-    int64_t ncells = 0, nrecs = 0;
+    int64_t ncells = 0, nrecs = 0;     // nrecs: record slots in use (a multiple of 32)
 };
 
 struct vote_ctx {
@@ -74,7 +77,7 @@ struct vote_ctx {
     int64_t chunk_records = 1 << 25;
     uint32_t initial_lb = 0;
     int kernel_timing = 0;
-    double two_level = 0.0;
+    int log = 0;               // VOTE_LOG=1: per-level counters on stderr after each solve
     int batch_workers = 4;
     int dive = 2;              // greedy dive: 0 off, 1 on, 2 on for n >= kDiveMinN
     int family = 0;
@@ -91,11 +94,10 @@ struct vote_ctx {
     int64_t trace_cap = 0;
     int64_t fault_alloc_at = 0, alloc_count = 0;
     LevelStore ls[GV_MAXL + 1];
-    DevBuf levs_dev, path, scal, alive, geo64, geo32, cnt, passmask, child_idx, cursor, keepflag, recn, bsums;
+    DevBuf levs_dev, path, scal, alive, geo64, geo32, cnt, tinfo, ballot, tdst, child_idx, cursor, keepflag, recn, bsums;
     DevBuf tr_level, tr_key, tr_ub, tr_lb, surf_tmp, mask_tmp;
-    DevBuf alive1, geo64b, geo32b, cntb, pm2, child_idxb, cursorb;
     DevBuf ss_partial, ss_io;  // soft score: block partials; point [d] + outputs [d] + grad_out [1]
-    DevBuf g_table, g_owner, g_newpos, g_ccount, g_ccur, g_qf[GV_MAXD], g_qt[GV_MAXT], g_mult, g_cell;
+    DevBuf g_table, g_owner, g_newpos, g_ccount, g_ccur, g_rbeg, g_rec, g_mult, g_tile;
     int64_t grouped_away = 0;  // records merged away by grouping in the last solve
     Scalars *h_sc = nullptr;   // pinned mirror of the device scalars
     uint64_t *h_tmp = nullptr; // pinned slot for single values
@@ -199,8 +201,6 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
         if (epsp < epsp_min) epsp_min = epsp;
         P.s_f[j] = pow2_floor(epsp / (double)(le + 1), nullptr);
         P.inv_s_f[j] = 1.0 / P.s_f[j];
-        P.s_ff[j] = (float)P.s_f[j];
-        P.inv_s_ff[j] = (float)P.inv_s_f[j];
     }
     double s_t[GV_MAXL + 1][GV_MAXT];
     int s_te[GV_MAXL + 1][GV_MAXT];
@@ -226,12 +226,10 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
             if (l < P.Lj[j]) v.split_mask |= 1 << j;
             v.h[j] = h[l][j];
             v.h1[j] = h[l + 1][j];
-            v.h1f[j] = (float)h[l + 1][j];
         }
         for (int m = 0; m < le; ++m) {
             v.s_t[m] = s_t[l][m];
             v.inv_s_t[m] = std::ldexp(1.0, -s_te[l][m]);
-            v.s_tf[m] = (float)s_t[l][m];
             if (l + 1 < P.L) {
                 int r = s_te[l + 1][m] - s_te[l][m];
                 if (r < 0 || r > 1) {
@@ -245,12 +243,81 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
             v.Rbase[j] = P.eps[k + j] + h[l + 1][k + j];
             v.A1[j] = A[l + 1][j];
             v.rlb[j] = P.eps[k + j] - A[l + 1][j];
-            v.Rbasef[j] = (float)v.Rbase[j];
-            v.A1f[j] = (float)v.A1[j];
-            v.rlbf[j] = (float)v.rlb[j];
+            // FP32 screen constants in steps of s_f,j (rounding is covered by its band)
+            for (int m = 0; m < le; ++m) v.gscale[j][m] = s_t[l][m] / P.s_f[j];
+            v.Hs[j] = (float)(h[l + 1][k + j] / P.s_f[j]);
+            v.rc0[j] = (float)((v.Rbase[j] + v.A1[j]) / P.s_f[j]);
+            v.Lc[j] = (float)(v.rlb[j] / P.s_f[j]);
+        }
+        // Lipschitz term of the radius from the essential parameters in steps
+        switch (fam) {
+        case VOTE_LINE2D:        // |t| h1_m
+            v.lam_c[0] = (float)(h[l + 1][0] * s_t[l][0] / P.s_f[0]);
+            break;
+        case VOTE_PLANE3D_SPH:   // |q| h1_theta + |q_xy| h1_phi; s_t,x = s_t,y
+            v.lam_c[0] = (float)(h[l + 1][0] * s_t[l][0] / P.s_f[0]);
+            v.lam_c[1] = (float)(h[l + 1][1] * s_t[l][0] / P.s_f[0]);
+            v.rho2 = (float)((s_t[l][2] / s_t[l][0]) * (s_t[l][2] / s_t[l][0]));
+            break;
+        case VOTE_POSE3DOF:      // sqrt(a^2 + b^2) h1_yaw; s_t,a = s_t,b
+            for (int j = 0; j < P.nd; ++j) v.lam_c[j] = (float)(h[l + 1][0] * s_t[l][0] / P.s_f[j]);
+            break;
+        }
+        if ((fam == VOTE_PLANE3D_SPH && s_t[l][0] != s_t[l][1]) || (fam == VOTE_POSE3DOF && s_t[l][0] != s_t[l][1])) {
+            set_err("internal: unequal essential steps at level %d", l);
+            return VOTE_EINTERNAL;
         }
     }
     return VOTE_OK;
+}
+
+// Upper bounds on the Lipschitz factors Lambda_ji from bounds T_m on |t_m|.
+static void lambda_max(int fam, const double *T, double *lam) {
+    switch (fam) {
+    case VOTE_LINE2D: lam[0] = T[0]; break;
+    case VOTE_PLANE3D_SPH:
+        lam[0] = std::sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+        lam[1] = std::sqrt(T[0] * T[0] + T[1] * T[1]);
+        break;
+    case VOTE_POSE3DOF: lam[0] = lam[1] = std::sqrt(T[0] * T[0] + T[1] * T[1]); break;
+    }
+}
+
+// Per-solve level constants, once the root records' largest |q| are known
+// (qmax[j] for free, qmax[nd + m] for essential parameters): bounds on the records'
+// fields at every level, and the record format of
+// each level (16-bit fields where every bound stays below 32000; level 0, and
+// every level in plain FP64 mode, 32-bit).  A level-l record (l >= 1) passed the
+// UB test of level l-1, so |f| <= that radius; |q_t| only shrinks as steps double.
+static void finalize_levels(vote_ctx *c, const unsigned *qmax) {
+    const Problem &P = c->P;
+    double rprev[GV_MAXD] = {};
+    for (int l = 0; l < P.L; ++l) {
+        Level &v = c->lev[l];
+        double T[GV_MAXT], lam[GV_MAXD * GV_MAXD], qtb[GV_MAXT];
+        bool fits = c->precision == 1 && l >= 1;
+        for (int m = 0; m < P.le; ++m) {
+            double ratio = v.s_t[m] / c->lev[0].s_t[m];                 // a power of two >= 1
+            qtb[m] = std::floor((double)qmax[P.nd + m] / ratio) + 1.0;
+            T[m] = (qtb[m] + 1.0) * v.s_t[m];
+            v.qt_max[m] = (float)qtb[m];
+            fits &= qtb[m] <= 32000.0;
+        }
+        lambda_max(P.fam, T, lam);
+        for (int j = 0; j < P.nd; ++j) {
+            double R = v.Rbase[j];
+            for (int i = 0; i < P.k; ++i) R += lam[j * P.k + i] * v.h1[i];
+            R = (R + v.A1[j]) * 1.001;
+            double qfb = l == 0 ? (double)qmax[j] + 1.0 : std::ceil(rprev[j] / P.s_f[j]) + 1.0;
+            fits &= qfb <= 32000.0;
+            rprev[j] = R;
+        }
+        v.q16 = fits ? 1 : 0;
+    }
+    // a level keeps 16-bit records only if every deeper level does (the bounds shrink
+    // with depth, so this only guards the format sequence the emit pass supports)
+    for (int l = P.L - 2; l >= 0; --l) c->lev[l].q16 &= c->lev[l + 1].q16;
+    for (int l = 0; l < P.L; ++l) c->lev[l].q16_next = l + 1 < P.L ? c->lev[l + 1].q16 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -286,16 +353,22 @@ static void release(vote_ctx *c, DevBuf &b) {
     b.bytes = 0;
 }
 
+static int family_nfp(int fam) { return fam == VOTE_LINE2D ? 2 : 4; }
+
+// bytes of one record of level l (its format is fixed per solve by finalize_levels)
+static int rec_bytes_at(const vote_ctx *c, int l) {
+    return 4 * rec_words(family_nfp(c->P.fam), l < c->P.L && c->lev[l].q16);
+}
+
 // Every array is checked against its own allocated size (ensure returns at once
 // when it is large enough), so no separate capacity figure can drift from the
-// allocations.
-static vote_status ensure_level(vote_ctx *c, int l, size_t recs, size_t cells) {
+// allocations.  slots: record slots (a multiple of 32).
+static vote_status ensure_level(vote_ctx *c, int l, size_t slots, size_t cells) {
     LevelStore &s = c->ls[l];
-    if (recs > 0) {
-        for (int j = 0; j < c->P.nd; ++j) TRY(ensure(c, s.qf[j], recs * 4));
-        for (int m = 0; m < c->P.le; ++m) TRY(ensure(c, s.qt[m], recs * 4));
-        if (c->group) TRY(ensure(c, s.mult, recs * 4));   // without grouping every mult is 1
-        TRY(ensure(c, s.cell, recs * 4));
+    if (slots > 0) {
+        TRY(ensure(c, s.rec, slots * rec_bytes_at(c, l)));
+        if (c->group) TRY(ensure(c, s.mult, slots * 4));   // without grouping every mult is 1
+        TRY(ensure(c, s.tile_cell, (slots / 32) * 4));
     }
     if (cells > 0) {
         TRY(ensure(c, s.key, cells * 8));
@@ -308,11 +381,9 @@ static vote_status ensure_level(vote_ctx *c, int l, size_t recs, size_t cells) {
 
 static RecView rec_view(vote_ctx *c, int l) {
     RecView v;
-    std::memset(&v, 0, sizeof(v));
-    for (int j = 0; j < c->P.nd; ++j) v.qf[j] = (int32_t *)c->ls[l].qf[j].p;
-    for (int m = 0; m < c->P.le; ++m) v.qt[m] = (int32_t *)c->ls[l].qt[m].p;
+    v.rec = (uint32_t *)c->ls[l].rec.p;
     v.mult = c->group ? (uint32_t *)c->ls[l].mult.p : nullptr;
-    v.cell = (uint32_t *)c->ls[l].cell.p;
+    v.tile_cell = (uint32_t *)c->ls[l].tile_cell.p;
     return v;
 }
 
@@ -364,92 +435,6 @@ static void ev_collect(vote_ctx *c) {
 // search
 // ---------------------------------------------------------------------------
 
-// Second half of a two-level step: the chunk ch of level-l cells has been counted
-// and its surviving children (level l+1, nc1 cells holding nrec1 records) laid out
-// in ls[l+1].  Their records are not written; k_test2 derives them from the level-l
-// records, counts the grandchildren, and writes the surviving grandchildren's
-// records into ls[l+2].  The level-(l+1) cells are then fully expanded.
-static vote_status expand_two(vote_ctx *c, int l, Chunk &ch, int64_t nr, int64_t nc1, int64_t nrec1) {
-    const Problem &P = c->P;
-    const Level &lev1 = c->lev[l + 1];
-    const int ns = c->ns;
-    int NB = P.fam == VOTE_LINE2D ? 1 : (P.fam == VOTE_PLANE3D_SPH ? 3 : 2);
-    int nvalid1 = 0;
-    for (int g = 0; g < ns; ++g)
-        if (!(g & ~lev1.split_mask)) ++nvalid1;
-    size_t nch1 = (size_t)nc1 * ns;
-    TRY(ensure(c, c->alive1, nc1));
-    TRY(ensure(c, c->geo64b, nch1 * NB * 8));
-    TRY(ensure(c, c->geo32b, (size_t)nc1 * (ns + 1) * NB * 4));
-    TRY(ensure(c, c->cntb, nch1 * 12));
-    TRY(ensure(c, c->pm2, (size_t)nr * ns));
-    TRY(ensure(c, c->child_idxb, nch1 * 4));
-    TRY(ensure(c, c->cursorb, nch1 * 4));
-    TRY(ensure(c, c->keepflag, nch1 * 4));
-    TRY(ensure(c, c->recn, nch1 * 4));
-    TRY(ensure(c, c->bsums, ((nch1 + 255) / 256) * 16 + 16));
-    if (!lev1.leaf_children) TRY(ensure_level(c, l + 2, 0, nch1));
-    CK(cudaMemsetAsync(c->cntb.p, 0, nch1 * 12, c->stream));
-    CK(cudaMemsetAsync(c->cursorb.p, 0, nch1 * 4, c->stream));
-    CK(cudaMemsetAsync(&dsc(c)->n_cells, 0, 16, c->stream));
-    Chunk c1 = ch;
-    c1.lev = lev1;
-    c1.cells = cell_view(c, l + 1);
-    c1.c0 = 0;
-    c1.nc = (int)nc1;
-    c1.r0 = c1.r1 = 0;
-    c1.alive = (uint8_t *)c->alive1.p;
-    c1.geo64 = (double *)c->geo64b.p;
-    c1.geo32 = (float *)c->geo32b.p;
-    c1.cnt = (uint32_t *)c->cntb.p;
-    c1.passmask = nullptr;
-    c1.child_idx = (int32_t *)c->child_idxb.p;
-    c1.cursor = (uint32_t *)c->cursorb.p;
-    if (!lev1.leaf_children) {
-        c1.next_cells = cell_view(c, l + 2);
-        c1.out = rec_view(c, l + 2);
-    }
-    ev_mark(c, -1);
-    launch_cell_geo(c1, c->stream);
-    ev_mark(c, VOTE_K_CELL_GEO);
-    launch_test2(ch, c1, false, nullptr, (uint8_t *)c->pm2.p, c->stream);
-    ev_mark(c, VOTE_K_TEST_COUNT);
-    launch_child_lbmax(c1, c->stream);
-    launch_child_alloc(c1, (uint32_t *)c->keepflag.p, (uint32_t *)c->recn.p, (unsigned long long *)c->bsums.p,
-                       c->stream);
-    ev_mark(c, VOTE_K_CHILDREN);
-    CK(cudaGetLastError());
-    int rec_bytes = 4 * (P.nd + P.le + 1 + (c->group ? 1 : 0));
-    c->kbytes[VOTE_K_TEST_COUNT] += (double)nr * (rec_bytes + 1 + ns);
-    c->stats.launches += lev1.leaf_children ? 4 : 6;
-    c->stats.cells += nc1;
-    c->stats.records += nrec1;
-    c->lv_cells[l + 1] += nc1;
-    c->lv_recs[l + 1] += nrec1;
-    c->ls[l + 1].ncells = 0;
-    c->ls[l + 1].nrecs = 0;
-    if (lev1.leaf_children) {
-        c->stats.leaves += nc1 * nvalid1;
-        return VOTE_OK;
-    }
-    CK(cudaMemcpyAsync(&c->h_sc->n_cells, &dsc(c)->n_cells, 16, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    int64_t nc2 = (int64_t)c->h_sc->n_cells, nrec2 = (int64_t)c->h_sc->n_recs;
-    if (nrec2 > 0) {
-        TRY(ensure_level(c, l + 2, (size_t)nrec2, 0));
-        c1.out = rec_view(c, l + 2);
-        launch_test2(ch, c1, true, (const uint8_t *)c->pm2.p, nullptr, c->stream);
-        CK(cudaGetLastError());
-        c->stats.launches += 1;
-        ev_mark(c, VOTE_K_TEST_EMIT);
-        c->kbytes[VOTE_K_TEST_EMIT] += (double)nr * (rec_bytes + 1 + ns) + (double)nrec2 * rec_bytes;
-    }
-    c->ls[l + 2].ncells = nc2;
-    c->ls[l + 2].nrecs = nrec2;
-    if (nrec2 > c->stats.peak_records) c->stats.peak_records = nrec2;
-    return VOTE_OK;
-}
-
 // Expand a chunk of level-l cells taken from the top of the level's stack.  With
 // only >= 0, the single cell `only` is expanded where it sits instead (greedy
 // dive); its UB is then set to 0, so the sweep later finds it below every
@@ -458,10 +443,11 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     const Problem &P = c->P;
     LevelStore &S = c->ls[l];
     const int ns = c->ns;
+    const Level &lev = c->lev[l];
     int nvalid = 0;
     for (int s = 0; s < ns; ++s)
-        if (!(s & ~c->lev[l].split_mask)) ++nvalid;
-    // chunk: cells [c0, ncells) from the top of the stack, about chunk_records records
+        if (!(s & ~lev.split_mask)) ++nvalid;
+    // chunk: cells [c0, c1) from the top of the stack, about chunk_records records
     int64_t c1 = only >= 0 ? only + 1 : S.ncells, r1 = S.nrecs;
     int64_t avg = S.nrecs / (S.ncells > 0 ? S.ncells : 1);
     int64_t K = c->chunk_records / (avg > 0 ? avg : 1);
@@ -477,22 +463,22 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
         ev_collect(c);
         r0 = (int64_t)c->h_tmp[0];
         if (only >= 0) {
-            r1 = r0 + (int64_t)(uint32_t)c->h_tmp[1];
+            r1 = r0 + (((int64_t)(uint32_t)c->h_tmp[1] + 31) & ~(int64_t)31);
             break;
         }
         if (r1 - r0 <= 2 * c->chunk_records || K == 1) break;
         K = K / 2;
     }
-    int nc = (int)(c1 - c0);
-    int64_t nr = r1 - r0;
-    const Level &lev = c->lev[l];
-    int NB = P.fam == VOTE_LINE2D ? 1 : (P.fam == VOTE_PLANE3D_SPH ? 3 : 2);
-    size_t nch = (size_t)nc * ns;
+    nvtxRangePushA("expand_chunk");
+    const int nc = (int)(c1 - c0);
+    const int nfs = 1 << P.k;
+    const int NB = P.fam == VOTE_LINE2D ? 1 : (P.fam == VOTE_PLANE3D_SPH ? 3 : 2);
+    const int gf = geo32_floats(nfs, P.nd, P.le);
+    const size_t nch = (size_t)nc * ns;
     TRY(ensure(c, c->alive, nc));
-    TRY(ensure(c, c->geo64, nch * NB * 8));
-    TRY(ensure(c, c->geo32, (size_t)nc * (ns + 1) * NB * 4));
+    TRY(ensure(c, c->geo64, (size_t)nc * nfs * NB * 8));
+    TRY(ensure(c, c->geo32, (size_t)nc * gf * 4));
     TRY(ensure(c, c->cnt, nch * 12));
-    TRY(ensure(c, c->passmask, (size_t)nr));
     TRY(ensure(c, c->child_idx, nch * 4));
     TRY(ensure(c, c->cursor, nch * 4));
     TRY(ensure(c, c->keepflag, nch * 4));
@@ -503,47 +489,6 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     CK(cudaMemsetAsync(c->cursor.p, 0, nch * 4, c->stream));
     CK(cudaMemsetAsync(&dsc(c)->n_cells, 0, 16, c->stream));
 
-    RecView in = rec_view(c, l);
-    int64_t g_r0 = r0, g_r1 = r1;
-    if (c->group && nr > 1) {
-        // canonization's grouping: merge records with equal (cell, q_f, q_t)
-        size_t cap = 1;
-        while (cap < (size_t)nr * 2) cap <<= 1;
-        TRY(ensure(c, c->g_table, cap * 4));
-        TRY(ensure(c, c->g_owner, (size_t)nr * 4));
-        TRY(ensure(c, c->g_newpos, (size_t)nr * 4));
-        TRY(ensure(c, c->g_ccount, (size_t)nc * 4));
-        TRY(ensure(c, c->g_ccur, (size_t)nc * 4));
-        for (int j = 0; j < P.nd; ++j) TRY(ensure(c, c->g_qf[j], (size_t)nr * 4));
-        for (int m = 0; m < P.le; ++m) TRY(ensure(c, c->g_qt[m], (size_t)nr * 4));
-        TRY(ensure(c, c->g_mult, (size_t)nr * 4));
-        TRY(ensure(c, c->g_cell, (size_t)nr * 4));
-        CK(cudaMemsetAsync(c->g_table.p, 0, cap * 4, c->stream));
-        CK(cudaMemsetAsync(c->g_ccount.p, 0, (size_t)nc * 4, c->stream));
-        CK(cudaMemsetAsync(c->g_ccur.p, 0, (size_t)nc * 4, c->stream));
-        RecView gv;
-        std::memset(&gv, 0, sizeof(gv));
-        for (int j = 0; j < P.nd; ++j) gv.qf[j] = (int32_t *)c->g_qf[j].p;
-        for (int m = 0; m < P.le; ++m) gv.qt[m] = (int32_t *)c->g_qt[m].p;
-        gv.mult = (uint32_t *)c->g_mult.p;
-        gv.cell = (uint32_t *)c->g_cell.p;
-        ev_mark(c, -1);
-        launch_group(P, in, r0, nr, c0, nc, (uint32_t *)c->g_table.p, (uint32_t)(cap - 1), (uint32_t *)c->g_owner.p,
-                     (uint32_t *)c->g_ccount.p, (uint32_t *)c->g_ccur.p, (uint32_t *)c->g_newpos.p,
-                     (unsigned long long *)c->h_tmp_dev(), gv, dsc(c), c->stream);
-        ev_mark(c, VOTE_K_GROUP);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(c->h_tmp, c->h_tmp_dev(), 8, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        int64_t ng = (int64_t)*c->h_tmp;
-        c->stats.launches += 4;
-        c->kbytes[VOTE_K_GROUP] += (double)nr * (4 * (P.nd + P.le + 2)) * 2;
-        c->grouped_away += nr - ng;
-        in = gv;
-        g_r0 = 0;
-        g_r1 = ng;
-        if (nr > 0) TRY(ensure(c, c->passmask, (size_t)ng));
-    }
     Chunk ch;
     std::memset(&ch, 0, sizeof(ch));
     ch.P = P;
@@ -551,20 +496,18 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     ch.cells = cell_view(c, l);
     ch.c0 = c0;
     ch.nc = nc;
-    ch.in = in;
-    ch.r0 = g_r0;
-    ch.r1 = g_r1;
+    ch.in = rec_view(c, l);
+    ch.in_rbeg = (const uint64_t *)S.rbeg.p;
+    ch.in_rcnt = (const uint32_t *)S.rcnt.p;
+    ch.in_c0 = c0;
+    ch.t0 = r0 / 32;
+    ch.t1 = r1 / 32;
     ch.alive = (uint8_t *)c->alive.p;
     ch.geo64 = (double *)c->geo64.p;
     ch.geo32 = (float *)c->geo32.p;
     ch.cnt = (uint32_t *)c->cnt.p;
-    ch.passmask = (uint8_t *)c->passmask.p;
     ch.child_idx = (int32_t *)c->child_idx.p;
     ch.cursor = (uint32_t *)c->cursor.p;
-    if (!lev.leaf_children) {
-        ch.next_cells = cell_view(c, l + 1);
-        ch.out = rec_view(c, l + 1);
-    }
     ch.sc = dsc(c);
     if (c->trace_cap > 0) {
         ch.trace.cap = (unsigned long long)c->trace_cap;
@@ -576,26 +519,77 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     ch.prune = c->prune;
     ch.precision = c->precision;
 
-    int rec_bytes = 4 * (P.nd + P.le + 1 + (c->group ? 1 : 0));
-    nr = g_r1 - g_r0;                 // records actually tested (after grouping)
+    const int rb = rec_bytes_at(c, l);
+    if (c->group && r1 - r0 > 32) {
+        // canonization's grouping: merge records with equal (cell, q_f, q_t)
+        const size_t nr = (size_t)(r1 - r0);
+        size_t cap = 1;
+        while (cap < nr * 2) cap <<= 1;
+        TRY(ensure(c, c->g_table, cap * 4));
+        TRY(ensure(c, c->g_owner, nr * 4));
+        TRY(ensure(c, c->g_newpos, nr * 4));
+        TRY(ensure(c, c->g_ccount, (size_t)nc * 4));
+        TRY(ensure(c, c->g_ccur, (size_t)nc * 4));
+        TRY(ensure(c, c->g_rbeg, (size_t)nc * 8));
+        // canonical records need at most the slots of the originals plus one tile per cell
+        const size_t gslots = nr + 32 * (size_t)nc;
+        TRY(ensure(c, c->g_rec, gslots * rb));
+        TRY(ensure(c, c->g_mult, gslots * 4));
+        TRY(ensure(c, c->g_tile, (gslots / 32) * 4));
+        CK(cudaMemsetAsync(c->g_table.p, 0, cap * 4, c->stream));
+        CK(cudaMemsetAsync(c->g_ccount.p, 0, (size_t)nc * 4, c->stream));
+        CK(cudaMemsetAsync(c->g_ccur.p, 0, (size_t)nc * 4, c->stream));
+        RecView gv;
+        gv.rec = (uint32_t *)c->g_rec.p;
+        gv.mult = (uint32_t *)c->g_mult.p;
+        gv.tile_cell = (uint32_t *)c->g_tile.p;
+        ev_mark(c, -1);
+        launch_group(ch, (uint32_t *)c->g_table.p, (uint32_t)(cap - 1), (uint32_t *)c->g_owner.p,
+                     (uint32_t *)c->g_ccount.p, (uint32_t *)c->g_ccur.p, (uint32_t *)c->g_newpos.p,
+                     (uint64_t *)c->g_rbeg.p, (unsigned long long *)c->h_tmp_dev(), gv, c->stream);
+        ev_mark(c, VOTE_K_GROUP);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(c->h_tmp, c->h_tmp_dev(), 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const int64_t gs = (int64_t)*c->h_tmp;
+        c->stats.launches += 4;
+        c->kbytes[VOTE_K_GROUP] += (double)nr * (rb + 4) * 2;
+        c->grouped_away += (int64_t)nr - gs;
+        ch.in = gv;
+        ch.in_rbeg = (const uint64_t *)c->g_rbeg.p;
+        ch.in_rcnt = (const uint32_t *)c->g_ccount.p;
+        ch.in_c0 = 0;
+        ch.t0 = 0;
+        ch.t1 = gs / 32;
+    }
+    const int64_t nt = ch.t1 - ch.t0;
+    TRY(ensure(c, c->tinfo, (size_t)(nt > 0 ? nt : 1) * 8 + 16));
+    TRY(ensure(c, c->ballot, (size_t)(nt > 0 ? nt : 1) * ns * 4));
+    ch.tinfo = (int2 *)c->tinfo.p;
+    ch.ballot = (uint32_t *)c->ballot.p;
+    if (!lev.leaf_children) {
+        ch.next_cells = cell_view(c, l + 1);
+        ch.out = rec_view(c, l + 1);
+    }
     ev_mark(c, -1);
     launch_cell_geo(ch, c->stream);
+    launch_tile_info(ch, c->stream);
     ev_mark(c, VOTE_K_CELL_GEO);
-    launch_test(ch, false, c->stream);
+    launch_count(ch, c->stream);
     ev_mark(c, VOTE_K_TEST_COUNT);
     launch_child_lbmax(ch, c->stream);
     launch_child_alloc(ch, (uint32_t *)c->keepflag.p, (uint32_t *)c->recn.p, (unsigned long long *)c->bsums.p,
                        c->stream);
     ev_mark(c, VOTE_K_CHILDREN);
-    c->kbytes[VOTE_K_TEST_COUNT] += (double)nr * (rec_bytes + 1);
+    // algorithmic bytes: the records of whole tiles read, the ballots written
+    c->kbytes[VOTE_K_TEST_COUNT] += (double)nt * 32 * rb + (double)nt * ns * 4;
     c->kbytes[VOTE_K_CELL_GEO] += (double)nc * (8 + 4);
     CK(cudaGetLastError());
     c->stats.chunks++;
-    c->stats.launches += lev.leaf_children ? 4 : 6;
+    c->stats.launches += lev.leaf_children ? 5 : 7;
     c->stats.cells += nc;
-    c->stats.records += nr;
     c->lv_cells[l] += nc;
-    c->lv_recs[l] += nr;
+    c->lv_recs[l] += nt * 32;
     if (only >= 0) {
         CK(cudaMemsetAsync((uint32_t *)S.ub.p + only, 0, 4, c->stream));
     } else {
@@ -604,28 +598,35 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     }
     if (lev.leaf_children) {
         c->stats.leaves += (int64_t)nc * nvalid;
+        nvtxRangePop();
         return VOTE_OK;
     }
     CK(cudaMemcpyAsync(&c->h_sc->n_cells, &dsc(c)->n_cells, 16, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    int64_t new_cells = (int64_t)c->h_sc->n_cells, new_recs = (int64_t)c->h_sc->n_recs;
-    // two levels per read only pays when parent cells hold whole tiles of records
-    // (blocks then stay on one cell and reduce in registers)
-    if (c->two_level > 0 && l + 2 <= P.L && new_cells > 0 && (double)new_recs > c->two_level * (double)nr &&
-        (c->two_level < 1e-3 || nr >= 2048 * (int64_t)nc))
-        return expand_two(c, l, ch, nr, new_cells, new_recs);
-    if (new_recs > 0) {
-        TRY(ensure_level(c, l + 1, (size_t)new_recs, 0));
+    int64_t new_cells = (int64_t)c->h_sc->n_cells, new_slots = (int64_t)c->h_sc->n_recs;
+    if (new_slots > 0) {
+        TRY(ensure_level(c, l + 1, (size_t)new_slots, 0));
+        TRY(ensure(c, c->tdst, (size_t)nt * ns * 8));
         ch.out = rec_view(c, l + 1);
-        launch_test(ch, true, c->stream);
-        c->stats.launches += 1;
+        ch.tdst = (unsigned long long *)c->tdst.p;
+        ev_mark(c, -1);
+        launch_next_tiles(ch, new_cells, c->stream);
+        launch_tile_dst(ch, c->stream);
+        ev_mark(c, VOTE_K_CHILDREN);
+        if (!launch_emit(ch, c->stream)) {
+            set_err("internal: no emit pass for record formats %d -> %d", lev.q16, lev.q16_next);
+            return VOTE_EINTERNAL;
+        }
+        c->stats.launches += 3;
         ev_mark(c, VOTE_K_TEST_EMIT);
-        c->kbytes[VOTE_K_TEST_EMIT] += (double)nr * (rec_bytes + 1) + (double)new_recs * rec_bytes;
+        c->kbytes[VOTE_K_TEST_EMIT] += (double)nt * 32 * rb + (double)nt * ns * 4 +
+                                       (double)new_slots * rec_bytes_at(c, l + 1);
     }
     CK(cudaGetLastError());
     c->ls[l + 1].ncells = new_cells;
-    c->ls[l + 1].nrecs = new_recs;
-    if (new_recs > c->stats.peak_records) c->stats.peak_records = new_recs;
+    c->ls[l + 1].nrecs = new_slots;
+    if (new_slots > c->stats.peak_records) c->stats.peak_records = new_slots;
+    nvtxRangePop();
     return VOTE_OK;
 }
 
@@ -651,8 +652,32 @@ static vote_status replay(vote_ctx *c, const double *surfaces, int64_t n, int la
 // pruning they buy (the whole search is then a few chunks).
 static const int64_t kDiveMinN = 1 << 17;
 
+static vote_status solve_inner(vote_ctx *c, const double *surfaces, int64_t n, double *best_point,
+                               int64_t *best_leaf, int64_t *depth, uint32_t *mask);
+
+// Per-level counters of the last solve on stderr (VOTE_LOG=1).
+static void log_solve(const vote_ctx *c, vote_status st) {
+    const vote_stats &x = c->stats;
+    std::fprintf(stderr, "[vote] family %d L %d status %d: %.3f s, %lld tests, %lld FP64 rechecks, %lld chunks, "
+                 "%lld launches, peak %lld record slots\n", c->P.fam, c->P.L, (int)st, x.seconds,
+                 (long long)x.tests, (long long)x.rechecks, (long long)x.chunks, (long long)x.launches,
+                 (long long)x.peak_records);
+    for (int l = 0; l < c->P.L; ++l)
+        std::fprintf(stderr, "[vote]   level %2d: %lld cells expanded, %lld record slots tested, records %s\n", l,
+                     (long long)c->lv_cells[l], (long long)c->lv_recs[l], c->lev[l].q16 ? "16-bit" : "32-bit");
+}
+
 static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, double *best_point,
                                 int64_t *best_leaf, int64_t *depth, uint32_t *mask) {
+    nvtxRangePushA("vote_solve");
+    vote_status st = solve_inner(c, surfaces, n, best_point, best_leaf, depth, mask);
+    nvtxRangePop();
+    if (c->log) log_solve(c, st);
+    return st;
+}
+
+static vote_status solve_inner(vote_ctx *c, const double *surfaces, int64_t n, double *best_point,
+                               int64_t *best_leaf, int64_t *depth, uint32_t *mask) {
     auto t0 = std::chrono::steady_clock::now();
     const Problem &P = c->P;
     std::memset(&c->stats, 0, sizeof(c->stats));
@@ -679,7 +704,8 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
     if (n > 0 && P.L == 0) {
         dep = n;                                   // the domain is a leaf: every surface counts
     } else if (n > 0) {
-        TRY(ensure_level(c, 0, (size_t)n, 1));
+        const int64_t slots0 = (n + 31) & ~(int64_t)31;
+        TRY(ensure_level(c, 0, (size_t)slots0, 1));
         ev_mark(c, -1);
         launch_lift(P, c->lev[0], surfaces, n, rec_view(c, 0), dsc(c), c->stream);
         c->stats.launches += 1;
@@ -693,14 +719,15 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         CK(cudaMemcpyAsync(c->ls[0].ub.p, &cnt0, 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));    // host sources above live on this frame
         c->ls[0].ncells = 1;
-        c->ls[0].nrecs = n;
+        c->ls[0].nrecs = slots0;
         TRY(read_scalars(c));
         ev_collect(c);
-        c->kbytes[VOTE_K_LIFT] += (double)n * (8 * P.np + 4 * (P.nd + P.le + 1 + (c->group ? 1 : 0)));
+        c->kbytes[VOTE_K_LIFT] += (double)n * (8 * P.np + rec_bytes_at(c, 0) + (c->group ? 4 : 0));
         if (c->h_sc->err) {
             set_err("surface parameters are not finite or out of the representable range");
             return VOTE_EINVAL;
         }
+        finalize_levels(c, c->h_sc->qmax);
         if (c->dive == 1 || (c->dive == 2 && n >= kDiveMinN)) {
             // greedy dive: from the root, expand only the child with the largest UB
             // (the first on ties) down to the leaves, so the sweep starts with a
@@ -735,6 +762,10 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
         }
         TRY(read_scalars(c));
         ev_collect(c);
+        if (c->h_sc->err & kErrTimeout) {
+            set_err("a bounded device-side wait ran out (bulk copy not completed)");
+            return VOTE_ETIMEOUT;
+        }
         if (c->h_sc->err) {
             set_err("internal: residual out of range (err %u)", c->h_sc->err);
             return VOTE_EINTERNAL;
@@ -745,6 +776,7 @@ static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, 
             leafkey = ~bk & ((1ull << P.coord_bits) - 1ull);
         }
         c->stats.tests = (int64_t)c->h_sc->tests;
+        c->stats.records = (int64_t)c->h_sc->records;
         c->stats.rechecks = (int64_t)c->h_sc->rechecks;
         c->trace_written = (int64_t)c->h_sc->trace_n;
         if (c->trace_cap && c->trace_written > c->trace_cap) c->trace_overflow = true;
@@ -801,6 +833,7 @@ vote_status vote_create(int family, int d, int k, const double *eps, const doubl
     // 3DoF prunes well and needs fine depth-first steps
     c->chunk_records = family == VOTE_PLANE3D_SPH ? (int64_t)1 << 27 : (int64_t)1 << 25;
     c->family = family;
+    if (const char *lg = std::getenv("VOTE_LOG")) c->log = std::atoi(lg) > 0;
     for (int j = 0; j < d; ++j) {
         c->eps_in[j] = eps[j];
         c->bounds_in[2 * j] = bounds[2 * j];
@@ -879,10 +912,6 @@ vote_status vote_set_option(vote_ctx *c, int key, double v) {
             for (int i = 0; i < vote_ctx::kEv; ++i) CK(cudaEventCreate(&c->ev[i]));
         c->kernel_timing = (int)v;
         return VOTE_OK;
-    case VOTE_OPT_TWO_LEVEL:
-        if (!(v >= 0 && v <= 1e6)) break;
-        c->two_level = v;
-        return VOTE_OK;
     case VOTE_OPT_BATCH_WORKERS:
         if (!(v >= 1 && v <= 32)) break;
         c->batch_workers = (int)v;
@@ -956,7 +985,6 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
         w->precision = c->precision;
         w->prune = c->prune;
         w->chunk_records = c->chunk_records;
-        w->two_level = c->two_level;
         w->dive = c->dive;
         w->group = c->group;
         w->fault_alloc_at = 0;
@@ -1228,19 +1256,16 @@ void vote_destroy(vote_ctx *c) {
     c->workers.clear();
     for (int l = 0; l <= GV_MAXL; ++l) {
         LevelStore &s = c->ls[l];
-        for (int j = 0; j < GV_MAXD; ++j) release(c, s.qf[j]);
-        for (int m = 0; m < GV_MAXT; ++m) release(c, s.qt[m]);
-        release(c, s.mult); release(c, s.cell); release(c, s.key); release(c, s.rbeg); release(c, s.rcnt); release(c, s.ub);
+        release(c, s.rec); release(c, s.mult); release(c, s.tile_cell);
+        release(c, s.key); release(c, s.rbeg); release(c, s.rcnt); release(c, s.ub);
     }
-    DevBuf *bufs[] = {&c->levs_dev, &c->path, &c->scal, &c->alive, &c->geo64, &c->geo32, &c->cnt, &c->passmask,
+    DevBuf *bufs[] = {&c->levs_dev, &c->path, &c->scal, &c->alive, &c->geo64, &c->geo32, &c->cnt, &c->tinfo,
+                      &c->ballot, &c->tdst,
                       &c->child_idx, &c->cursor, &c->keepflag, &c->recn, &c->bsums, &c->tr_level, &c->tr_key,
-                      &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp, &c->alive1, &c->geo64b,
-                      &c->geo32b, &c->cntb, &c->pm2, &c->child_idxb, &c->cursorb, &c->ss_partial,
+                      &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp, &c->ss_partial,
                       &c->ss_io, &c->g_table, &c->g_owner, &c->g_newpos, &c->g_ccount, &c->g_ccur,
-                      &c->g_mult, &c->g_cell};
+                      &c->g_rbeg, &c->g_rec, &c->g_mult, &c->g_tile};
     for (DevBuf *b : bufs) release(c, *b);
-    for (int j = 0; j < GV_MAXD; ++j) release(c, c->g_qf[j]);
-    for (int m = 0; m < GV_MAXT; ++m) release(c, c->g_qt[m]);
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < vote_ctx::kEv; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);

@@ -6,20 +6,18 @@
 //   k_cell_geo    per cell of a chunk: pruning re-check and the change of the
 //                 family's basis functions from the cell centre to each child
 //                 centre (own sin/cos, FP64)
-//   k_test        the cell x surface proximity test ("eps plus the cell radius"),
-//                 count pass (UB / LB / record count per child, warp-reduced) and
-//                 emit pass (child records, snapped for the next level)
+//   (k_count, k_emit: the proximity test itself, in gv_count.cu and gv_emit.cu)
 //   k_child_*     best lower bound, pruning, allocation of surviving children,
 //                 leaf argmax as a packed 64-bit atomicMax
 //   k_path_geo,   replay of every original surface along one root-to-cell path:
 //   k_replay      inlier mask of the best leaf and per-cell counts
 #include <cstdio>
+#include <map>
+#include <mutex>
 
-#include "gv_kernels.h"
+#include "gv_tile.cuh"
 
 namespace gv {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ unsigned prune_threshold(const Problem &P, const Scalars *sc, int prune) {
     if (!prune) return 1u;
@@ -30,12 +28,6 @@ __device__ __forceinline__ unsigned prune_threshold(const Problem &P, const Scal
     return t > 1u ? t : 1u;
 }
 
-// round-half-even of q/2: re-snap of an essential parameter when the step doubles
-__device__ __forceinline__ int32_t resnap_half(int32_t q) {
-    int32_t k = q >> 1;
-    return k + ((q & 1) & (k & 1));
-}
-
 // ---------------------------------------------------------------------------
 // A0 lift
 // ---------------------------------------------------------------------------
@@ -43,28 +35,48 @@ template <int FAM>
 __global__ void k_lift(Problem P, Level lev0, const double *__restrict__ prm, int64_t n, RecView out,
                        Scalars *sc) {
     using F = Fam<FAM>;
+    constexpr int NW = rec_words(F::NFP, false);
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double c[F::D], psi[F::NB], f[F::ND], t[F::LE];
+    const int lane = threadIdx.x & 31;
+    unsigned qa[F::ND + F::LE];
 #pragma unroll
-    for (int j = 0; j < F::D; ++j) c[j] = cell_center(P, lev0.h, j, 0);
-    F::basis(c, psi);
-    F::lift(prm, n, i, c, psi, f, t);
+    for (int x = 0; x < F::ND + F::LE; ++x) qa[x] = 0u;
     bool bad = false;
+    if (i < n) {
+        double c[F::D], psi[F::NB], f[F::ND], t[F::LE];
 #pragma unroll
-    for (int j = 0; j < F::ND; ++j) {
-        double q = rint(dmul(f[j], P.inv_s_f[j]));
-        bad |= !(fabs(q) < 1073741824.0);
-        out.qf[j][i] = bad ? 0 : (int32_t)q;
-    }
+        for (int j = 0; j < F::D; ++j) c[j] = cell_center(P, lev0.h, j, 0);
+        F::basis(c, psi);
+        F::lift(prm, n, i, c, psi, f, t);
+        uint32_t w[NW];
 #pragma unroll
-    for (int m = 0; m < F::LE; ++m) {
-        double q = rint(dmul(t[m], lev0.inv_s_t[m]));
-        bad |= !(fabs(q) < 1073741824.0);
-        out.qt[m][i] = bad ? 0 : (int32_t)q;
+        for (int x = 0; x < NW; ++x) w[x] = 0u;
+#pragma unroll
+        for (int j = 0; j < F::ND; ++j) {
+            double q = rint(dmul(f[j], P.inv_s_f[j]));
+            bad |= !(fabs(q) < 1073741824.0);
+            int qi = bad ? 0 : (int)q;
+            w[j] = (uint32_t)qi;
+            qa[j] = (unsigned)abs(qi);
+        }
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) {
+            double q = rint(dmul(t[m], lev0.inv_s_t[m]));
+            bad |= !(fabs(q) < 1073741824.0);
+            int qi = bad ? 0 : (int)q;
+            w[F::ND + m] = (uint32_t)qi;
+            qa[F::ND + m] = (unsigned)abs(qi);
+        }
+        store_words<NW>(out.rec, i, w);
+        if (out.mult) out.mult[i] = 1u;
+        if ((i & 31) == 0) out.tile_cell[i >> 5] = 0u;
     }
-    if (out.mult) out.mult[i] = 1u;
-    out.cell[i] = 0u;
+    // largest |q| per field (it sets the screen's band and the record formats)
+#pragma unroll
+    for (int x = 0; x < F::ND + F::LE; ++x) {
+        unsigned m = __reduce_max_sync(kFull, qa[x]);
+        if (lane == 0 && m) atomicMax(&sc->qmax[x], m);
+    }
     if (bad) atomicOr(&sc->err, 1u);
 }
 
@@ -106,135 +118,56 @@ __device__ __forceinline__ void parent_psi(const Problem &P, const Level &lev, u
 }
 
 // One thread per (cell, free-coordinate child slot fs); the 2^k threads of a cell
-// are consecutive lanes and combine their max |dpsi| by shuffles.
+// are consecutive lanes.  Writes the FP64 basis changes (for the exact recheck) and
+// the screen's coefficients G[fs][j][m] = coef_jm(dpsi) * s_t,m / s_f,j rounded to
+// FP32, and per (j, m) the largest |G| over the child slots (rounded up), which
+// bounds the magnitudes the screen's band scales with.
 template <int FAM>
 __global__ void k_cell_geo(Chunk c) {
     using F = Fam<FAM>;
-    constexpr int NS = 1 << F::D;
     constexpr int NF = 1 << F::K;
+    constexpr int GF = geo32_floats(NF, F::ND, F::LE);
     static_assert(32 % NF == 0, "a cell's threads must lie in one warp");
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int cell = gid / NF, fs = gid % NF;
     const bool in = cell < c.nc;
     const Problem &P = c.P;
     const Level &lev = c.lev;
-    float mx[F::NB];
+    float ga[F::ND * F::LE];
 #pragma unroll
-    for (int m = 0; m < F::NB; ++m) mx[m] = 0.0f;
+    for (int x = 0; x < F::ND * F::LE; ++x) ga[x] = 0.0f;
     if (in) {
         if (fs == 0) {
             unsigned thr = prune_threshold(P, c.sc, c.prune);
             c.alive[cell] = c.cells.ub[c.c0 + cell] >= thr ? 1 : 0;
         }
+        double dpsi[F::NB];
+#pragma unroll
+        for (int m = 0; m < F::NB; ++m) dpsi[m] = 0.0;
         if (!(fs & ~lev.split_mask & (NF - 1))) {
             uint64_t key = c.cells.key[c.c0 + cell];
             double psi_par[F::NB];
             parent_psi<FAM>(P, lev, key, psi_par);
-            double dpsi[F::NB];
             child_dpsi<FAM>(P, lev, key, fs, psi_par, dpsi);
-            for (int s = fs; s < NS; s += NF) {          // dependent-coordinate bits share psi
-                if (s & ~lev.split_mask) continue;
+        }
 #pragma unroll
-                for (int m = 0; m < F::NB; ++m) {
-                    c.geo64[((size_t)cell * NS + s) * F::NB + m] = dpsi[m];
-                    c.geo32[((size_t)cell * (NS + 1) + s) * F::NB + m] = (float)dpsi[m];
-                }
-            }
+        for (int m = 0; m < F::NB; ++m) c.geo64[((size_t)cell * NF + fs) * F::NB + m] = dpsi[m];
+        double g[F::ND * F::LE];
+        F::coef(dpsi, g);
 #pragma unroll
-            for (int m = 0; m < F::NB; ++m) mx[m] = fabsf((float)dpsi[m]);
+        for (int x = 0; x < F::ND * F::LE; ++x) {
+            const double gx = g[x] * lev.gscale[x / F::LE][x % F::LE];
+            c.geo32[(size_t)cell * GF + fs * F::ND * F::LE + x] = (float)gx;
+            ga[x] = __double2float_ru(fabs(gx));
         }
     }
 #pragma unroll
     for (int o = 1; o < NF; o <<= 1)
 #pragma unroll
-        for (int m = 0; m < F::NB; ++m) mx[m] = fmaxf(mx[m], __shfl_xor_sync(kFull, mx[m], o));
+        for (int x = 0; x < F::ND * F::LE; ++x) ga[x] = fmaxf(ga[x], __shfl_xor_sync(kFull, ga[x], o));
     if (in && fs == 0)
 #pragma unroll
-        for (int m = 0; m < F::NB; ++m) c.geo32[((size_t)cell * (NS + 1) + NS) * F::NB + m] = mx[m];
-}
-
-// ---------------------------------------------------------------------------
-// A4 proximity test (count pass and emit pass) and A6 emission
-// ---------------------------------------------------------------------------
-template <int FAM>
-__device__ __forceinline__ void shifts64(const Level &lev, int s, double *sh) {
-    using F = Fam<FAM>;
-#pragma unroll
-    for (int j = 0; j < F::D; ++j) {
-        bool split = (lev.split_mask >> j) & 1;
-        sh[j] = split ? (((s >> j) & 1) ? lev.h1[j] : -lev.h1[j]) : 0.0;
-    }
-}
-
-template <int FAM>
-__device__ __forceinline__ void shifts32(const Level &lev, int s, float *sh) {
-    using F = Fam<FAM>;
-#pragma unroll
-    for (int j = 0; j < F::D; ++j) {
-        bool split = (lev.split_mask >> j) & 1;
-        sh[j] = split ? (((s >> j) & 1) ? lev.h1f[j] : -lev.h1f[j]) : 0.0f;
-    }
-}
-
-// FP64 upper-bound radius of a record (Lipschitz test): R_j = ((eps_j + h1_j) +
-// sum_i lam_ji h1_i) + A1_j, in this order.
-template <int FAM>
-__device__ __forceinline__ void radius64(const Level &lev, const double *t, double *R) {
-    using F = Fam<FAM>;
-    double lam[F::ND * F::K];
-    F::lipschitz64(t, lam);
-#pragma unroll
-    for (int j = 0; j < F::ND; ++j) {
-        double r = lev.Rbase[j];
-#pragma unroll
-        for (int i = 0; i < F::K; ++i) r = dadd(r, dmul(lam[j * F::K + i], lev.h1[i]));
-        R[j] = dadd(r, lev.A1[j]);
-    }
-}
-
-// exact FP64 test of one (record, child): bit 0 UB pass, bit 1 LB pass
-template <int FAM>
-__device__ __forceinline__ int test64(const Level &lev, const double *f, const double *t, const double *R,
-                                      const double *dpsi, int s, double *fo) {
-    using F = Fam<FAM>;
-    double sh[F::D];
-    shifts64<FAM>(lev, s, sh);
-    F::residual64(f, t, dpsi, sh, fo);
-    int ub = 1, lb = 1;
-#pragma unroll
-    for (int j = 0; j < F::ND; ++j) {
-        double a = fabs(fo[j]);
-        ub &= a <= R[j];
-        lb &= a <= lev.rlb[j];
-    }
-    return ub | (lb << 1);
-}
-
-// Bits 0-3 of x moved to bits 0, 8, 16, 24 (the four shifted copies of x do not
-// overlap, so the product has no carries).
-__device__ __forceinline__ unsigned spread4(unsigned x) { return (x * 0x00204081u) & 0x01010101u; }
-
-// Lanes of a warp hold consecutive records and a cell's records are contiguous, so
-// the lanes of one cell form one run of lanes.  Returns the calling lane's run (key:
-// the lane's cell, or -1 for a lane without a record).
-__device__ __forceinline__ unsigned run_mask(int key, int lane) {
-    int prev = __shfl_up_sync(kFull, key, 1);
-    unsigned heads = __ballot_sync(kFull, lane == 0 || prev != key);
-    unsigned upto = lane == 31 ? kFull : ((2u << lane) - 1u);     // lanes 0..lane
-    int start = 31 - __clz(heads & upto);
-    unsigned after = heads & ~upto;
-    unsigned below_end = after ? ((1u << (__ffs(after) - 1)) - 1u) : kFull;
-    return below_end & ~((1u << start) - 1u);
-}
-
-// Child slots that exist at this level (slots that split only unsplit coordinates do not).
-template <int NS>
-__device__ __forceinline__ unsigned valid_slots(int smask) {
-    unsigned v = 0;
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-        if (!(s & ~smask)) v |= 1u << s;
-    return v;
+        for (int x = 0; x < F::ND * F::LE; ++x) c.geo32[(size_t)cell * GF + NF * F::ND * F::LE + x] = ga[x];
 }
 
 // Block-wide exclusive scan of one 64-bit value per thread (blockDim = 256).
@@ -263,871 +196,6 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
     *total = warp_tot[7];
     __syncthreads();
     return before + x - v;
-}
-
-// Per-record state of the proximity test: the canonical record in FP32 (screen)
-// and, on demand, in FP64 (exact definition).
-template <int FAM, int PREC>
-struct RecState {
-    using F = Fam<FAM>;
-    int32_t qf[F::ND], qt[F::LE];
-    uint32_t mult;
-    float f32[F::ND], t32[F::LE], R32[F::ND], Eub[F::ND], Elb[F::ND];
-    double f64[F::ND], t64[F::LE], R64[F::ND];
-    bool have64;
-
-    __device__ __forceinline__ void load(const RecView &in, int64_t r) {
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) qf[j] = in.qf[j][r];
-#pragma unroll
-        for (int m = 0; m < F::LE; ++m) qt[m] = in.qt[m][r];
-        mult = in.mult ? in.mult[r] : 1u;
-        have64 = false;
-    }
-    __device__ __forceinline__ void set(const int32_t *qf_, const int32_t *qt_, uint32_t mult_) {
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) qf[j] = qf_[j];
-#pragma unroll
-        for (int m = 0; m < F::LE; ++m) qt[m] = qt_[m];
-        mult = mult_;
-        have64 = false;
-    }
-    __device__ __forceinline__ void need64(const Problem &P, const Level &lev) {
-        if (have64) return;
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) f64[j] = dmul((double)qf[j], P.s_f[j]);
-#pragma unroll
-        for (int m = 0; m < F::LE; ++m) t64[m] = dmul((double)qt[m], lev.s_t[m]);
-        radius64<FAM>(lev, t64, R64);
-        have64 = true;
-    }
-    // FP32 values and the screen's error margins; gmax = max |dpsi| over children
-    __device__ __forceinline__ void prep32(const Problem &P, const Level &lev, const float *gmax) {
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) f32[j] = (float)qf[j] * P.s_ff[j];
-#pragma unroll
-        for (int m = 0; m < F::LE; ++m) t32[m] = (float)qt[m] * lev.s_tf[m];
-        float lam[F::ND * F::K];
-        F::lipschitz32(t32, lam);
-        float shmax[F::D], err[F::ND];
-#pragma unroll
-        for (int j = 0; j < F::D; ++j) shmax[j] = ((lev.split_mask >> j) & 1) ? lev.h1f[j] : 0.0f;
-        F::errmag32(f32, t32, gmax, shmax, err);
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) {
-            float rr = lev.Rbasef[j];
-#pragma unroll
-            for (int i = 0; i < F::K; ++i) rr = rr + lam[j * F::K + i] * lev.h1f[i];
-            R32[j] = rr + lev.A1f[j];
-            Eub[j] = kScreenRel * (err[j] + R32[j]);
-            Elb[j] = kScreenRel * (err[j] + fabsf(lev.rlbf[j]));
-        }
-    }
-};
-
-// Signed shift of dependent coordinate j (index k + j) for child slot s.
-template <int FAM>
-__device__ __forceinline__ double dep_shift64(const Level &lev, int j, int s) {
-    constexpr int K = Fam<FAM>::K;
-    bool split = (lev.split_mask >> (K + j)) & 1;
-    return split ? (((s >> (K + j)) & 1) ? lev.h1[K + j] : -lev.h1[K + j]) : 0.0;
-}
-template <int FAM>
-__device__ __forceinline__ float dep_shift32(const Level &lev, int j, int s) {
-    constexpr int K = Fam<FAM>::K;
-    bool split = (lev.split_mask >> (K + j)) & 1;
-    return split ? (((s >> (K + j)) & 1) ? lev.h1f[K + j] : -lev.h1f[K + j]) : 0.0f;
-}
-
-// UB/LB decisions of one record against every child.  g32 / g64: the cell's basis
-// changes per child slot ([slot][NB]; slots that differ only in dependent bits share
-// them).  Returns the UB-pass and LB-pass slot masks; counts FP64 rechecks.
-template <int FAM, int PREC>
-__device__ __forceinline__ void eval_record(const Problem &P, const Level &lev, RecState<FAM, PREC> &st,
-                                            const float *g32, const double *g64, unsigned &ubm, unsigned &lbm,
-                                            unsigned &nrechk) {
-    using F = Fam<FAM>;
-    constexpr int NS = 1 << F::D;
-    constexpr int NF = 1 << F::K;
-    const int smask = lev.split_mask;
-    ubm = 0;
-    lbm = 0;
-    unsigned unsure = 0;
-#pragma unroll
-    for (int fs = 0; fs < NF; ++fs) {
-        if (fs & ~smask) continue;
-        if (PREC == 0) {
-            double pr[F::ND];
-            F::partial64(st.f64, st.t64, g64 + fs * F::NB, pr);
-#pragma unroll
-            for (int s = fs; s < NS; s += NF) {
-                if (s & ~smask) continue;
-                int ub = 1, lb = 1;
-#pragma unroll
-                for (int j = 0; j < F::ND; ++j) {
-                    double a = fabs(dsub(pr[j], dep_shift64<FAM>(lev, j, s)));
-                    ub &= a <= st.R64[j];
-                    lb &= a <= lev.rlb[j];
-                }
-                ubm |= (unsigned)ub << s;
-                lbm |= (unsigned)lb << s;
-            }
-        } else {
-            float pr[F::ND];
-            F::partial32(st.f32, st.t32, g32 + fs * F::NB, pr);
-#pragma unroll
-            for (int s = fs; s < NS; s += NF) {
-                if (s & ~smask) continue;
-                // pass bits from the signs of |f'| - R; a slot is uncertain when a
-                // margin is within the screen's error bound (the UB test's, or the
-                // LB test's when the UB test passes)
-                bool ub = true, lb = true, bu = false, bl = false;
-#pragma unroll
-                for (int j = 0; j < F::ND; ++j) {
-                    float a = fabsf(pr[j] - dep_shift32<FAM>(lev, j, s));
-                    float du = a - st.R32[j], dl = a - lev.rlbf[j];
-                    ub &= du < 0.0f;
-                    lb &= dl < 0.0f;
-                    bu |= fabsf(du) <= st.Eub[j];
-                    bl |= fabsf(dl) <= st.Elb[j];
-                }
-                ubm |= (unsigned)ub << s;
-                lbm |= (unsigned)(ub & lb) << s;
-                unsure |= (unsigned)(bu | (ub & bl)) << s;
-            }
-        }
-    }
-    if (PREC == 1 && unsure) {
-        // the FP32 screen could not decide these children: exact FP64 test (one
-        // copy of the code, not unrolled)
-        ubm &= ~unsure;
-        lbm &= ~unsure;
-        st.need64(P, lev);
-#pragma unroll 1
-        for (unsigned u = unsure; u; u &= u - 1) {
-            int s = __ffs(u) - 1;
-            ++nrechk;
-            double pr[F::ND];
-            F::partial64(st.f64, st.t64, g64 + (s & (NF - 1)) * F::NB, pr);
-            int ub = 1, lb = 1;
-#pragma unroll
-            for (int j = 0; j < F::ND; ++j) {
-                double a = fabs(dsub(pr[j], dep_shift64<FAM>(lev, j, s)));
-                ub &= a <= st.R64[j];
-                lb &= a <= lev.rlb[j];
-            }
-            ubm |= (unsigned)ub << s;
-            lbm |= (unsigned)lb << s;
-        }
-    }
-}
-
-// Exact FP64 snap of one child residual, out of line: the FP32 screen needs it
-// rarely, and one shared copy keeps the emit kernels' instruction footprint small.
-// Everything is passed by value (no reference to kernel parameters).
-struct Snap64In {
-    int32_t qf[2], qt[3];
-    double sf[2], st[3], inv[2], sh[2];
-    const double *g64;   // basis changes of the child ([NB] doubles)
-};
-
-template <int FAM>
-__device__ __noinline__ void snap64(Snap64In a, int32_t *qn, Scalars *sc) {
-    using F = Fam<FAM>;
-    double f[2], t[3], pr[2];
-#pragma unroll
-    for (int j = 0; j < F::ND; ++j) f[j] = dmul((double)a.qf[j], a.sf[j]);
-#pragma unroll
-    for (int m = 0; m < F::LE; ++m) t[m] = dmul((double)a.qt[m], a.st[m]);
-    F::partial64(f, t, a.g64, pr);
-#pragma unroll
-    for (int j = 0; j < F::ND; ++j) {
-        double q = rint(dmul(dsub(pr[j], a.sh[j]), a.inv[j]));
-        if (!(fabs(q) < 1073741824.0)) {
-            atomicOr(&sc->err, 2u);
-            q = 0.0;
-        }
-        qn[j] = (int32_t)q;
-    }
-}
-
-// Snapped free parameters of the record's surface at the centre of child s.
-template <int FAM, int PREC>
-__device__ __forceinline__ void child_qf(const Problem &P, const Level &lev, RecState<FAM, PREC> &st,
-                                         const float *g32, const double *g64, int s, int32_t *qn, unsigned &nrechk,
-                                         Scalars *sc) {
-    using F = Fam<FAM>;
-    constexpr int NF = 1 << F::K;
-    const int fs = s & (NF - 1);
-    bool done = false;
-    if (PREC == 1) {
-        float pr[F::ND];
-        F::partial32(st.f32, st.t32, g32 + fs * F::NB, pr);
-        done = true;
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) {
-            float y = (pr[j] - dep_shift32<FAM>(lev, j, s)) * P.inv_s_ff[j];
-            float q = rintf(y);
-            float margin = 0.5f - fabsf(y - q);
-            if (margin > st.Eub[j] * P.inv_s_ff[j] && fabsf(q) < 1.6e7f) qn[j] = (int32_t)q;
-            else done = false;
-        }
-        if (!done) ++nrechk;
-    }
-    if (!done) {
-        Snap64In a;
-#pragma unroll
-        for (int j = 0; j < F::ND; ++j) {
-            a.qf[j] = st.qf[j];
-            a.sf[j] = P.s_f[j];
-            a.inv[j] = P.inv_s_f[j];
-            a.sh[j] = dep_shift64<FAM>(lev, j, s);
-        }
-#pragma unroll
-        for (int m = 0; m < F::LE; ++m) {
-            a.qt[m] = st.qt[m];
-            a.st[m] = lev.s_t[m];
-        }
-        a.g64 = g64 + fs * F::NB;
-        snap64<FAM>(a, qn, sc);
-    }
-}
-
-template <int FAM, int PREC>
-__device__ __forceinline__ void write_child(const Chunk &c, const RecState<FAM, PREC> &st, const int32_t *qn,
-                                            int ci, uint64_t at) {
-    using F = Fam<FAM>;
-#pragma unroll
-    for (int j = 0; j < F::ND; ++j) c.out.qf[j][at] = qn[j];
-#pragma unroll
-    for (int m = 0; m < F::LE; ++m) c.out.qt[m][at] = c.lev.st_ratio_log2[m] ? resnap_half(st.qt[m]) : st.qt[m];
-    if (c.out.mult) c.out.mult[at] = st.mult;
-    c.out.cell[at] = (uint32_t)ci;
-}
-
-// Tile shape of the proximity kernels: 4 records per thread in the count pass, 2 in
-// the emit pass, at least 5 blocks of 256 threads per SM (48 registers).  Measured
-// fastest on GB300 among 2-4 records per thread and 4-6 blocks per SM.
-#ifndef GV_KRPT
-#define GV_KRPT 4
-#endif
-#ifndef GV_MINBLOCKS
-#define GV_MINBLOCKS 5
-#endif
-constexpr int kRPT = GV_KRPT;        // records per thread in one tile (count pass, two-level)
-#ifndef GV_KRPT_EMIT
-#define GV_KRPT_EMIT 2
-#endif
-constexpr int kRPTEmit = GV_KRPT_EMIT;  // records per thread in one tile (emit pass)
-constexpr int kTile = 256 * kRPT;    // records per block
-constexpr int kSpanCells = 64;       // tiles spanning at most this many cells count in shared memory
-
-// Proximity test of a chunk's records against all children of their cells.
-// Count pass (EMIT = false): per child UB = sum of mult over UB-passing records,
-// LB likewise, and the number of passing records; per record the UB-pass mask.
-// Emit pass (EMIT = true): every UB-passing record of a surviving child is
-// written into the child's record range, snapped for the next level.
-// A block takes a tile of kTile consecutive records.  Records are sorted by cell,
-// so a tile whose first and last record share a cell lies in one cell: then the
-// cell's geometry is staged in shared memory, counts are reduced in registers
-// and across the block (one global atomic per counter), and the emit pass
-// reserves the child ranges with one atomic per child and a block scan.  Tiles
-// spanning several cells fall back to warp-level aggregation.
-template <int FAM, int PREC, bool EMIT>
-__global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test(Chunk c) {
-    using F = Fam<FAM>;
-    constexpr int NS = 1 << F::D;
-    constexpr int RPT = EMIT ? kRPTEmit : kRPT;   // records per thread (tuned per pass)
-    constexpr int TILE = 256 * RPT;
-    const Problem &P = c.P;
-    const Level &lev = c.lev;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int smask = lev.split_mask;
-    __shared__ float s_g32[(NS + 1) * F::NB];
-    __shared__ double s_g64[NS * F::NB];
-    __shared__ unsigned s_red[8][3 * NS];
-    __shared__ int s_ci[NS];
-    __shared__ unsigned long long s_base[NS];
-    __shared__ unsigned s_span[kSpanCells * NS * 3];
-    __shared__ unsigned s_xw[2 * NS];
-    const int64_t t0 = c.r0 + (int64_t)blockIdx.x * TILE;
-    const int64_t t1 = t0 + TILE < c.r1 ? t0 + TILE : c.r1;
-    // This thread's records (and, in the emit pass, their pass masks) are loaded
-    // first, so that their latency overlaps the tile's classification and the
-    // staging of the cell's geometry.
-    int32_t pqf[RPT][F::ND], pqt[RPT][F::LE];
-    uint32_t pmult[RPT], ppm[RPT];
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        int64_t r = t0 + threadIdx.x + k * 256;
-        ppm[k] = 0;
-        if (r < t1) {
-#pragma unroll
-            for (int j = 0; j < F::ND; ++j) pqf[k][j] = c.in.qf[j][r];
-#pragma unroll
-            for (int m = 0; m < F::LE; ++m) pqt[k][m] = c.in.qt[m][r];
-            pmult[k] = c.in.mult ? c.in.mult[r] : 1u;
-            if (EMIT) ppm[k] = c.passmask[r - c.r0];
-        }
-    }
-    const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
-    const int clast = (int)((int64_t)c.in.cell[t1 - 1] - c.c0);
-    unsigned nrechk = 0, ntest = 0;
-    if (cfirst == clast) {
-        // ------------------------------ one cell ------------------------------
-        const int cl = cfirst;
-        if (!c.alive[cl]) return;                        // uniform: whole block exits
-        for (int i = threadIdx.x; i < (NS + 1) * F::NB; i += blockDim.x)
-            s_g32[i] = c.geo32[(size_t)cl * (NS + 1) * F::NB + i];
-        for (int i = threadIdx.x; i < NS * F::NB; i += blockDim.x) s_g64[i] = c.geo64[(size_t)cl * NS * F::NB + i];
-        if (EMIT && threadIdx.x < NS) s_ci[threadIdx.x] = c.child_idx[(size_t)cl * NS + threadIdx.x];
-        if (!EMIT && threadIdx.x < 2 * NS) s_xw[threadIdx.x] = 0u;
-        __syncthreads();
-        if (!EMIT) {
-            // Per-slot pass counts packed one byte per slot (slots 0-3 in pu[0]/pl[0],
-            // 4-7 in pu[1]/pl[1]): a thread adds at most RPT per byte and a warp at most
-            // 32 * RPT < 256, so no byte carries into the next.  The weight of a record
-            // beyond 1 (multiplicity after grouping) goes to shared counters.
-            static_assert(32 * RPT < 256, "packed per-slot counters would overflow a byte");
-            constexpr int NW = NS > 4 ? 2 : 1;
-            unsigned pu[NW], pl[NW];
-#pragma unroll
-            for (int w = 0; w < NW; ++w) pu[w] = pl[w] = 0u;
-            unsigned nrec = 0;
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                int64_t r = t0 + threadIdx.x + k * 256;
-                if (r < t1) {
-                    RecState<FAM, PREC> st;
-                    st.set(pqf[k], pqt[k], pmult[k]);
-                    if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
-                    else st.need64(P, lev);
-                    unsigned ubm, lbm;
-                    eval_record<FAM, PREC>(P, lev, st, s_g32, s_g64, ubm, lbm, nrechk);
-                    c.passmask[r - c.r0] = (uint8_t)ubm;
-                    ++nrec;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        pu[w] += spread4((ubm >> (4 * w)) & 15u);
-                        pl[w] += spread4((lbm >> (4 * w)) & 15u);
-                    }
-                    if (st.mult != 1u) {
-                        unsigned x = st.mult - 1u;
-                        for (unsigned b = ubm; b; b &= b - 1) atomicAdd(&s_xw[2 * (__ffs(b) - 1)], x);
-                        for (unsigned b = lbm; b; b &= b - 1) atomicAdd(&s_xw[2 * (__ffs(b) - 1) + 1], x);
-                    }
-                }
-            }
-            ntest = nrec * (unsigned)__popc(valid_slots<NS>(smask));
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                unsigned a = __reduce_add_sync(kFull, pu[w]);
-                unsigned b = __reduce_add_sync(kFull, pl[w]);
-                if (lane == 0) {
-#pragma unroll
-                    for (int q = 0; q < 4 && 4 * w + q < NS; ++q) {
-                        unsigned na = (a >> (8 * q)) & 255u, nb = (b >> (8 * q)) & 255u;
-                        s_red[warp][3 * (4 * w + q)] = na;
-                        s_red[warp][3 * (4 * w + q) + 1] = nb;
-                        s_red[warp][3 * (4 * w + q) + 2] = na;
-                    }
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x < 3 * NS) {
-                unsigned v = 0;
-#pragma unroll
-                for (int w = 0; w < 8; ++w) v += s_red[w][threadIdx.x];
-                int s = threadIdx.x / 3, f = threadIdx.x % 3;
-                if (f < 2) v += s_xw[2 * s + f];   // UB and LB sums are weighted by multiplicity
-                if (v) atomicAdd(c.cnt + (size_t)cl * NS * 3 + threadIdx.x, v);
-            }
-        } else {
-            // Positions in (k, warp, lane) order so that each warp's stores for one
-            // child are contiguous: per k and slot, warp counts are scanned in smem.
-            __shared__ unsigned s_wcnt[RPT][8][NS];
-            unsigned em[RPT];
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                int64_t r = t0 + threadIdx.x + k * 256;
-                unsigned m = 0;
-                if (r < t1) {
-                    m = ppm[k];
-#pragma unroll
-                    for (int s = 0; s < NS; ++s)
-                        if (s_ci[s] < 0) m &= ~(1u << s);
-                }
-                em[k] = m;
-#pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    unsigned b = __ballot_sync(kFull, (m >> s) & 1);
-                    if (lane == 0) s_wcnt[k][warp][s] = __popc(b);
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x < NS) {
-                int s = threadIdx.x;
-                unsigned run = 0;
-                for (int k = 0; k < RPT; ++k)
-                    for (int w = 0; w < 8; ++w) {
-                        unsigned v = s_wcnt[k][w][s];
-                        s_wcnt[k][w][s] = run;
-                        run += v;
-                    }
-                s_base[s] = (run && s_ci[s] >= 0) ? atomicAdd(&c.cursor[(size_t)cl * NS + s], run) : 0;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                unsigned m = em[k];
-                int64_t r = t0 + threadIdx.x + k * 256;
-                RecState<FAM, PREC> st;
-                if (m) {
-                    st.set(pqf[k], pqt[k], pmult[k]);
-                    if (PREC == 1) st.prep32(P, lev, s_g32 + NS * F::NB);
-                }
-                // only the slots some lane of the warp writes; one copy of the body
-#pragma unroll 1
-                for (unsigned u = __reduce_or_sync(kFull, m); u; u &= u - 1) {
-                    const int s = __ffs(u) - 1;
-                    unsigned b = __ballot_sync(kFull, (m >> s) & 1);
-                    if (!((m >> s) & 1)) continue;
-                    unsigned pos = (unsigned)s_base[s] + s_wcnt[k][warp][s] + __popc(b & ((1u << lane) - 1u));
-                    int32_t qn[F::ND];
-                    child_qf<FAM, PREC>(P, lev, st, s_g32, s_g64, s, qn, nrechk, c.sc);
-                    int ci = s_ci[s];
-                    write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos);
-                }
-            }
-        }
-    } else if (clast - cfirst < kSpanCells) {
-        // ------------------ a few cells: shared-memory counters -------------------
-        const int span = clast - cfirst + 1;
-        for (int i = threadIdx.x; i < span * NS * 3; i += blockDim.x) s_span[i] = 0u;
-        __syncthreads();
-        if (!EMIT) {
-#pragma unroll 1
-            for (int k = 0; k < RPT; ++k) {
-                int64_t r = t0 + threadIdx.x + k * 256;
-                if (r >= t1) break;
-                int cl = (int)((int64_t)c.in.cell[r] - c.c0);
-                if (!c.alive[cl]) continue;
-                RecState<FAM, PREC> st;
-                st.load(c.in, r);
-                if (PREC == 1) st.prep32(P, lev, c.geo32 + ((size_t)cl * (NS + 1) + NS) * F::NB);
-                else st.need64(P, lev);
-                unsigned ubm, lbm;
-                eval_record<FAM, PREC>(P, lev, st, c.geo32 + (size_t)cl * (NS + 1) * F::NB,
-                                       c.geo64 + (size_t)cl * NS * F::NB, ubm, lbm, nrechk);
-                c.passmask[r - c.r0] = (uint8_t)ubm;
-                unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
-                for (int s = 0; s < NS; ++s) {
-                    if (s & ~smask) continue;
-                    ++ntest;
-                    if ((ubm >> s) & 1) {
-                        atomicAdd(cnt + 3 * s, st.mult);
-                        atomicAdd(cnt + 3 * s + 2, 1u);
-                    }
-                    if ((lbm >> s) & 1) atomicAdd(cnt + 3 * s + 1, st.mult);
-                }
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < span * NS * 3; i += blockDim.x)
-                if (s_span[i]) atomicAdd(c.cnt + (size_t)cfirst * NS * 3 + i, s_span[i]);
-        } else {
-            // count this block's records per (cell, child), reserve each child's range
-            // with one global atomic, then place records by shared-memory ranks
-            unsigned em[RPT];
-            int ck[RPT];
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                int64_t r = t0 + threadIdx.x + k * 256;
-                unsigned m = 0;
-                ck[k] = -1;
-                if (r < t1) {
-                    int cl = (int)((int64_t)c.in.cell[r] - c.c0);
-                    ck[k] = cl;
-                    if (c.alive[cl]) {
-                        m = ppm[k];
-                        for (int s = 0; s < NS; ++s)
-                            if (((m >> s) & 1) && c.child_idx[(size_t)cl * NS + s] < 0) m &= ~(1u << s);
-                        unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
-                        for (int s = 0; s < NS; ++s)
-                            if ((m >> s) & 1) atomicAdd(cnt + 3 * s, 1u);
-                    }
-                }
-                em[k] = m;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < span * NS; i += blockDim.x) {
-                unsigned v = s_span[3 * i];
-                if (v) s_span[3 * i + 1] = atomicAdd(&c.cursor[(size_t)cfirst * NS + i], v);
-                s_span[3 * i + 2] = 0u;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                unsigned m = em[k];
-                unsigned wm = __reduce_or_sync(kFull, m);
-                if (!wm) continue;                                  // uniform
-                const unsigned run = run_mask(ck[k], lane);
-                int cl = ck[k] < 0 ? cfirst : ck[k];
-                const float *g32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
-                const double *g64 = c.geo64 + (size_t)cl * NS * F::NB;
-                RecState<FAM, PREC> st;
-                if (m) {
-                    st.set(pqf[k], pqt[k], pmult[k]);
-                    if (PREC == 1) st.prep32(P, lev, g32 + NS * F::NB);
-                }
-                unsigned *cnt = s_span + (cl - cfirst) * NS * 3;
-#pragma unroll 1
-                for (unsigned u = wm; u; u &= u - 1) {
-                    const int s = __ffs(u) - 1;
-                    bool want = (m >> s) & 1;
-                    // lanes of one cell writing to the same child form a group: one
-                    // shared atomic per group, contiguous positions inside it
-                    unsigned grp = __ballot_sync(kFull, want) & run;
-                    int leader = __ffs(grp) - 1;
-                    unsigned base = 0;
-                    if (want && lane == leader) base = atomicAdd(cnt + 3 * s + 2, (unsigned)__popc(grp));
-                    base = __shfl_sync(kFull, base, want ? leader : lane);
-                    if (!want) continue;
-                    unsigned pos = cnt[3 * s + 1] + base + __popc(grp & ((1u << lane) - 1u));
-                    int32_t qn[F::ND];
-                    child_qf<FAM, PREC>(P, lev, st, g32, g64, s, qn, nrechk, c.sc);
-                    int ci = c.child_idx[(size_t)cl * NS + s];
-                    write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos);
-                }
-            }
-        }
-    } else {
-        // --------------------------- many cells ----------------------------
-#pragma unroll 1
-        for (int k = 0; k < RPT; ++k) {
-            int64_t r = t0 + threadIdx.x + k * 256;
-            bool act = false;
-            int cl = 0;
-            RecState<FAM, PREC> st;
-            if (r < t1) {
-                cl = (int)((int64_t)c.in.cell[r] - c.c0);
-                act = c.alive[cl] != 0;
-                if (act) {
-                    st.load(c.in, r);
-                    if (PREC == 1) st.prep32(P, lev, c.geo32 + ((size_t)cl * (NS + 1) + NS) * F::NB);
-                    else st.need64(P, lev);
-                }
-            }
-            const float *g32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
-            const double *g64 = c.geo64 + (size_t)cl * NS * F::NB;
-            unsigned actb = __ballot_sync(kFull, act);
-            if (!actb) continue;
-            int leader = __ffs(actb) - 1;
-            int cl0 = __shfl_sync(kFull, cl, leader);
-            if (!EMIT) {
-                unsigned ubm = 0, lbm = 0;
-                if (act) {
-                    eval_record<FAM, PREC>(P, lev, st, g32, g64, ubm, lbm, nrechk);
-                    c.passmask[r - c.r0] = (uint8_t)ubm;
-                }
-                bool uniform = __all_sync(kFull, !act || cl == cl0);
-#pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    if (s & ~smask) continue;
-                    if (act) ++ntest;
-                    unsigned pu = act && ((ubm >> s) & 1);
-                    unsigned vub = pu ? st.mult : 0u, vlb = (act && ((lbm >> s) & 1)) ? st.mult : 0u;
-                    if (uniform) {
-                        vub = __reduce_add_sync(kFull, vub);
-                        vlb = __reduce_add_sync(kFull, vlb);
-                        unsigned vn = __reduce_add_sync(kFull, pu);
-                        if (lane == leader) {
-                            uint32_t *b = c.cnt + ((size_t)cl0 * NS + s) * 3;
-                            if (vub) atomicAdd(b, vub);
-                            if (vlb) atomicAdd(b + 1, vlb);
-                            if (vn) atomicAdd(b + 2, vn);
-                        }
-                    } else if (pu) {
-                        uint32_t *b = c.cnt + ((size_t)cl * NS + s) * 3;
-                        atomicAdd(b, vub);
-                        if (vlb) atomicAdd(b + 1, vlb);
-                        atomicAdd(b + 2, 1u);
-                    }
-                }
-            } else {
-                unsigned ubm = act ? c.passmask[r - c.r0] : 0u;
-                const unsigned run = run_mask(r < t1 ? cl : -1, lane);
-#pragma unroll 1
-                for (unsigned u = __reduce_or_sync(kFull, ubm); u; u &= u - 1) {
-                    const int s = __ffs(u) - 1;
-                    bool want = (ubm >> s) & 1;
-                    int ci = -1;
-                    if (want) {
-                        ci = c.child_idx[(size_t)cl * NS + s];
-                        want = ci >= 0;
-                    }
-                    // one global atomic per (cell, child) group of lanes
-                    unsigned grp = __ballot_sync(kFull, want) & run;
-                    int ldr = __ffs(grp) - 1;
-                    unsigned base = 0;
-                    if (want && lane == ldr) base = atomicAdd(&c.cursor[(size_t)cl * NS + s], (unsigned)__popc(grp));
-                    base = __shfl_sync(kFull, base, want ? ldr : lane);
-                    if (!want) continue;
-                    unsigned pos = base + __popc(grp & ((1u << lane) - 1u));
-                    int32_t qn[F::ND];
-                    child_qf<FAM, PREC>(P, lev, st, g32, g64, s, qn, nrechk, c.sc);
-                    write_child<FAM, PREC>(c, st, qn, ci, c.next_cells.rbeg[ci] + pos);
-                }
-            }
-        }
-    }
-    // counters (all threads of the block reach this point unless the block exited above)
-    ntest = __reduce_add_sync(kFull, ntest);
-    nrechk = __reduce_add_sync(kFull, nrechk);
-    if (lane == 0) {
-        if (!EMIT && ntest) atomicAdd(&c.sc->tests, (unsigned long long)ntest);
-        if (nrechk) atomicAdd(&c.sc->rechecks, (unsigned long long)nrechk);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Two levels per record read.  c is a chunk of level-l cells whose counts, child
-// cells (level l+1, in c1.cells) and UB-pass masks are known; c1 describes those
-// child cells (their geometry, alive flags, grandchild counters, grandchild cells
-// in c1.next_cells).  The level-(l+1) records are never written: each block takes a
-// tile of level-l records and one child slot s, re-derives the child record of
-// every record that passes child s (residual at the child centre, snapped for
-// level l+1) and tests it against the grandchildren.  Count pass: grandchild
-// UB/LB/record counts and the grandchild pass mask per (record, s).  Emit pass:
-// the grandchild records, snapped for level l+2.
-// ---------------------------------------------------------------------------
-template <int FAM, int PREC>
-__device__ __forceinline__ void derive_child(const Problem &P, const Level &lev, RecState<FAM, PREC> &st,
-                                             const float *g32, const double *g64, int s, RecState<FAM, PREC> &ch,
-                                             unsigned &nrechk, Scalars *sc) {
-    using F = Fam<FAM>;
-    int32_t qn[F::ND], qt[F::LE];
-    child_qf<FAM, PREC>(P, lev, st, g32, g64, s, qn, nrechk, sc);
-#pragma unroll
-    for (int m = 0; m < F::LE; ++m) qt[m] = lev.st_ratio_log2[m] ? resnap_half(st.qt[m]) : st.qt[m];
-    ch.set(qn, qt, st.mult);
-}
-
-template <int FAM, int PREC, bool EMIT>
-__global__ void __launch_bounds__(256, GV_MINBLOCKS) k_test2(Chunk c, Chunk c1, const uint8_t *__restrict__ pm2_in,
-                                                   uint8_t *pm2_out) {
-    using F = Fam<FAM>;
-    constexpr int NS = 1 << F::D;
-    const Problem &P = c.P;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int s = blockIdx.x % NS;
-    const int64_t tile = blockIdx.x / NS;
-    __shared__ float s_pg32[(NS + 1) * F::NB], s_cg32[(NS + 1) * F::NB];
-    __shared__ double s_pg64[NS * F::NB], s_cg64[NS * F::NB];
-    __shared__ unsigned s_red[8][3 * NS];
-    __shared__ int s_gi[NS];
-    __shared__ unsigned long long s_base[NS];
-    __shared__ unsigned s_wcnt[kRPT][8][NS];
-    __shared__ int s_list[kTile];
-    __shared__ uint8_t s_em[kTile];
-    __shared__ unsigned s_n;
-    if (s & ~c.lev.split_mask) return;
-    const int64_t t0 = c.r0 + tile * kTile;
-    const int64_t t1 = t0 + kTile < c.r1 ? t0 + kTile : c.r1;
-    const int cfirst = (int)((int64_t)c.in.cell[t0] - c.c0);
-    const int clast = (int)((int64_t)c.in.cell[t1 - 1] - c.c0);
-    unsigned nrechk = 0, ntest = 0;
-    if (cfirst == clast) {
-        const int cl = cfirst;
-        if (!c.alive[cl]) return;
-        const int ci = c.child_idx[(size_t)cl * NS + s];
-        if (ci < 0 || !c1.alive[ci]) return;                   // uniform over the block
-        for (int i = threadIdx.x; i < (NS + 1) * F::NB; i += blockDim.x) {
-            s_pg32[i] = c.geo32[(size_t)cl * (NS + 1) * F::NB + i];
-            s_cg32[i] = c1.geo32[(size_t)ci * (NS + 1) * F::NB + i];
-        }
-        for (int i = threadIdx.x; i < NS * F::NB; i += blockDim.x) {
-            s_pg64[i] = c.geo64[(size_t)cl * NS * F::NB + i];
-            s_cg64[i] = c1.geo64[(size_t)ci * NS * F::NB + i];
-        }
-        if (EMIT && threadIdx.x < NS) s_gi[threadIdx.x] = c1.child_idx[(size_t)ci * NS + threadIdx.x];
-        if (threadIdx.x == 0) s_n = 0;
-        __syncthreads();
-        // Compact the tile's records that have work for child s (count pass: pass
-        // child s; emit pass: also reach a surviving grandchild) so that every lane
-        // of a warp works on one.
-#pragma unroll
-        for (int k = 0; k < kRPT; ++k) {
-            int64_t r = t0 + threadIdx.x + k * 256;
-            unsigned m = 0;
-            if (r < t1 && ((c.passmask[r - c.r0] >> s) & 1)) {
-                if (!EMIT) {
-                    m = 1;
-                } else {
-                    m = pm2_in[(size_t)(r - c.r0) * NS + s];
-#pragma unroll
-                    for (int g = 0; g < NS; ++g)
-                        if (s_gi[g] < 0) m &= ~(1u << g);
-                }
-            }
-            unsigned b = __ballot_sync(kFull, m != 0);
-            unsigned base = 0;
-            if (lane == 0 && b) base = atomicAdd(&s_n, (unsigned)__popc(b));
-            base = __shfl_sync(kFull, base, 0);
-            if (m) {
-                unsigned at = base + __popc(b & ((1u << lane) - 1u));
-                s_list[at] = (int)(r - t0);
-                s_em[at] = (uint8_t)m;
-            }
-        }
-        __syncthreads();
-        const int nlist = (int)s_n;
-        if (!EMIT) {
-            unsigned aub[NS], alb[NS], an[NS];
-#pragma unroll
-            for (int g = 0; g < NS; ++g) aub[g] = alb[g] = an[g] = 0;
-#pragma unroll 1
-            for (int i = threadIdx.x; i < nlist; i += 256) {
-                int64_t r = t0 + s_list[i];
-                RecState<FAM, PREC> st, ch;
-                st.load(c.in, r);
-                if (PREC == 1) st.prep32(P, c.lev, s_pg32 + NS * F::NB);
-                derive_child<FAM, PREC>(P, c.lev, st, s_pg32, s_pg64, s, ch, nrechk, c.sc);
-                if (PREC == 1) ch.prep32(P, c1.lev, s_cg32 + NS * F::NB);
-                else ch.need64(P, c1.lev);
-                unsigned ubm, lbm;
-                eval_record<FAM, PREC>(P, c1.lev, ch, s_cg32, s_cg64, ubm, lbm, nrechk);
-                pm2_out[(size_t)(r - c.r0) * NS + s] = (uint8_t)ubm;
-#pragma unroll
-                for (int g = 0; g < NS; ++g) {
-                    if (g & ~c1.lev.split_mask) continue;
-                    ++ntest;
-                    aub[g] += ((ubm >> g) & 1) ? ch.mult : 0u;
-                    alb[g] += ((lbm >> g) & 1) ? ch.mult : 0u;
-                    an[g] += (ubm >> g) & 1;
-                }
-            }
-#pragma unroll
-            for (int g = 0; g < NS; ++g) {
-                unsigned a = __reduce_add_sync(kFull, aub[g]);
-                unsigned b = __reduce_add_sync(kFull, alb[g]);
-                unsigned d = __reduce_add_sync(kFull, an[g]);
-                if (lane == 0) {
-                    s_red[warp][3 * g] = a;
-                    s_red[warp][3 * g + 1] = b;
-                    s_red[warp][3 * g + 2] = d;
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x < 3 * NS) {
-                unsigned v = 0;
-#pragma unroll
-                for (int w = 0; w < 8; ++w) v += s_red[w][threadIdx.x];
-                if (v) atomicAdd(c1.cnt + (size_t)ci * NS * 3 + threadIdx.x, v);
-            }
-        } else {
-            // positions in (iteration, warp, lane) order over the compacted list
-#pragma unroll
-            for (int k = 0; k < kRPT; ++k) {
-                int i = threadIdx.x + k * 256;
-                unsigned m = i < nlist ? s_em[i] : 0u;
-#pragma unroll
-                for (int g = 0; g < NS; ++g) {
-                    unsigned b = __ballot_sync(kFull, (m >> g) & 1);
-                    if (lane == 0) s_wcnt[k][warp][g] = __popc(b);
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x < NS) {
-                int g = threadIdx.x;
-                unsigned run = 0;
-                for (int k = 0; k < kRPT; ++k)
-                    for (int w = 0; w < 8; ++w) {
-                        unsigned v = s_wcnt[k][w][g];
-                        s_wcnt[k][w][g] = run;
-                        run += v;
-                    }
-                s_base[g] = (run && s_gi[g] >= 0) ? atomicAdd(&c1.cursor[(size_t)ci * NS + g], run) : 0;
-            }
-            __syncthreads();
-#pragma unroll 1
-            for (int k = 0; k < kRPT; ++k) {
-                int i = threadIdx.x + k * 256;
-                if (k * 256 >= nlist) break;                     // uniform
-                unsigned m = i < nlist ? s_em[i] : 0u;
-                RecState<FAM, PREC> st, ch;
-                if (m) {
-                    int64_t r = t0 + s_list[i];
-                    st.load(c.in, r);
-                    if (PREC == 1) st.prep32(P, c.lev, s_pg32 + NS * F::NB);
-                    derive_child<FAM, PREC>(P, c.lev, st, s_pg32, s_pg64, s, ch, nrechk, c.sc);
-                    if (PREC == 1) ch.prep32(P, c1.lev, s_cg32 + NS * F::NB);
-                }
-#pragma unroll
-                for (int g = 0; g < NS; ++g) {
-                    unsigned b = __ballot_sync(kFull, (m >> g) & 1);
-                    if (!((m >> g) & 1)) continue;
-                    unsigned pos = (unsigned)s_base[g] + s_wcnt[k][warp][g] + __popc(b & ((1u << lane) - 1u));
-                    int32_t qn[F::ND];
-                    child_qf<FAM, PREC>(P, c1.lev, ch, s_cg32, s_cg64, g, qn, nrechk, c.sc);
-                    int gi = s_gi[g];
-                    write_child<FAM, PREC>(c1, ch, qn, gi, c1.next_cells.rbeg[gi] + pos);
-                }
-            }
-        }
-    } else {
-        // tile spans several level-l cells: per record, global atomics
-#pragma unroll 1
-        for (int k = 0; k < kRPT; ++k) {
-            int64_t r = t0 + threadIdx.x + k * 256;
-            if (r >= t1) break;
-            int cl = (int)((int64_t)c.in.cell[r] - c.c0);
-            if (!c.alive[cl] || !((c.passmask[r - c.r0] >> s) & 1)) continue;
-            int ci = c.child_idx[(size_t)cl * NS + s];
-            if (ci < 0 || !c1.alive[ci]) continue;
-            const float *pg32 = c.geo32 + (size_t)cl * (NS + 1) * F::NB;
-            const double *pg64 = c.geo64 + (size_t)cl * NS * F::NB;
-            const float *cg32 = c1.geo32 + (size_t)ci * (NS + 1) * F::NB;
-            const double *cg64 = c1.geo64 + (size_t)ci * NS * F::NB;
-            RecState<FAM, PREC> st, ch;
-            st.load(c.in, r);
-            if (PREC == 1) st.prep32(P, c.lev, pg32 + NS * F::NB);
-            derive_child<FAM, PREC>(P, c.lev, st, pg32, pg64, s, ch, nrechk, c.sc);
-            if (PREC == 1) ch.prep32(P, c1.lev, cg32 + NS * F::NB);
-            else ch.need64(P, c1.lev);
-            if (!EMIT) {
-                unsigned ubm, lbm;
-                eval_record<FAM, PREC>(P, c1.lev, ch, cg32, cg64, ubm, lbm, nrechk);
-                pm2_out[(size_t)(r - c.r0) * NS + s] = (uint8_t)ubm;
-                for (int g = 0; g < NS; ++g) {
-                    if (g & ~c1.lev.split_mask) continue;
-                    ++ntest;
-                    uint32_t *b = c1.cnt + ((size_t)ci * NS + g) * 3;
-                    if ((ubm >> g) & 1) {
-                        atomicAdd(b, ch.mult);
-                        atomicAdd(b + 2, 1u);
-                    }
-                    if ((lbm >> g) & 1) atomicAdd(b + 1, ch.mult);
-                }
-            } else {
-                unsigned m = pm2_in[(size_t)(r - c.r0) * NS + s];
-                for (int g = 0; g < NS; ++g) {
-                    if (!((m >> g) & 1)) continue;
-                    int gi = c1.child_idx[(size_t)ci * NS + g];
-                    if (gi < 0) continue;
-                    unsigned pos = atomicAdd(&c1.cursor[(size_t)ci * NS + g], 1u);
-                    int32_t qn[F::ND];
-                    child_qf<FAM, PREC>(P, c1.lev, ch, cg32, cg64, g, qn, nrechk, c.sc);
-                    write_child<FAM, PREC>(c1, ch, qn, gi, c1.next_cells.rbeg[gi] + pos);
-                }
-            }
-        }
-    }
-    ntest = __reduce_add_sync(kFull, ntest);
-    nrechk = __reduce_add_sync(kFull, nrechk);
-    if (lane == 0) {
-        if (!EMIT && ntest) atomicAdd(&c.sc->tests, (unsigned long long)ntest);
-        if (nrechk) atomicAdd(&c.sc->rechecks, (unsigned long long)nrechk);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1179,13 +247,15 @@ __global__ void __launch_bounds__(256) k_child_mark(Chunk c, uint32_t *keepflag,
         }
         return;
     }
+    // a child's records start at a multiple of 32 (whole tiles)
+    const unsigned slots = keep ? (nrec + 31u) & ~31u : 0u;
     if (idx < c.nc * NS) {
         keepflag[idx] = keep ? 1u : 0u;
-        recn[idx] = keep ? nrec : 0u;
+        recn[idx] = slots;
     }
     unsigned long long tc, tr;
     block_excl_scan(keep ? 1ull : 0ull, &tc);
-    block_excl_scan(keep ? (unsigned long long)nrec : 0ull, &tr);
+    block_excl_scan((unsigned long long)slots, &tr);
     if (threadIdx.x == 0) {
         bs_cells[blockIdx.x] = tc;
         bs_recs[blockIdx.x] = tr;
@@ -1215,7 +285,7 @@ __global__ void __launch_bounds__(256) k_scan_sums(unsigned long long *a, unsign
 }
 
 // Phase C: surviving children get consecutive cell indices and record ranges in
-// (parent, slot) order.
+// (parent, slot) order; recn holds the slots (record count rounded up to 32).
 template <int NS>
 __global__ void __launch_bounds__(256) k_child_write(Chunk c, const uint32_t *keepflag, const uint32_t *recn,
                                                      const unsigned long long *bs_cells,
@@ -1233,12 +303,81 @@ __global__ void __launch_bounds__(256) k_child_write(Chunk c, const uint32_t *ke
         unsigned long long ci = bs_cells[blockIdx.x] + ec;
         c.next_cells.key[ci] = child_key(c.P, c.cells.key[c.c0 + cl], c.lev.l, s);
         c.next_cells.rbeg[ci] = bs_recs[blockIdx.x] + er;
-        c.next_cells.rcnt[ci] = nrec;
+        c.next_cells.rcnt[ci] = c.cnt[(size_t)idx * 3 + 2];
         c.next_cells.ub[ci] = c.cnt[(size_t)idx * 3];
         c.child_idx[idx] = (int32_t)ci;
     } else {
         c.child_idx[idx] = -1;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Per-tile bookkeeping of the proximity test, so that the count and emit passes
+// stream their inputs with bulk copies and never chase a pointer per tile.
+// ---------------------------------------------------------------------------
+
+// per tile: the chunk-local cell (-1 if it was pruned) and how many of its 32 lanes
+// hold records
+__global__ void k_tile_info(Chunk c) {
+    const int64_t t = c.t0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= c.t1) return;
+    const int64_t cell = (int64_t)c.in.tile_cell[t];
+    const int cl = (int)(cell - c.in_c0);
+    const int64_t left = (int64_t)c.in_rbeg[cell] + (int64_t)c.in_rcnt[cell] - 32 * t;
+    c.tinfo[t - c.t0] = make_int2(c.alive[cl] ? cl : -1, left < 32 ? (int)left : 32);
+}
+
+// the next level's tile -> cell table: one warp per new cell writes its tiles
+__global__ void k_next_tiles(CellView next, RecView out, int64_t ncells) {
+    const int64_t cell = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= ncells) return;
+    const int64_t t0 = (int64_t)(next.rbeg[cell] >> 5), nt = ((int64_t)next.rcnt[cell] + 31) >> 5;
+    for (int64_t i = lane; i < nt; i += 32) out.tile_cell[t0 + i] = (uint32_t)cell;
+}
+
+// Output positions of the emit pass.  A block takes kBlockTiles consecutive tiles;
+// warp s handles child slot s with one lane per tile: a segmented scan over the
+// tiles (segments = runs of one cell) gives every tile its offset inside the run,
+// the run's last lane reserves the run's records in the child with one atomic on
+// the child's cursor, and the run's base is broadcast back.  tdst[tile][s] = first
+// slot of the tile's records in child s, or ~0 when the tile writes none there.
+template <int NS>
+__global__ void __launch_bounds__(256) k_tile_dst(Chunk c) {
+    static_assert(kBlockTiles == 32, "one lane per tile");
+    const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
+    if (s >= NS) return;
+    const int64_t t = c.t0 + (int64_t)blockIdx.x * 32 + lane;
+    const bool in = t < c.t1;
+    int cl = -1;
+    unsigned n = 0;
+    int ci = -1;
+    if (in) {
+        cl = c.tinfo[t - c.t0].x;
+        if (cl >= 0) {
+            ci = c.child_idx[(size_t)cl * NS + s];
+            if (ci >= 0) n = __popc(c.ballot[(size_t)(t - c.t0) * NS + s]);
+        }
+    }
+    // segments: maximal runs of lanes with the same cell
+    const int prev = __shfl_up_sync(kFull, cl, 1);
+    const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != cl);
+    const int next = __shfl_down_sync(kFull, cl, 1);
+    const unsigned tails = __ballot_sync(kFull, lane == 31 || next != cl);
+    const int head = 31 - __clz(heads & ((2u << lane) - 1u));          // this lane's segment head
+    // inclusive scan of n inside the segment
+    unsigned x = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(kFull, x, o);
+        if (lane - o >= head) x += y;
+    }
+    unsigned long long base = 0;
+    if (((tails >> lane) & 1) && cl >= 0 && ci >= 0 && x)
+        base = c.next_cells.rbeg[ci] + atomicAdd(&c.cursor[(size_t)cl * NS + s], x);
+    const int tail = __ffs(tails & ~((1u << lane) - 1u)) - 1;          // this lane's segment tail
+    base = __shfl_sync(kFull, base, tail);
+    if (in) c.tdst[(size_t)(t - c.t0) * NS + s] = n ? base + (x - n) : ~0ull;
 }
 
 // ---------------------------------------------------------------------------
@@ -1314,89 +453,100 @@ __global__ void __launch_bounds__(256) k_replay(Problem P, const Level *__restri
 // per-cell counts) and their multiplicities summed with integer atomics, so the
 // grouped records are deterministic up to their order inside a cell.
 // ---------------------------------------------------------------------------
-template <int ND, int LE>
-__device__ __forceinline__ bool same_key(const RecView &in, int64_t a, int64_t b) {
-    if (in.cell[a] != in.cell[b]) return false;
-#pragma unroll
-    for (int j = 0; j < ND; ++j)
-        if (in.qf[j][a] != in.qf[j][b]) return false;
-#pragma unroll
-    for (int m = 0; m < LE; ++m)
-        if (in.qt[m][a] != in.qt[m][b]) return false;
-    return true;
+// A record slot of the chunk: its chunk-local cell, or -1 for the padding after a
+// cell's last record.
+__device__ __forceinline__ int slot_cell(const Chunk &c, int64_t r) {
+    int64_t cell = (int64_t)c.in.tile_cell[r >> 5];
+    int cl = (int)(cell - c.in_c0);
+    return r < (int64_t)c.in_rbeg[cell] + (int64_t)c.in_rcnt[cell] ? cl : -1;
 }
 
-template <int ND, int LE>
-__device__ __forceinline__ uint64_t key_hash(const RecView &in, int64_t r) {
-    uint64_t h = 0x9E3779B97F4A7C15ull ^ in.cell[r];
+template <int NW>
+__device__ __forceinline__ uint64_t key_hash(int cl, const uint32_t *w) {
+    uint64_t h = 0x9E3779B97F4A7C15ull ^ (uint32_t)cl;
 #pragma unroll
-    for (int j = 0; j < ND; ++j) h = (h ^ (uint32_t)in.qf[j][r]) * 0xff51afd7ed558ccdull;
-#pragma unroll
-    for (int m = 0; m < LE; ++m) h = (h ^ (uint32_t)in.qt[m][r]) * 0xc4ceb9fe1a85ec53ull;
+    for (int i = 0; i < NW; ++i) h = (h ^ w[i]) * 0xff51afd7ed558ccdull;
     return h ^ (h >> 29);
 }
 
-template <int FAM>
-__global__ void k_group_insert(RecView in, int64_t r0, int64_t nr, int64_t c0, uint32_t *table, uint32_t tmask,
-                               uint32_t *owner, uint32_t *ccount, Scalars *sc) {
-    using F = Fam<FAM>;
+template <int FAM, bool Q16>
+__global__ void k_group_insert(Chunk c, uint32_t *table, uint32_t tmask, uint32_t *owner, uint32_t *ccount) {
+    constexpr int NW = rec_words(Fam<FAM>::NFP, Q16);
+    const int64_t nr = (c.t1 - c.t0) * 32;
     int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (x >= nr) return;
-    int64_t r = r0 + x;
-    uint32_t slot = (uint32_t)key_hash<F::ND, F::LE>(in, r) & tmask;
+    const int64_t r = c.t0 * 32 + x;
+    const int cl = slot_cell(c, r);
+    if (cl < 0) {
+        owner[x] = 0xffffffffu;
+        return;
+    }
+    uint32_t w[NW];
+    load_words<NW>(c.in.rec, r, w);
+    uint32_t slot = (uint32_t)key_hash<NW>(cl, w) & tmask;
     for (uint32_t probe = 0; probe <= tmask; ++probe) {
         uint32_t prev = atomicCAS(&table[slot], 0u, (uint32_t)(x + 1));
         if (prev == 0u) {                                   // new canonical record
             owner[x] = (uint32_t)x;
-            atomicAdd(&ccount[in.cell[r] - c0], 1u);
+            atomicAdd(&ccount[cl], 1u);
             return;
         }
-        if (same_key<F::ND, F::LE>(in, r, r0 + (int64_t)(prev - 1))) {
+        const int64_t r2 = c.t0 * 32 + (int64_t)(prev - 1);
+        bool same = slot_cell(c, r2) == cl;
+        if (same) {
+            uint32_t w2[NW];
+            load_words<NW>(c.in.rec, r2, w2);
+#pragma unroll
+            for (int i = 0; i < NW; ++i) same &= w2[i] == w[i];
+        }
+        if (same) {
             owner[x] = prev - 1;
             return;
         }
         slot = (slot + 1) & tmask;
     }
-    atomicOr(&sc->err, 4u);                                 // table full (cannot happen at load <= 1/2)
+    atomicOr(&c.sc->err, 4u);                               // table full (cannot happen at load <= 1/2)
     owner[x] = (uint32_t)x;
 }
 
-// exclusive scan of n u32 values in place (one block of 256 threads); *total = sum
-__global__ void __launch_bounds__(256) k_scan_u32(uint32_t *a, int64_t n, unsigned long long *total) {
+// exclusive scan of per-cell record counts rounded up to whole tiles (one block of
+// 256 threads): start[i], *total = slots used
+__global__ void __launch_bounds__(256) k_scan_slots(const uint32_t *cnt, uint64_t *start, int64_t n,
+                                                    unsigned long long *total) {
     unsigned long long carry = 0;
     for (int64_t base = 0; base < n; base += 256) {
         int64_t i = base + threadIdx.x;
-        unsigned long long v = i < n ? a[i] : 0u, t;
+        unsigned long long v = i < n ? (cnt[i] + 31u) & ~31u : 0u, t;
         unsigned long long e = block_excl_scan(v, &t);
-        if (i < n) a[i] = (uint32_t)(carry + e);
+        if (i < n) start[i] = carry + e;
         carry += t;
     }
     if (threadIdx.x == 0 && total) *total = carry;
 }
 
-template <int FAM>
-__global__ void k_group_place(RecView in, int64_t r0, int64_t nr, int64_t c0, const uint32_t *owner,
-                              const uint32_t *coff, uint32_t *ccur, uint32_t *newpos, RecView out) {
-    using F = Fam<FAM>;
+template <int FAM, bool Q16>
+__global__ void k_group_place(Chunk c, const uint32_t *owner, const uint64_t *grbeg, uint32_t *ccur,
+                              uint32_t *newpos, RecView out) {
+    constexpr int NW = rec_words(Fam<FAM>::NFP, Q16);
+    const int64_t nr = (c.t1 - c.t0) * 32;
     int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (x >= nr || owner[x] != (uint32_t)x) return;
-    int64_t r = r0 + x;
-    uint32_t cl = in.cell[r] - (uint32_t)c0;
-    uint32_t pos = coff[cl] + atomicAdd(&ccur[cl], 1u);
-    newpos[x] = pos;
-#pragma unroll
-    for (int j = 0; j < F::ND; ++j) out.qf[j][pos] = in.qf[j][r];
-#pragma unroll
-    for (int m = 0; m < F::LE; ++m) out.qt[m][pos] = in.qt[m][r];
-    out.cell[pos] = in.cell[r];
+    const int64_t r = c.t0 * 32 + x;
+    const int cl = slot_cell(c, r);
+    const uint64_t pos = grbeg[cl] + atomicAdd(&ccur[cl], 1u);
+    newpos[x] = (uint32_t)pos;
+    uint32_t w[NW];
+    load_words<NW>(c.in.rec, r, w);
+    store_words<NW>(out.rec, (int64_t)pos, w);
     out.mult[pos] = 0u;
+    if ((pos & 31u) == 0) out.tile_cell[pos >> 5] = (uint32_t)cl;
 }
 
-__global__ void k_group_mult(RecView in, int64_t r0, int64_t nr, const uint32_t *owner, const uint32_t *newpos,
-                             RecView out) {
+__global__ void k_group_mult(Chunk c, const uint32_t *owner, const uint32_t *newpos, RecView out) {
+    const int64_t nr = (c.t1 - c.t0) * 32;
     int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (x >= nr) return;
-    atomicAdd(&out.mult[newpos[owner[x]]], in.mult[r0 + x]);
+    if (x >= nr || owner[x] == 0xffffffffu) return;
+    atomicAdd(&out.mult[newpos[owner[x]]], c.in.mult ? c.in.mult[c.t0 * 32 + x] : 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -1423,32 +573,52 @@ void launch_cell_geo(const Chunk &c, cudaStream_t st) {
     GV_DISPATCH(c.P.fam, (k_cell_geo<FAMV><<<blocks_for((int64_t)c.nc << Fam<FAMV>::K, 64), 64, 0, st>>>(c)));
 }
 
-void launch_test(const Chunk &c, bool emit, cudaStream_t st) {
-    int64_t nr = c.r1 - c.r0;
-    if (nr <= 0) return;
-    unsigned g = blocks_for(nr, emit ? 256 * kRPTEmit : kTile);
-    if (c.precision == 0) {
-        if (emit) { GV_DISPATCH(c.P.fam, (k_test<FAMV, 0, true><<<g, 256, 0, st>>>(c))); }
-        else      { GV_DISPATCH(c.P.fam, (k_test<FAMV, 0, false><<<g, 256, 0, st>>>(c))); }
-    } else {
-        if (emit) { GV_DISPATCH(c.P.fam, (k_test<FAMV, 1, true><<<g, 256, 0, st>>>(c))); }
-        else      { GV_DISPATCH(c.P.fam, (k_test<FAMV, 1, false><<<g, 256, 0, st>>>(c))); }
+// Persistent grid: as many blocks as fit on the device at once (the kernel's
+// occupancy at its shared memory), at most one per group.  The occupancy of each
+// kernel is looked up once.
+void launch_persistent(const void *kern, size_t smem, int64_t groups, const Chunk &c, cudaStream_t st) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, size_t>, int> occ;
+    static int sms = 0;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (sms <= 0) sms = 1;
+        }
+        auto it = occ.find({kern, smem});
+        if (it == occ.end()) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1)
+                per_sm = 1;
+            occ[{kern, smem}] = per_sm;
+        } else {
+            per_sm = it->second;
+        }
     }
+    int64_t g = (int64_t)sms * per_sm;
+    if (g > groups) g = groups;
+    void *args[] = {(void *)&c};
+    cudaLaunchKernel(kern, dim3((unsigned)g), dim3(256), args, smem, st);
 }
 
-void launch_test2(const Chunk &c, const Chunk &c1, bool emit, const uint8_t *pm2_in, uint8_t *pm2_out,
-                  cudaStream_t st) {
-    int64_t nr = c.r1 - c.r0;
-    if (nr <= 0) return;
-    int ns = 1 << c.P.d;
-    unsigned g = blocks_for(nr, kTile) * ns;
-    if (c.precision == 0) {
-        if (emit) { GV_DISPATCH(c.P.fam, (k_test2<FAMV, 0, true><<<g, 256, 0, st>>>(c, c1, pm2_in, pm2_out))); }
-        else      { GV_DISPATCH(c.P.fam, (k_test2<FAMV, 0, false><<<g, 256, 0, st>>>(c, c1, pm2_in, pm2_out))); }
-    } else {
-        if (emit) { GV_DISPATCH(c.P.fam, (k_test2<FAMV, 1, true><<<g, 256, 0, st>>>(c, c1, pm2_in, pm2_out))); }
-        else      { GV_DISPATCH(c.P.fam, (k_test2<FAMV, 1, false><<<g, 256, 0, st>>>(c, c1, pm2_in, pm2_out))); }
-    }
+void launch_tile_info(const Chunk &c, cudaStream_t st) {
+    const int64_t nt = c.t1 - c.t0;
+    if (nt > 0) k_tile_info<<<blocks_for(nt, 256), 256, 0, st>>>(c);
+}
+
+void launch_next_tiles(const Chunk &c, int64_t ncells, cudaStream_t st) {
+    if (ncells > 0) k_next_tiles<<<blocks_for(ncells * 32, 256), 256, 0, st>>>(c.next_cells, c.out, ncells);
+}
+
+void launch_tile_dst(const Chunk &c, cudaStream_t st) {
+    const int64_t nt = c.t1 - c.t0;
+    if (nt <= 0) return;
+    const int ns = 1 << c.P.d;
+    if (ns == 4) k_tile_dst<4><<<blocks_for(nt, 32), 32 * 4, 0, st>>>(c);
+    else k_tile_dst<8><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
 }
 
 void launch_child_lbmax(const Chunk &c, cudaStream_t st) {
@@ -1474,15 +644,24 @@ void launch_child_alloc(const Chunk &c, uint32_t *keepflag, uint32_t *recn, unsi
     else k_child_write<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
 }
 
-void launch_group(const Problem &P, RecView in, int64_t r0, int64_t nr, int64_t c0, int nc, uint32_t *table,
-                  uint32_t tmask, uint32_t *owner, uint32_t *ccount, uint32_t *ccur, uint32_t *newpos,
-                  unsigned long long *total, RecView out, Scalars *sc, cudaStream_t st) {
+void launch_group(const Chunk &c, uint32_t *table, uint32_t tmask, uint32_t *owner, uint32_t *ccount,
+                  uint32_t *ccur, uint32_t *newpos, uint64_t *grbeg, unsigned long long *total, RecView out,
+                  cudaStream_t st) {
+    const int64_t nr = (c.t1 - c.t0) * 32;
     if (nr <= 0) return;
     unsigned g = blocks_for(nr, 256);
-    GV_DISPATCH(P.fam, (k_group_insert<FAMV><<<g, 256, 0, st>>>(in, r0, nr, c0, table, tmask, owner, ccount, sc)));
-    k_scan_u32<<<1, 256, 0, st>>>(ccount, nc, total);
-    GV_DISPATCH(P.fam, (k_group_place<FAMV><<<g, 256, 0, st>>>(in, r0, nr, c0, owner, ccount, ccur, newpos, out)));
-    k_group_mult<<<g, 256, 0, st>>>(in, r0, nr, owner, newpos, out);
+    if (c.lev.q16) {
+        GV_DISPATCH(c.P.fam, (k_group_insert<FAMV, true><<<g, 256, 0, st>>>(c, table, tmask, owner, ccount)));
+    } else {
+        GV_DISPATCH(c.P.fam, (k_group_insert<FAMV, false><<<g, 256, 0, st>>>(c, table, tmask, owner, ccount)));
+    }
+    k_scan_slots<<<1, 256, 0, st>>>(ccount, grbeg, c.nc, total);
+    if (c.lev.q16) {
+        GV_DISPATCH(c.P.fam, (k_group_place<FAMV, true><<<g, 256, 0, st>>>(c, owner, grbeg, ccur, newpos, out)));
+    } else {
+        GV_DISPATCH(c.P.fam, (k_group_place<FAMV, false><<<g, 256, 0, st>>>(c, owner, grbeg, ccur, newpos, out)));
+    }
+    k_group_mult<<<g, 256, 0, st>>>(c, owner, newpos, out);
 }
 
 void launch_path_geo(const Problem &P, const Level *levs_dev, int lam, uint64_t key, PathStep *path,

@@ -23,7 +23,7 @@ _lib = None
 
 VOTE_OPT_PRECISION, VOTE_OPT_PRUNE, VOTE_OPT_CHUNK_RECORDS = 1, 2, 3
 VOTE_OPT_TRACE_CAP, VOTE_OPT_GROUP, VOTE_OPT_FAULT_ALLOC_AT = 4, 5, 6
-VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING, VOTE_OPT_TWO_LEVEL, VOTE_OPT_BATCH_WORKERS = 7, 8, 9, 10
+VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING, VOTE_OPT_BATCH_WORKERS = 7, 8, 10
 VOTE_OPT_DIVE = 11
 KERNEL_CLASSES = ["lift", "cell_geo", "test_count", "test_emit", "children", "replay", "group", "spare"]
 STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
@@ -138,8 +138,7 @@ class Solver:
     inlier mask (CUDA int32 tensor holding the uint32 words)."""
 
     def __init__(self, family: int, eps, bounds, precision: int = 1, prune: bool = True,
-                 chunk_records: int | None = None, trace_cap: int = 0, stream=None,
-                 two_level: float | None = None):
+                 chunk_records: int | None = None, trace_cap: int = 0, stream=None):
         self.lib = load()
         self.family = family
         self.d, self.k = FAMILY_DK[family]
@@ -156,8 +155,6 @@ class Solver:
             self.set_option(VOTE_OPT_CHUNK_RECORDS, chunk_records)
         if trace_cap:
             self.set_option(VOTE_OPT_TRACE_CAP, trace_cap)
-        if two_level is not None:
-            self.set_option(VOTE_OPT_TWO_LEVEL, two_level)
         if stream is not None:
             self.set_stream(stream)
 

@@ -33,11 +33,11 @@ def test_tune_picks_fastest_and_caches(tmp_path):
     cost = {1 << 23: 3.0, 1 << 25: 1.0, 1 << 26: 2.0, 1 << 27: 2.5}
 
     def timer(solver, x):
-        return cost[solver.opts[3]] + (0.5 if solver.opts[9] else 0.0)
+        return cost[solver.opts[3]]
 
     out = autotune.tune(s, FakeSurfaces(), timer=timer, gpu="GB300", cache_path=path)
-    assert out["best"] == dict(chunk_records=1 << 25, two_level=0.0)
-    assert s.opts[3] == 1 << 25 and s.opts[9] == 0.0
+    assert out["best"] == dict(chunk_records=1 << 25)
+    assert s.opts[3] == 1 << 25
     s2 = FakeSolver()
     assert autotune.apply_cached(s2, 12000, "GB300", cache_path=path)
     assert s2.opts[3] == 1 << 25

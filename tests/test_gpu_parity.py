@@ -142,39 +142,15 @@ def test_cell_counts_replay_equals_oracle(family):
 
 
 @pytest.mark.parametrize("family", FAMS)
-@pytest.mark.parametrize("two_level", [0.0, 1e-9])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_two_level_expansion_parity(family, two_level, precision):
-    # 1e-9: every expansion with a grandchild level takes the two-level path
-    p = small(family, 2500, 13)
-    o = oracle.solve(p.family, p.eps, p.bounds, p.params)
-    g = gpu_solve(p, precision, two_level=two_level, chunk_records=3000)
-    assert_same(g, o, p.n)
-
-
-def test_two_level_trace_equals_oracle_without_pruning():
-    p = small(inputs.POSE3DOF, 400, 14)
-    cap = 4_000_000
-    o = oracle.solve(p.family, p.eps, p.bounds, p.params, flags=oracle.NO_PRUNE, trace_cap=cap)
-    g = gpu_solve(p, 1, prune=False, trace_cap=cap, two_level=1e-9)
-    tg = g["solver"].trace(cap)
-    to = o["trace"]
-    key = lambda l, c: (int(l), tuple(int(x) for x in c))
-    dg = {key(l, c): (int(u), int(b)) for l, c, u, b in zip(tg["level"], tg["coords"], tg["ub"], tg["lb"])}
-    do = {key(l, c): (int(u), int(b)) for l, c, u, b in zip(to["level"], to["coords"], to["ub"], to["lb"])}
-    assert dg == do
-
-
-@pytest.mark.parametrize("family", FAMS)
-@pytest.mark.parametrize("two_level", [0.0, 1e-9])
-def test_grouping_parity_and_merging(family, two_level):
+def test_grouping_parity_and_merging(family, precision):
     # grouping merges equal canonical records; results must not change
     v = vote_mod()
     p = small(family, 2500, 15)
     params = np.concatenate([p.params, p.params[:, :700], p.params[:, :300]], axis=1)   # duplicates merge
     o = oracle.solve(p.family, p.eps, p.bounds, params)
-    s0 = v.Solver(p.family, p.eps, p.bounds, two_level=two_level, chunk_records=4000)
-    s1 = v.Solver(p.family, p.eps, p.bounds, two_level=two_level, chunk_records=4000)
+    s0 = v.Solver(p.family, p.eps, p.bounds, precision=precision, chunk_records=4000)
+    s1 = v.Solver(p.family, p.eps, p.bounds, precision=precision, chunk_records=4000)
     s1.set_option(v.VOTE_OPT_GROUP, 1)
     t = torch.from_numpy(np.ascontiguousarray(params)).cuda()
     r0, r1 = s0.solve(t), s1.solve(t)

@@ -1,84 +1,159 @@
-"""Host checks of the bit arithmetic the proximity kernels use inside a warp.
+"""Host checks of the bit and float arithmetic the proximity kernels use.
 
-* Byte-packed per-slot counters (count pass): a record's slot mask is spread to one
-  byte per slot with (x * 0x00204081) & 0x01010101 for four slots at a time, and the
-  words of all records of a warp are added.  Checked: the spread is exact for every
-  4-bit mask, and a warp's sums (32 lanes x 4 records) decode to the per-slot
-  counts, so no byte carries into the next.
-* Run masks (emit pass): a warp's lanes hold consecutive records and a cell's
-  records are contiguous, so the lanes of one cell form a run; the kernel finds a
-  lane's run from the ballot of run heads.  Checked against brute force on random
-  sorted cell sequences with idle tail lanes.
+* Byte-packed per-slot counters (count pass): a lane adds 1 << 8 (s % 4) to word
+  s // 4 for every child slot s its record passes, over at most kTW tiles, and
+  the warp adds its lanes' words (one reduction per word).  Checked: the sums
+  decode to the per-slot counts, so no byte carries into the next.
+* 16-bit record fields (biased by 2^15): a field becomes a float by placing its
+  16 bits under the exponent of 1.5 * 2^23 (a byte permute with 0x4B40) and
+  subtracting 1.5 * 2^23 + 2^15.  Checked exactly for all 65536 values.
+* Rounding by a magic constant (emit pass): y + (1.5 * 2^23 + 2^15) in FP32 holds
+  round-half-even(y) + 2^15 in its low 16 bits (|y| < 2^15), and the fused
+  q * 0.5 + that constant holds the re-snap round-half-even(q / 2) + 2^15; the
+  32-bit form y + 1.5 * 2^23 holds round-half-even(y) in its bits minus 0x4B400000.
+  Checked on ties and random values, against Python's round (half to even).
+* Child ranges (emit pass): one thread per child slot walks a block's tiles in
+  order, takes one range per (cell, child) run with an atomic on the child's
+  cursor and hands every tile its offset; positions of all blocks together are a
+  permutation of [0, count) for every (cell, child).  Checked on random tile
+  sequences.
 """
 import numpy as np
 
-FULL = 0xFFFFFFFF
-RPT = 4          # records per thread in the count pass
+KTW = 4          # tiles per warp (gv_tile.cuh)
+KWARPS = 8
 
 
-def spread4(x):
-    return (x * 0x00204081) & 0x01010101
+def f32(x):
+    return np.float32(x)
 
 
-def run_mask(keys, lane):
-    """Python restatement of the kernel's run_mask for one lane (keys: per-lane
-    cell, -1 for a lane without a record)."""
-    heads = 0
-    for i in range(32):
-        prev = keys[i - 1] if i > 0 else keys[0]
-        if i == 0 or prev != keys[i]:
-            heads |= 1 << i
-    upto = FULL if lane == 31 else ((2 << lane) - 1)
-    start = (heads & upto).bit_length() - 1
-    after = heads & ~upto & FULL
-    if after:
-        first_after = (after & -after).bit_length() - 1
-        below_end = (1 << first_after) - 1
-    else:
-        below_end = FULL
-    return below_end & ~((1 << start) - 1) & FULL
+def bits(x):
+    return int(np.asarray(np.float32(x)).view(np.uint32))
 
 
-def test_spread4_exact():
-    for x in range(16):
-        want = sum(((x >> i) & 1) << (8 * i) for i in range(4))
-        assert spread4(x) == want
+def from_bits(b):
+    return float(np.asarray(np.uint32(b)).view(np.float32))
 
 
-def test_packed_warp_counts_do_not_carry():
+def byte_perm(x, y, sel):
+    src = [(x >> (8 * i)) & 255 for i in range(4)] + [(y >> (8 * i)) & 255 for i in range(4)]
+    return sum(src[(sel >> (4 * i)) & 7] << (8 * i) for i in range(4))
+
+
+MAGIC = 12582912.0
+MAGIC16 = 12615680.0
+
+
+def test_packed_counters_do_not_carry():
     rng = np.random.default_rng(0)
     for trial in range(200):
-        # worst cases included: every lane passes every slot for every record
         p = 1.0 if trial == 0 else rng.random()
-        masks = (rng.random((32, RPT, 8)) < p)
+        passes = rng.random((32, KTW, 8)) < p            # lane, tile, slot
         words = [0, 0]
         for lane in range(32):
-            for k in range(RPT):
-                m = sum(int(b) << s for s, b in enumerate(masks[lane, k]))
-                words[0] += spread4(m & 15)
-                words[1] += spread4((m >> 4) & 15)
-        assert all(w < 2 ** 32 for w in words)
-        counts = masks.sum(axis=(0, 1))
+            w = [0, 0]
+            for k in range(KTW):
+                for s in range(8):
+                    if passes[lane, k, s]:
+                        w[s >> 2] += 1 << (8 * (s & 3))
+            words[0] += w[0]
+            words[1] += w[1]
+        assert all(x < 2 ** 32 for x in words)
+        counts = passes.sum(axis=(0, 1))
         for s in range(8):
-            assert (words[s // 4] >> (8 * (s % 4))) & 255 == counts[s]
-    assert 32 * RPT < 256
+            assert (words[s >> 2] >> (8 * (s & 3))) & 255 == counts[s]
+    assert 32 * KTW < 256
 
 
-def test_run_mask_matches_brute_force():
+def test_16bit_fields_to_float_exact():
+    for q in range(-32768, 32768):
+        u = q + 32768
+        word = (u << 16) | 0x1234 if q % 2 else (0xABCD << 16) | u
+        sel = 0x5432 if q % 2 else 0x5410
+        b = byte_perm(word, 0x4B40, sel)
+        v = f32(f32(from_bits(b)) - f32(MAGIC16))
+        assert float(v) == q
+
+
+def round_half_even(x):
+    return int(round(x))           # Python rounds halves to even
+
+
+def test_magic_rounding_and_resnap():
     rng = np.random.default_rng(1)
-    for _ in range(2000):
-        nrec = int(rng.integers(1, 33))
-        ncells = int(rng.integers(1, 9))
-        keys = sorted(int(x) for x in rng.integers(0, ncells, size=nrec)) + [-1] * (32 - nrec)
-        for lane in range(32):
-            want = 0
-            # the maximal block of equal keys around this lane
-            a = lane
-            while a > 0 and keys[a - 1] == keys[lane]:
-                a -= 1
-            b = lane
-            while b < 31 and keys[b + 1] == keys[lane]:
-                b += 1
-            for i in range(a, b + 1):
-                want |= 1 << i
-            assert run_mask(keys, lane) == want, (keys, lane)
+    ys = np.concatenate([np.arange(-40, 41) * 0.5, rng.uniform(-32000, 32000, 20000),
+                         [32766.5, -32767.5, 0.4999999, -0.5000001]])
+    for y in ys:
+        y = float(f32(y))
+        t = f32(f32(y) + f32(MAGIC16))                  # FP32 add, one rounding
+        q = round_half_even(y)
+        assert bits(t) & 0xFFFF == (q + 32768) & 0xFFFF, y
+        assert float(f32(t - f32(MAGIC16))) == q
+        if abs(y) < 2 ** 22:
+            t32 = f32(f32(y) + f32(MAGIC))
+            d = (bits(t32) - 0x4B400000) & 0xFFFFFFFF
+            assert (d - (1 << 32) if d >= 1 << 31 else d) == q
+    # the re-snap of an essential parameter when its step doubles: fma(q, 0.5, MAGIC16)
+    for q in list(range(-300, 301)) + list(rng.integers(-32768, 32768, 5000)):
+        q = int(q)
+        exact = q * 0.5 + MAGIC16                        # exact in FP64, one FP32 rounding as in fma
+        t = f32(exact)
+        k = q >> 1
+        want = k + ((q & 1) & (k & 1))                  # the integer re-snap of the 32-bit path
+        assert want == round_half_even(q / 2)
+        assert bits(t) & 0xFFFF == (want + 32768) & 0xFFFF
+
+
+def walk_offsets(tile_cells, ballots, cursor, ns):
+    """Python restatement of the emit pass's phase 2 for one block."""
+    nt = len(tile_cells)
+    off = np.zeros((nt, ns), np.int64)
+    for s in range(ns):
+        cur, start, run = -1, 0, 0
+        for i in range(nt + 1):
+            cl = tile_cells[i] if i < nt else -2
+            if cl != cur:
+                if cur >= 0 and run:
+                    base = cursor[cur, s]
+                    cursor[cur, s] += run
+                    off[start:i, s] += base
+                cur, run, start = cl, 0, i
+            if i < nt:
+                off[i, s] = run
+                run += bin(ballots[i][s]).count("1")
+    return off
+
+
+def test_child_ranges_are_permutations():
+    rng = np.random.default_rng(2)
+    ns = 8
+    for trial in range(60):
+        ncell = int(rng.integers(1, 7))
+        sizes = rng.integers(1, 200, ncell)
+        tile_cells, tile_valid = [], []
+        for cl, n in enumerate(sizes):
+            for t in range((n + 31) // 32):
+                tile_cells.append(cl)
+                tile_valid.append(min(32, n - 32 * t))
+        ballots = []
+        for v in tile_valid:
+            m = (1 << v) - 1
+            ballots.append([int(rng.integers(0, 2 ** 32)) & m for _ in range(ns)])
+        cursor = np.zeros((ncell, ns), np.int64)
+        nb = 4 * KWARPS * KTW // 8                      # blocks of various sizes over the same tiles
+        positions = {}
+        for b0 in range(0, len(tile_cells), nb):
+            tc = tile_cells[b0:b0 + nb]
+            bl = ballots[b0:b0 + nb]
+            off = walk_offsets(tc, bl, cursor, ns)
+            for i, cl in enumerate(tc):
+                for s in range(ns):
+                    b = bl[i][s]
+                    for lane in range(32):
+                        if (b >> lane) & 1:
+                            pos = off[i, s] + bin(b & ((1 << lane) - 1)).count("1")
+                            positions.setdefault((cl, s), []).append(pos)
+        for (cl, s), ps in positions.items():
+            assert sorted(ps) == list(range(len(ps)))
+            assert cursor[cl, s] == len(ps)
