@@ -43,6 +43,8 @@ WORKLOADS = {
                           "eps 0.25 m / 0.5 deg, (yaw,x,y) space"),
     "line2d_n1e4": dict(make=lambda: inputs.line2d(), desc="2D line fitting, 1e4 points, 10% inliers, eps 0.01, "
                         "(m,b) space"),
+    "plane3d_n1e4": dict(make=lambda: inputs.plane3d(n=10_000), desc="3D plane fitting, 1e4 points (the plane "
+                         "workload's shape at a hundredth of its size; a whole solve is a small profiler capture)"),
     "plane3d_n1e5": dict(make=lambda: inputs.plane3d(n=100_000), desc="3D plane fitting, 1e5 points (the plane "
                          "workload's shape at a tenth of its size; a small target for profiler captures)"),
     "pose3dof_n3e5": dict(make=lambda: inputs.pose3dof(n=300_000), desc="3DoF camera voting, 3e5 matches (a small "

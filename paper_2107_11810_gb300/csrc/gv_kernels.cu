@@ -336,7 +336,7 @@ __global__ void k_next_tiles(CellView next, RecView out, int64_t ncells) {
     for (int64_t i = lane; i < nt; i += 32) out.tile_cell[t0 + i] = (uint32_t)cell;
 }
 
-// Output positions of the emit pass.  A block takes kBlockTiles consecutive tiles;
+// Output positions of the emit pass.  A block takes 32 consecutive tiles;
 // warp s handles child slot s with one lane per tile: a segmented scan over the
 // tiles (segments = runs of one cell) gives every tile its offset inside the run,
 // the run's last lane reserves the run's records in the child with one atomic on
@@ -344,7 +344,6 @@ __global__ void k_next_tiles(CellView next, RecView out, int64_t ncells) {
 // slot of the tile's records in child s, or ~0 when the tile writes none there.
 template <int NS>
 __global__ void __launch_bounds__(256) k_tile_dst(Chunk c) {
-    static_assert(kBlockTiles == 32, "one lane per tile");
     const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
     if (s >= NS) return;
     const int64_t t = c.t0 + (int64_t)blockIdx.x * 32 + lane;
@@ -591,6 +590,7 @@ void launch_persistent(const void *kern, size_t smem, int64_t groups, const Chun
         }
         auto it = occ.find({kern, smem});
         if (it == occ.end()) {
+            if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1)
                 per_sm = 1;
             occ[{kern, smem}] = per_sm;
