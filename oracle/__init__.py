@@ -47,7 +47,7 @@ _lib = None
 
 LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF = 1, 2, 3, 4
 NO_MERGE, NO_PRUNE, REVERSE = 1, 2, 4
-FAMILY_SHAPE = {LINE2D: (2, 1, 1, 2), PLANE3D_SPH: (3, 2, 3, 3), POSE3DOF: (3, 1, 2, 4)}
+FAMILY_SHAPE = {LINE2D: (2, 1, 1, 2), PLANE3D_SPH: (3, 2, 3, 3), POSE3DOF: (3, 1, 2, 4), POSE6DOF: (6, 4, 11, 5)}
 """family -> (d, k, number of essential params, number of input params)"""
 
 _CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11", "-fopenmp"]
@@ -86,6 +86,8 @@ def _declare(lib):
     lib.gvo_lipschitz.argtypes = [i32, i32, i32, P, P]
     lib.gvo_path_records.restype = i32
     lib.gvo_path_records.argtypes = [i32, i32, i32, P, P, P, i64, i64, i32, P, P, P]
+    lib.gvo_rotation.restype = None
+    lib.gvo_rotation.argtypes = [P, P]
     return lib
 
 
@@ -129,6 +131,15 @@ def vsin(x: float) -> float:
 
 def vcos(x: float) -> float:
     return _load().gvo_vcos(float(x))
+
+
+def rotation(ph, lib=None) -> np.ndarray:
+    """The 3x3 rotation matrix of axis-angle vector ph that the POSE6DOF family's
+    basis uses (Rodrigues' formula by power series in |ph|^2)."""
+    ph = np.ascontiguousarray(ph, dtype=np.float64).reshape(3)
+    out = np.zeros(9)
+    (lib or _load()).gvo_rotation(_ptr(ph), _ptr(out))
+    return out.reshape(3, 3)
 
 
 def source() -> str:

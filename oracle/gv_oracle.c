@@ -64,7 +64,7 @@
 #include <string.h>
 
 #define GVO_MAXD 6
-#define GVO_MAXT 5
+#define GVO_MAXT 11
 #define GVO_MAXL 40
 
 enum { GVO_LINE2D = 1, GVO_PLANE3D_SPH = 2, GVO_POSE3DOF = 3, GVO_POSE6DOF = 4 };
@@ -164,13 +164,14 @@ double gvo_vcos(double x)
 /* ------------------------------------------------------------------------- */
 
 typedef struct {
-    int fam, d, k, nd, le, np;
+    int fam, d, k, nd, le, np, nb;   /* nb: basis values psi (Sec. 3.2's canonization frame) */
     int L, Lj[GVO_MAXD];
     double lo[GVO_MAXD], W[GVO_MAXD], eps[GVO_MAXD];
     double h[GVO_MAXL + 1][GVO_MAXD];     /* half-width of a level-l cell      */
     double s_f[GVO_MAXD];                 /* snap step of free param j (dep.)  */
     double s_t[GVO_MAXL + 1][GVO_MAXT];   /* snap step of essential param m    */
     double A[GVO_MAXL + 2][GVO_MAXD];     /* accumulated error, dependent j    */
+    double inv_fact[31];                  /* 1/m!, m! = m (m-1)! in FP64 (Rodrigues) */
 } gvo_problem;
 
 typedef struct {
@@ -187,6 +188,7 @@ static int family_shape(int fam, int d, int k, int *le, int *np)
     case GVO_LINE2D:      if (d != 2 || k != 1) return 1; *le = 1; *np = 2; return 0;
     case GVO_PLANE3D_SPH: if (d != 3 || k != 2) return 1; *le = 3; *np = 3; return 0;
     case GVO_POSE3DOF:    if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
+    case GVO_POSE6DOF:    if (d != 6 || k != 4) return 1; *le = 11; *np = 5; return 0;
     default: return 1;
     }
 }
@@ -209,7 +211,23 @@ static void family_sigma(const gvo_problem *p, const double *h, double *sigma)
         sigma[0] = h[0];
         sigma[1] = h[0];
         break;
+    case GVO_POSE6DOF: {  /* F = sum_m t_m psi_m with psi = entries of R(phi) and z */
+        /* An entry R_ki of R(phi) has gradient e_k . (J e_a x R e_i) along phi_a, J the
+         * rotation's Jacobian (operator norm 1), so |grad R_ki| <= 1 and the entry moves
+         * by at most |d phi|_2 <= h_phi1 + h_phi2 + h_phi3 across the cell; z is linear. */
+        double hr = (h[0] + h[1]) + h[2];
+        for (int m = 0; m < 9; ++m) sigma[m] = hr;
+        sigma[9] = h[3];
+        sigma[10] = h[3];
+        break;
     }
+    }
+}
+
+/* number of basis values psi of a family */
+static int family_nb(int fam, int le)
+{
+    return fam == GVO_POSE6DOF ? 10 : le;
 }
 
 static double pow2_floor(double x)  /* 2^floor(log2 x), exact */
@@ -226,6 +244,9 @@ static int problem_init(gvo_problem *p, int fam, int d, int k, const double *eps
     int le, np;
     if (family_shape(fam, d, k, &le, &np)) return 1;
     p->fam = fam; p->d = d; p->k = k; p->nd = d - k; p->le = le; p->np = np;
+    p->nb = family_nb(fam, le);
+    p->inv_fact[0] = 1.0;
+    for (int m = 1; m < 31; ++m) p->inv_fact[m] = p->inv_fact[m - 1] / (double)m;
     p->L = 0;
     for (int j = 0; j < d; ++j) {
         double lo = bounds[2 * j], hi = bounds[2 * j + 1];
@@ -275,8 +296,34 @@ static double cell_center(const gvo_problem *p, int l, int j, int64_t i)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Families (Sec. 3 Eq. 2 line duality; Sec. 4.1 plane fitting; 3DoF posing).  */
+/* Families (Sec. 3 Eq. 2 line duality; Sec. 4.1 plane fitting; 3DoF posing;   */
+/* Sec. 4.2.3 calibrated 6DoF posing).                                        */
 /* ------------------------------------------------------------------------- */
+
+/* Rotation matrix (row-major) of the axis-angle vector ph, theta = |ph|, by
+ * Rodrigues' formula R = cos(theta) I + (sin(theta)/theta) [ph]x
+ * + ((1 - cos(theta))/theta^2) ph ph^T.  The three scalar functions are even in
+ * theta, so each is a power series in s = theta^2: cos = sum_n (-1)^n s^n/(2n)!,
+ * sin(theta)/theta = sum_n (-1)^n s^n/(2n+1)!, (1 - cos)/theta^2 = sum_n (-1)^n
+ * s^n/(2n+2)!, evaluated by Horner's rule with 15 terms (for theta <= 2 the first
+ * omitted term is below 1e-21), coefficients 1/m! from m! = m (m-1)! as divisions
+ * in FP64.  No division by theta and no sin/cos: the formula holds at theta = 0. */
+static void rodrigues(const double *inv_fact, const double *ph, double *R)
+{
+    double s = (ph[0] * ph[0] + ph[1] * ph[1]) + ph[2] * ph[2];
+    double C = 0.0, A = 0.0, B = 0.0;
+    for (int n = 14; n >= 0; --n) {
+        double sg = (n & 1) ? -1.0 : 1.0;
+        C = C * s + sg * inv_fact[2 * n];
+        A = A * s + sg * inv_fact[2 * n + 1];
+        B = B * s + sg * inv_fact[2 * n + 2];
+    }
+    double a0 = A * ph[0], a1 = A * ph[1], a2 = A * ph[2];
+    double b0 = B * ph[0], b1 = B * ph[1], b2 = B * ph[2];
+    R[0] = C + b0 * ph[0];  R[1] = b0 * ph[1] - a2;  R[2] = b0 * ph[2] + a1;
+    R[3] = b1 * ph[0] + a2; R[4] = C + b1 * ph[1];  R[5] = b1 * ph[2] - a0;
+    R[6] = b2 * ph[0] - a1; R[7] = b2 * ph[1] + a0; R[8] = C + b2 * ph[2];
+}
 
 /* Basis values psi(c) at the centre of the level-l cell with coords i. */
 static void family_basis(const gvo_problem *p, int l, const int64_t *i, double *psi)
@@ -299,6 +346,13 @@ static void family_basis(const gvo_problem *p, int l, const int64_t *i, double *
         double yaw = cell_center(p, l, 0, i[0]);
         psi[0] = gvo_vcos(yaw);
         psi[1] = gvo_vsin(yaw);
+        break;
+    }
+    case GVO_POSE6DOF: {                                      /* rows of R(phi), then z */
+        double ph[3];
+        for (int j = 0; j < 3; ++j) ph[j] = cell_center(p, l, j, i[j]);
+        rodrigues(p->inv_fact, ph, psi);
+        psi[9] = cell_center(p, l, 3, i[3]);
         break;
     }
     }
@@ -332,6 +386,28 @@ static void family_lift(const gvo_problem *p, const double *params, int64_t n, i
         r->t[0] = a; r->t[1] = b;
         r->f[0] = (w1 - (a * psi[0] - b * psi[1])) - c[1];
         r->f[1] = (w2 - (a * psi[1] + b * psi[0])) - c[2];
+        break;
+    }
+    case GVO_POSE6DOF: {
+        /* match (w, xi, eta): x = xi (r3 . w + z) - r1 . w, y = eta (r3 . w + z) - r2 . w
+         * (Sec. 4.2.2 with f = 1, Sec. 4.2.3).  Affine in the basis (rows of R, z) with
+         * coefficients t = (w, xi w, eta w, xi, eta). */
+        double w[3], xi = params[3 * n + i], eta = params[4 * n + i];
+        for (int j = 0; j < 3; ++j) w[j] = params[j * n + i];
+        for (int j = 0; j < 3; ++j) {
+            r->t[j] = w[j];
+            r->t[3 + j] = xi * w[j];
+            r->t[6 + j] = eta * w[j];
+        }
+        r->t[9] = xi;
+        r->t[10] = eta;
+        const double *t = r->t;
+        double sx3 = (t[3] * psi[6] + t[4] * psi[7]) + t[5] * psi[8];
+        double sx1 = (t[0] * psi[0] + t[1] * psi[1]) + t[2] * psi[2];
+        double sy3 = (t[6] * psi[6] + t[7] * psi[7]) + t[8] * psi[8];
+        double sy2 = (t[0] * psi[3] + t[1] * psi[4]) + t[2] * psi[5];
+        r->f[0] = ((sx3 + t[9] * psi[9]) - sx1) - c[4];
+        r->f[1] = ((sy3 + t[10] * psi[9]) - sy2) - c[5];
         break;
     }
     }
@@ -372,7 +448,8 @@ static void child_geometry(const gvo_problem *p, int l, const int64_t *i, const 
     } else {
         double psi_child[GVO_MAXT];
         family_basis(p, l + 1, g->ci, psi_child);
-        for (int m = 0; m < p->le; ++m) g->dpsi[m] = psi_child[m] - psi_parent[m];
+        for (int m = 0; m < p->nb; ++m) g->dpsi[m] = psi_child[m] - psi_parent[m];
+        if (p->fam == GVO_POSE6DOF) g->dpsi[9] = g->shift[3];   /* z is linear: exact shift */
     }
 }
 
@@ -391,6 +468,16 @@ static void family_residual(const gvo_problem *p, const double *f, const double 
         fo[0] = (f[0] - (t[0] * g->dpsi[0] - t[1] * g->dpsi[1])) - g->shift[1];
         fo[1] = (f[1] - (t[0] * g->dpsi[1] + t[1] * g->dpsi[0])) - g->shift[2];
         break;
+    case GVO_POSE6DOF: {
+        const double *d = g->dpsi;
+        double sx3 = (t[3] * d[6] + t[4] * d[7]) + t[5] * d[8];
+        double sx1 = (t[0] * d[0] + t[1] * d[1]) + t[2] * d[2];
+        double sy3 = (t[6] * d[6] + t[7] * d[7]) + t[8] * d[8];
+        double sy2 = (t[0] * d[3] + t[1] * d[4]) + t[2] * d[5];
+        fo[0] = (f[0] + ((sx3 + t[9] * d[9]) - sx1)) - g->shift[4];
+        fo[1] = (f[1] + ((sy3 + t[10] * d[9]) - sy2)) - g->shift[5];
+        break;
+    }
     }
 }
 
@@ -409,6 +496,17 @@ static void family_lipschitz(const gvo_problem *p, const double *t, double *lam)
         double r = sqrt(t[0] * t[0] + t[1] * t[1]);
         lam[0] = r;
         lam[1] = r;
+        break;
+    }
+    case GVO_POSE6DOF: {
+        /* d/dphi_a of e_k . R v is e_k . (J e_a x R v), at most |v| (J of norm 1):
+         * |dx/dphi_a| <= |xi w| + |w|, |dy/dphi_a| <= |eta w| + |w|; dx/dz = xi, dy/dz = eta */
+        double nw = sqrt((t[0] * t[0] + t[1] * t[1]) + t[2] * t[2]);
+        double nxw = sqrt((t[3] * t[3] + t[4] * t[4]) + t[5] * t[5]);
+        double nyw = sqrt((t[6] * t[6] + t[7] * t[7]) + t[8] * t[8]);
+        double lx = nxw + nw, ly = nyw + nw;
+        lam[0] = lx; lam[1] = lx; lam[2] = lx; lam[3] = fabs(t[9]);
+        lam[4] = ly; lam[5] = ly; lam[6] = ly; lam[7] = fabs(t[10]);
         break;
     }
     }
@@ -799,13 +897,24 @@ int gvo_cell_counts(int fam, int d, int k, const double *eps, const double *boun
 /* tests can check the bounds they rest on against the surface equations.    */
 /* ------------------------------------------------------------------------- */
 
+/* R[9] (row-major): the rotation matrix of axis-angle vector ph[3] that the
+ * POSE6DOF family's basis uses. */
+void gvo_rotation(const double *ph, double *R)
+{
+    gvo_problem p;
+    memset(&p, 0, sizeof(p));
+    p.inv_fact[0] = 1.0;
+    for (int m = 1; m < 31; ++m) p.inv_fact[m] = p.inv_fact[m - 1] / (double)m;
+    rodrigues(p.inv_fact, ph, R);
+}
+
 /* sigma[le]: the bound family_sigma gives for a cell of half-widths h[d]. */
 int gvo_sigma(int fam, int d, int k, const double *h, double *sigma)
 {
     gvo_problem p;
     memset(&p, 0, sizeof(p));
     if (family_shape(fam, d, k, &p.le, &p.np)) return 1;
-    p.fam = fam; p.d = d; p.k = k; p.nd = d - k;
+    p.fam = fam; p.d = d; p.k = k; p.nd = d - k; p.nb = family_nb(fam, p.le);
     family_sigma(&p, h, sigma);
     return 0;
 }
@@ -817,7 +926,7 @@ int gvo_lipschitz(int fam, int d, int k, const double *t, double *lam)
     gvo_problem p;
     memset(&p, 0, sizeof(p));
     if (family_shape(fam, d, k, &p.le, &p.np)) return 1;
-    p.fam = fam; p.d = d; p.k = k; p.nd = d - k;
+    p.fam = fam; p.d = d; p.k = k; p.nd = d - k; p.nb = family_nb(fam, p.le);
     family_lipschitz(&p, t, lam);
     return 0;
 }

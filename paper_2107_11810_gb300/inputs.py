@@ -16,6 +16,12 @@ Surface parameters are FP64, structure-of-arrays ``params[P, n]``:
   voting space (yaw, x, y) with x = w1 - (a cos yaw - b sin yaw) and
   y = w2 - (a sin yaw + b cos yaw); (a, b) = r (cos beta, sin beta), r the
   horizontal distance implied by the elevation, beta the bearing azimuth.
+* ``POSE6DOF``    (calibrated camera, Sec. 4.2.3: the 7DoF surfaces of Sec. 4.2.2
+  with f = 1): P = 5, rows (w1, w2, w3, xi, eta) of a match between world point w
+  and normalized image point (xi, eta); voting space (phi1, phi2, phi3, z, x, y),
+  phi the axis-angle vector of the rotation and (x, y, z) the translation of the
+  camera frame X = R(phi) w + (x, y, z), with x = xi (r3 . w + z) - r1 . w and
+  y = eta (r3 . w + z) - r2 . w.
 """
 from __future__ import annotations
 
@@ -26,7 +32,7 @@ import numpy as np
 
 LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF = 1, 2, 3, 4
 FAMILY_NAMES = {LINE2D: "LINE2D", PLANE3D_SPH: "PLANE3D_SPH", POSE3DOF: "POSE3DOF", POSE6DOF: "POSE6DOF"}
-FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1)}
+FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1), POSE6DOF: (6, 4)}
 SEED_BASE = 2107118100
 
 
@@ -217,6 +223,82 @@ def pose3dof_batch(num: int = 256, n_lo: float = 1e3, n_hi: float = 1e6, frac_lo
     return probs
 
 
+def rotvec_matrix(ph) -> np.ndarray:
+    """Rotation matrix of an axis-angle vector (numpy's own trigonometry; scene
+    generation only)."""
+    ph = np.asarray(ph, float)
+    th = float(np.linalg.norm(ph))
+    if th == 0.0:
+        return np.eye(3)
+    k = ph / th
+    K = np.array([[0.0, -k[2], k[1]], [k[2], 0.0, -k[0]], [-k[1], k[0], 0.0]])
+    return np.eye(3) + math.sin(th) * K + (1.0 - math.cos(th)) * (K @ K)
+
+
+def pose6dof(n: int = 5000, inlier_frac: float = 0.05, prior_deg: float = 30.0, box: float = 10.0,
+             levels: int = 7, noise_deg: float = 0.1, points=(20.0, 20.0, 5.0), fov: float = 1.0,
+             seed: int = SEED_BASE + 4, rng: np.random.Generator | None = None) -> Problem:
+    """Calibrated-camera posing (6DoF).  World points uniform in
+    [0, points_0] x [0, points_1] x [0, points_2]; the camera maps w to
+    X = R(phi) w + t.  Truth: phi = phi_prior + U[-prior, prior]^3 with phi_prior
+    uniform in the ball of radius 1 rad, t ~ U[0, box]^3 (redrawn until a quarter of
+    the points lie in front of the camera).  Inliers: points with X_3 > 1 m seen at
+    (X_1/X_3, X_2/X_3) within the field of view |xi|, |eta| <= fov, the bearing
+    perturbed by N(0, noise) on both image angles; outliers: a random point with a
+    random image point of the field of view.  Voting domain: phi in
+    phi_prior +- prior per axis, (z, x, y) in [0, box]^3; every coordinate splits
+    ``levels`` times (leaf widths 2 prior / 2^levels and box / 2^levels), and the
+    depth tolerance of x and y is their leaf width (a constant vertical distance)."""
+    if rng is None:
+        rng = np.random.default_rng(seed)
+    pr = math.radians(prior_deg)
+    while True:
+        v = rng.normal(size=3)
+        prior = v / np.linalg.norm(v) * rng.uniform(0.0, 1.0) ** (1.0 / 3.0)
+        phi = prior + rng.uniform(-pr, pr, 3)
+        t = rng.uniform(0.0, box, 3)
+        R = rotvec_matrix(phi)
+        w = np.stack([rng.uniform(0, points[0], 4096), rng.uniform(0, points[1], 4096),
+                      rng.uniform(0, points[2], 4096)], axis=1)
+        X = w @ R.T + t
+        vis = (X[:, 2] > 1.0) & (np.abs(X[:, 0]) <= fov * X[:, 2]) & (np.abs(X[:, 1]) <= fov * X[:, 2])
+        if vis.mean() >= 0.25:
+            break
+    n_in = int(round(n * inlier_frac))
+    sig = math.radians(noise_deg)
+    out = np.empty((5, n))
+    got = 0
+    while got < n_in:
+        m = 4 * (n_in - got) + 16
+        w = np.stack([rng.uniform(0, points[0], m), rng.uniform(0, points[1], m),
+                      rng.uniform(0, points[2], m)], axis=1)
+        X = w @ R.T + t
+        ok = (X[:, 2] > 1.0) & (np.abs(X[:, 0]) <= fov * X[:, 2]) & (np.abs(X[:, 1]) <= fov * X[:, 2])
+        w, X = w[ok][: n_in - got], X[ok][: n_in - got]
+        a = np.arctan2(X[:, 0], X[:, 2]) + rng.normal(0, sig, len(w))
+        b = np.arctan2(X[:, 1], X[:, 2]) + rng.normal(0, sig, len(w))
+        sl = slice(got, got + len(w))
+        out[0:3, sl] = w.T
+        out[3, sl], out[4, sl] = np.tan(a), np.tan(b)
+        got += len(w)
+    m = n - n_in
+    out[0, n_in:] = rng.uniform(0, points[0], m)
+    out[1, n_in:] = rng.uniform(0, points[1], m)
+    out[2, n_in:] = rng.uniform(0, points[2], m)
+    out[3, n_in:] = rng.uniform(-fov, fov, m)
+    out[4, n_in:] = rng.uniform(-fov, fov, m)
+    perm = rng.permutation(n)
+    out = out[:, perm]
+    inliers = np.nonzero(perm < n_in)[0]
+    lo = np.concatenate([prior - pr, [0.0, 0.0, 0.0]])
+    hi = np.concatenate([prior + pr, [box, box, box]])
+    bounds = np.stack([lo, hi], axis=1).reshape(-1)
+    eps = (hi - lo) / 2.0 ** levels
+    truth = np.concatenate([phi, [t[2], t[0], t[1]]])
+    return Problem(POSE6DOF, eps, bounds, np.ascontiguousarray(out), truth, inliers, "pose6dof",
+                   dict(inlier_frac=inlier_frac, prior=prior, prior_deg=prior_deg, levels=levels))
+
+
 # ---------------------------------------------------------------------------
 # Standard workloads
 # ---------------------------------------------------------------------------
@@ -236,4 +318,6 @@ def random_small(family: int, n: int, seed: int, inlier_frac: float = 0.3, **kw)
         return plane3d(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
     if family == POSE3DOF:
         return pose3dof(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
+    if family == POSE6DOF:
+        return pose6dof(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
     raise ValueError(family)

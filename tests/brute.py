@@ -11,7 +11,7 @@ import itertools
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF = 1, 2, 3
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF = 1, 2, 3, 4
 
 
 def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.ndarray:
@@ -31,6 +31,17 @@ def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.n
         yaw, x, y = pts[:, 0:1], pts[:, 1:2], pts[:, 2:3]
         fx = w1 - (a * np.cos(yaw) - b * np.sin(yaw))
         fy = w2 - (a * np.sin(yaw) + b * np.cos(yaw))
+        return np.stack([x - fx, y - fy], axis=-1)
+    if family == POSE6DOF:               # calibrated camera: X = R(phi) w + (x, y, z) (Sec. 4.2.3)
+        from scipy.spatial.transform import Rotation
+        w = np.asarray(params[0:3], float)                    # [3, n]
+        xi, eta = params[3], params[4]
+        Rm = Rotation.from_rotvec(pts[:, 0:3]).as_matrix()    # [npts, 3, 3]
+        Rw = np.einsum("pij,jn->pin", Rm, w)                  # rows r_i . w: [npts, 3, n]
+        z, x, y = pts[:, 3:4], pts[:, 4:5], pts[:, 5:6]
+        depth_ = Rw[:, 2, :] + z
+        fx = xi[None, :] * depth_ - Rw[:, 0, :]
+        fy = eta[None, :] * depth_ - Rw[:, 1, :]
         return np.stack([x - fx, y - fy], axis=-1)
     raise ValueError(family)
 

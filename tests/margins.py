@@ -28,12 +28,20 @@ import numpy as np
 import brute
 import oracle
 
-LINE2D, PLANE3D_SPH, POSE3DOF = 1, 2, 3
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF = 1, 2, 3, 4
+
+
+def _rot(x):
+    from scipy.spatial.transform import Rotation
+    sh = x.shape[:-1]
+    return Rotation.from_rotvec(x.reshape(-1, 3)).as_matrix().reshape(sh + (3, 3))
 
 
 def basis(family: int, x: np.ndarray) -> np.ndarray:
     """psi_m(x) [..., le] at free coordinates x [..., k]: the functions multiplying
-    the essential parameters in each surface equation."""
+    the essential parameters in each surface equation.  For POSE6DOF, where one
+    parameter multiplies different functions in the x and y equations, [..., 2 le]:
+    the x equation's functions, then the y equation's."""
     if family == LINE2D:            # b = y - x m: t = x multiplies -m
         return x[..., 0:1].copy()
     if family == PLANE3D_SPH:       # d = q . n(theta, phi)
@@ -41,6 +49,13 @@ def basis(family: int, x: np.ndarray) -> np.ndarray:
         return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=-1)
     if family == POSE3DOF:          # (x, y) = w - R(yaw) (a, b)
         return np.stack([np.cos(x[..., 0]), np.sin(x[..., 0])], axis=-1)
+    if family == POSE6DOF:          # t = (w, xi w, eta w, xi, eta); rows of R(phi) and z
+        Rm = _rot(x[..., 0:3])
+        z = x[..., 3:4]
+        zero3, zero1 = np.zeros(x.shape[:-1] + (3,)), np.zeros(x.shape[:-1] + (1,))
+        fx = np.concatenate([-Rm[..., 0, :], Rm[..., 2, :], zero3, z, zero1], axis=-1)
+        fy = np.concatenate([-Rm[..., 1, :], zero3, Rm[..., 2, :], zero1, z], axis=-1)
+        return np.concatenate([fx, fy], axis=-1)
     raise ValueError(family)
 
 
@@ -56,6 +71,9 @@ def t_part(family: int, t: np.ndarray, x: np.ndarray) -> np.ndarray:
         a, b = t
         c, s = psi[..., 0], psi[..., 1]
         return np.stack([-(a * c - b * s), -(a * s + b * c)], axis=-1)
+    if family == POSE6DOF:
+        t = np.asarray(t, float)
+        return np.stack([psi[..., :11] @ t, psi[..., 11:] @ t], axis=-1)
     raise ValueError(family)
 
 
@@ -83,13 +101,17 @@ def check_sigma(p, cells_per_level=4, points=100_000, seed=0, lib=None):
     worst = []
     for l in range(lv["L"]):
         sig = oracle.sigma(p.family, lv["h"][l], lib=lib)
+        if p.family == POSE6DOF:
+            sig = np.concatenate([sig, sig])          # x-equation and y-equation functions
         w = 0.0
         for _ in range(cells_per_level):
             ci = random_cell(lv["Lj"], l, rng)
             c = cell_center(lo, lv["h"][l], ci)[:k]
             x = cell_points(c, lv["h"][l][:k], points, rng)
             dpsi = np.abs(basis(p.family, x) - basis(p.family, c[None])).max(axis=0)
-            w = max(w, float((dpsi / sig).max()))
+            used = sig > 0
+            assert np.all(dpsi[~used] == 0.0)
+            w = max(w, float((dpsi[used] / sig[used]).max()))
         worst.append(w)
     return np.array(worst)
 

@@ -5,7 +5,8 @@ mistake that only tightens a conservative margin slips through them unless a
 surface happens to sit inside that margin.  Here each margin is checked on its
 own, against the surface equations (tests/margins.py), on the level structures
 of the benchmark workloads (2D line eps 0.01, 3D plane eps 0.005, 3DoF camera
-0.25 m / 0.5 deg):
+0.25 m / 0.5 deg, 6DoF camera with a +-30 deg rotation prior in a 10 m box, 7
+levels):
 
 * sigma_m bounds the change of every basis function across every level's cells
   (Sec. 3.2: the essential parameters are rounded to a step scaled by how much
@@ -29,6 +30,7 @@ WORKLOADS = {
     "line": lambda: inputs.line2d(n=400, seed=inputs.SEED_BASE),
     "plane": lambda: inputs.plane3d(n=400, seed=inputs.SEED_BASE + 1),
     "pose": lambda: inputs.pose3dof(n=400, seed=inputs.SEED_BASE + 2),
+    "pose6": lambda: inputs.pose6dof(n=400, seed=inputs.SEED_BASE + 4),
 }
 
 
@@ -48,9 +50,16 @@ def essential_samples(p, rng):
     elif p.family == inputs.PLANE3D_SPH:
         ts = [p.params[:, i] for i in rng.choice(p.n, 20, replace=False)]
         ts += [np.array(v, float) for v in ([1, 1, 0], [1, 0, 0], [0, 0, 1], [0.7, -0.7, 0.1], [1, 1, 1])]
-    else:
+    elif p.family == inputs.POSE3DOF:
         ts = [p.params[2:, i] for i in rng.choice(p.n, 20, replace=False)]
         ts += [np.array(v, float) for v in ([50, 50], [-30, 80], [100, 0], [0, -100])]
+    else:                      # t = (w, xi w, eta w, xi, eta), plus arbitrary coefficient vectors
+        ts = []
+        for i in rng.choice(p.n, 20, replace=False):
+            w, xi, eta = p.params[0:3, i], p.params[3, i], p.params[4, i]
+            ts.append(np.concatenate([w, xi * w, eta * w, [xi, eta]]))
+        ts += [rng.normal(0.0, 10.0, 11) for _ in range(4)]
+        ts += [np.array([20, 20, 5, 20, 20, 5, -20, -20, -5, 1, -1], float)]
     return ts
 
 

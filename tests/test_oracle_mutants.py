@@ -44,8 +44,13 @@ MUTANTS = {
                                     "lam[1] = fabs(t[2]);"),
     "pose_lipschitz_max_component": ("lam[0] = r;\n        lam[1] = r;",
                                      "lam[0] = fmax(fabs(t[0]), fabs(t[1]));\n        lam[1] = lam[0];"),
-    "pose_sigma_halved": ("sigma[0] = h[0];\n        sigma[1] = h[0];\n        break;\n    }\n}",
-                          "sigma[0] = 0.5 * h[0];\n        sigma[1] = 0.5 * h[0];\n        break;\n    }\n}"),
+    "pose6_residual_row": ("double sy2 = (t[0] * d[3] + t[1] * d[4]) + t[2] * d[5];",
+                           "double sy2 = (t[0] * d[0] + t[1] * d[1]) + t[2] * d[2];"),
+    "pose6_rotation_sign": ("R[1] = b0 * ph[1] - a2;", "R[1] = b0 * ph[1] + a2;"),
+    "pose6_lipschitz_without_w": ("double lx = nxw + nw, ly = nyw + nw;", "double lx = nxw, ly = nyw;"),
+    "pose6_sigma_one_axis": ("double hr = (h[0] + h[1]) + h[2];", "double hr = h[0];"),
+    "pose_sigma_halved": ("(a, b) */\n        sigma[0] = h[0];\n        sigma[1] = h[0];",
+                          "(a, b) */\n        sigma[0] = 0.5 * h[0];\n        sigma[1] = 0.5 * h[0];"),
     "error_step_missing_essential_term": ("delta = delta + (p->s_t[l][m] * 0.5) * sigma[m];",
                                           "delta = delta + (p->s_t[l][m] * 0.25) * sigma[m];"),
 }
@@ -55,6 +60,7 @@ CASES = {
     inputs.PLANE3D_SPH: lambda s: inputs.plane3d(n=120, inlier_frac=0.3, eps=0.08, sigma=0.002, seed=s),
     inputs.POSE3DOF: lambda s: inputs.pose3dof(n=200, inlier_frac=0.3, eps_xy=2.0, eps_yaw_deg=4.0,
                                                noise_deg=0.05, seed=s),
+    inputs.POSE6DOF: lambda s: inputs.pose6dof(n=80, inlier_frac=0.3, levels=3, seed=s),
 }
 
 
@@ -78,13 +84,18 @@ def pins_hold(lib, fam, seed):
     if r["depth"] < max(best, int(brute.depth(p.family, p.params, dep, pts).max())):
         return False
     L, hL = lv["L"], lv["h"][lv["L"]]
+    st = lv["s_t"][-1].max()
     if p.family == inputs.LINE2D:
-        lam = np.abs(p.params[0]).max() + lv["s_t"][-1].max()
+        free = (np.abs(p.params[0]).max() + st) * hL[: p.k].sum()
     elif p.family == inputs.PLANE3D_SPH:
-        lam = np.linalg.norm(p.params, axis=0).max() + 2 * lv["s_t"][-1].max()
+        free = (np.linalg.norm(p.params, axis=0).max() + 2 * st) * hL[: p.k].sum()
+    elif p.family == inputs.POSE3DOF:
+        free = (np.hypot(p.params[2], p.params[3]).max() + 2 * st) * hL[: p.k].sum()
     else:
-        lam = np.hypot(p.params[2], p.params[3]).max() + 2 * lv["s_t"][-1].max()
-    ep = dep + hL[p.k:] + lam * hL[: p.k].sum() + 2 * lv["A"][L] + 1e-9
+        c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
+        free = ((((1.0 + c) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st) * hL[0:3].sum()
+                + (c.max() + st) * hL[3])
+    ep = dep + hL[p.k:] + free + 2 * lv["A"][L] + 1e-9
     if r["depth"] > brute.depth(p.family, p.params, ep, r["best_point"][None])[0]:
         return False
     members = oracle.mask_to_indices(r["mask"], p.n)
@@ -98,11 +109,14 @@ MARGIN_CASES = {
     inputs.LINE2D: lambda: inputs.line2d(n=200, seed=inputs.SEED_BASE),
     inputs.PLANE3D_SPH: lambda: inputs.plane3d(n=200, seed=inputs.SEED_BASE + 1),
     inputs.POSE3DOF: lambda: inputs.pose3dof(n=200, seed=inputs.SEED_BASE + 2),
+    inputs.POSE6DOF: lambda: inputs.pose6dof(n=200, seed=inputs.SEED_BASE + 4),
 }
 MARGIN_T = {
     inputs.LINE2D: [np.array([1.0]), np.array([0.3])],
     inputs.PLANE3D_SPH: [np.array(v, float) for v in ([1, 1, 0], [0.2, 0.9, 0.4], [1, 1, 1])],
     inputs.POSE3DOF: [np.array(v, float) for v in ([50, 50], [-30, 80], [100, 0])],
+    inputs.POSE6DOF: [np.array(v, float) for v in ([20, 20, 5, 20, 20, 5, -20, -20, -5, 1, -1],
+                                                   [3, -14, 2, 1, -5, 0.5, 2, -9, 1, 0.4, 0.6])],
 }
 
 
@@ -140,6 +154,7 @@ def test_planted_mistake_is_caught(name):
 
 @pytest.mark.parametrize("name", [m for m in sorted(MUTANTS) if m.startswith(("plane_sigma", "plane_lipschitz",
                                                                                "pose_lipschitz", "pose_sigma",
+                                                                               "pose6_lipschitz", "pose6_sigma",
                                                                                "error_step"))])
 def test_margin_mistake_is_caught_by_the_margin_pins(name):
     old, new = MUTANTS[name]

@@ -17,7 +17,7 @@ import brute
 import oracle
 from paper_2107_11810_gb300 import inputs
 
-L2, PL, P3 = oracle.LINE2D, oracle.PLANE3D_SPH, oracle.POSE3DOF
+L2, PL, P3, P6 = oracle.LINE2D, oracle.PLANE3D_SPH, oracle.POSE3DOF, oracle.POSE6DOF
 
 
 def small_plane(n, seed, eps=0.08, frac=0.3):
@@ -34,10 +34,15 @@ def small_line(n, seed, eps=0.01, frac=0.3):
     return inputs.line2d(n=n, inlier_frac=frac, eps=eps, seed=seed)
 
 
+def small_pose6(n, seed, frac=0.3, levels=3):
+    return inputs.pose6dof(n=n, inlier_frac=frac, levels=levels, seed=seed)
+
+
 CASES = [
     ("line", lambda s: small_line(300, s, eps=0.02)),
     ("plane", lambda s: small_plane(120, s)),
     ("pose", lambda s: small_pose(200, s)),
+    ("pose6", lambda s: small_pose6(80, s)),
 ]
 
 
@@ -134,12 +139,18 @@ def relaxed_eps(p, lv):
     change of the Lipschitz factor by snapping)."""
     L = lv["L"]
     hL = lv["h"][L]
+    st = lv["s_t"][-1].max()
     if p.family == L2:
-        lam = np.abs(p.params[0]).max() + lv["s_t"][-1].max()
+        lam = np.abs(p.params[0]).max() + st
     elif p.family == PL:
-        lam = np.linalg.norm(p.params, axis=0).max() + 2 * lv["s_t"][-1].max()
-    else:
-        lam = np.hypot(p.params[2], p.params[3]).max() + 2 * lv["s_t"][-1].max()
+        lam = np.linalg.norm(p.params, axis=0).max() + 2 * st
+    elif p.family == P3:
+        lam = np.hypot(p.params[2], p.params[3]).max() + 2 * st
+    else:          # |dF/dphi_a| <= (1 + max(|xi|, |eta|)) |w|, |dF/dz| <= max(|xi|, |eta|)
+        c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
+        lam_phi = ((1.0 + c) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st
+        lam_z = c.max() + st
+        return dep_eps(p) + hL[p.k:] + lam_phi * hL[0:3].sum() + lam_z * hL[3] + 2 * lv["A"][L] + 1e-9
     free = hL[: p.k].sum()
     return dep_eps(p) + hL[p.k:] + lam * free + 2 * lv["A"][L] + 1e-9
 
@@ -222,7 +233,8 @@ def test_trace_counts_equal_replay_and_monotone(name, mk):
 # ---------------------------------------------------------------------------
 
 def test_empty_input():
-    for mk in (lambda: small_line(10, 1), lambda: small_plane(10, 1), lambda: small_pose(10, 1)):
+    for mk in (lambda: small_line(10, 1), lambda: small_plane(10, 1), lambda: small_pose(10, 1),
+               lambda: small_pose6(10, 1)):
         p = mk()
         r = oracle.solve(p.family, p.eps, p.bounds, p.params[:, :0])
         assert r["depth"] == 0
