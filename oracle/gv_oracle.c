@@ -67,7 +67,7 @@
 #define GVO_MAXT 11
 #define GVO_MAXL 40
 
-enum { GVO_LINE2D = 1, GVO_PLANE3D_SPH = 2, GVO_POSE3DOF = 3, GVO_POSE6DOF = 4 };
+enum { GVO_LINE2D = 1, GVO_PLANE3D_SPH = 2, GVO_POSE3DOF = 3, GVO_POSE6DOF = 4, GVO_RAYS3D = 5 };
 enum { GVO_NO_MERGE = 1, GVO_NO_PRUNE = 2, GVO_REVERSE = 4 };
 
 /* ------------------------------------------------------------------------- */
@@ -189,6 +189,7 @@ static int family_shape(int fam, int d, int k, int *le, int *np)
     case GVO_PLANE3D_SPH: if (d != 3 || k != 2) return 1; *le = 3; *np = 3; return 0;
     case GVO_POSE3DOF:    if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
     case GVO_POSE6DOF:    if (d != 6 || k != 4) return 1; *le = 11; *np = 5; return 0;
+    case GVO_RAYS3D:      if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
     default: return 1;
     }
 }
@@ -211,6 +212,10 @@ static void family_sigma(const gvo_problem *p, const double *h, double *sigma)
         sigma[0] = h[0];
         sigma[1] = h[0];
         break;
+    case GVO_RAYS3D:      /* y = a x + b, z = c x + d: a and c multiply x */
+        sigma[0] = h[0];
+        sigma[1] = h[0];
+        break;
     case GVO_POSE6DOF: {  /* F = sum_m t_m psi_m with psi = entries of R(phi) and z */
         /* An entry R_ki of R(phi) has gradient e_k . (J e_a x R e_i) along phi_a, J the
          * rotation's Jacobian (operator norm 1), so |grad R_ki| <= 1 and the entry moves
@@ -227,7 +232,7 @@ static void family_sigma(const gvo_problem *p, const double *h, double *sigma)
 /* number of basis values psi of a family */
 static int family_nb(int fam, int le)
 {
-    return fam == GVO_POSE6DOF ? 10 : le;
+    return fam == GVO_POSE6DOF ? 10 : (fam == GVO_RAYS3D ? 1 : le);
 }
 
 static double pow2_floor(double x)  /* 2^floor(log2 x), exact */
@@ -297,7 +302,7 @@ static double cell_center(const gvo_problem *p, int l, int j, int64_t i)
 
 /* ------------------------------------------------------------------------- */
 /* Families (Sec. 3 Eq. 2 line duality; Sec. 4.1 plane fitting; 3DoF posing;   */
-/* Sec. 4.2.3 calibrated 6DoF posing).                                        */
+/* Sec. 4.2.3 calibrated 6DoF posing; Sec. 4.3 rays in 3-space).              */
 /* ------------------------------------------------------------------------- */
 
 /* Rotation matrix (row-major) of the axis-angle vector ph, theta = |ph|, by
@@ -331,6 +336,9 @@ static void family_basis(const gvo_problem *p, int l, const int64_t *i, double *
     switch (p->fam) {
     case GVO_LINE2D:
         psi[0] = cell_center(p, l, 0, i[0]);                  /* m */
+        break;
+    case GVO_RAYS3D:
+        psi[0] = cell_center(p, l, 0, i[0]);                  /* x */
         break;
     case GVO_PLANE3D_SPH: {
         double th = cell_center(p, l, 0, i[0]);
@@ -388,6 +396,14 @@ static void family_lift(const gvo_problem *p, const double *params, int64_t n, i
         r->f[1] = (w2 - (a * psi[1] + b * psi[0])) - c[2];
         break;
     }
+    case GVO_RAYS3D: {                      /* ray y = a x + b, z = c x + d (Sec. 4.3) */
+        double a = params[0 * n + i], b = params[1 * n + i];
+        double cc = params[2 * n + i], dd = params[3 * n + i];
+        r->t[0] = a; r->t[1] = cc;
+        r->f[0] = (a * psi[0] + b) - c[1];
+        r->f[1] = (cc * psi[0] + dd) - c[2];
+        break;
+    }
     case GVO_POSE6DOF: {
         /* match (w, xi, eta): x = xi (r3 . w + z) - r1 . w, y = eta (r3 . w + z) - r2 . w
          * (Sec. 4.2.2 with f = 1, Sec. 4.2.3).  Affine in the basis (rows of R, z) with
@@ -443,7 +459,7 @@ static void child_geometry(const gvo_problem *p, int l, const int64_t *i, const 
             g->shift[j] = 0.0;
         }
     }
-    if (p->fam == GVO_LINE2D) {
+    if (p->fam == GVO_LINE2D || p->fam == GVO_RAYS3D) {
         g->dpsi[0] = g->shift[0];       /* psi is linear: exact shift */
     } else {
         double psi_child[GVO_MAXT];
@@ -467,6 +483,10 @@ static void family_residual(const gvo_problem *p, const double *f, const double 
     case GVO_POSE3DOF:
         fo[0] = (f[0] - (t[0] * g->dpsi[0] - t[1] * g->dpsi[1])) - g->shift[1];
         fo[1] = (f[1] - (t[0] * g->dpsi[1] + t[1] * g->dpsi[0])) - g->shift[2];
+        break;
+    case GVO_RAYS3D:
+        fo[0] = (f[0] + t[0] * g->dpsi[0]) - g->shift[1];
+        fo[1] = (f[1] + t[1] * g->dpsi[0]) - g->shift[2];
         break;
     case GVO_POSE6DOF: {
         const double *d = g->dpsi;
@@ -498,6 +518,10 @@ static void family_lipschitz(const gvo_problem *p, const double *t, double *lam)
         lam[1] = r;
         break;
     }
+    case GVO_RAYS3D:                        /* dy/dx = a, dz/dx = c */
+        lam[0] = fabs(t[0]);
+        lam[1] = fabs(t[1]);
+        break;
     case GVO_POSE6DOF: {
         /* d/dphi_a of e_k . R v is e_k . (J e_a x R v), at most |v| (J of norm 1):
          * |dx/dphi_a| <= |xi w| + |w|, |dy/dphi_a| <= |eta w| + |w|; dx/dz = xi, dy/dz = eta */

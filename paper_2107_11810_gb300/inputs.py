@@ -22,6 +22,8 @@ Surface parameters are FP64, structure-of-arrays ``params[P, n]``:
   phi the axis-angle vector of the rotation and (x, y, z) the translation of the
   camera frame X = R(phi) w + (x, y, z), with x = xi (r3 . w + z) - r1 . w and
   y = eta (r3 . w + z) - r2 . w.
+* ``RAYS3D``      (intersection of rays in 3-space, Sec. 4.3): P = 4, rows (a, b, c, d)
+  of the ray y = a x + b, z = c x + d; voting space (x, y, z).
 """
 from __future__ import annotations
 
@@ -30,9 +32,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF = 1, 2, 3, 4
-FAMILY_NAMES = {LINE2D: "LINE2D", PLANE3D_SPH: "PLANE3D_SPH", POSE3DOF: "POSE3DOF", POSE6DOF: "POSE6DOF"}
-FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1), POSE6DOF: (6, 4)}
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D = 1, 2, 3, 4, 5
+FAMILY_NAMES = {LINE2D: "LINE2D", PLANE3D_SPH: "PLANE3D_SPH", POSE3DOF: "POSE3DOF", POSE6DOF: "POSE6DOF",
+                RAYS3D: "RAYS3D"}
+FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1), POSE6DOF: (6, 4), RAYS3D: (3, 1)}
 SEED_BASE = 2107118100
 
 
@@ -299,6 +302,31 @@ def pose6dof(n: int = 5000, inlier_frac: float = 0.05, prior_deg: float = 30.0, 
                    dict(inlier_frac=inlier_frac, prior=prior, prior_deg=prior_deg, levels=levels))
 
 
+def rays3d(n: int = 100_000, inlier_frac: float = 0.02, eps: float = 0.002, noise: float = 0.0005,
+           slope: float = 2.0, seed: int = SEED_BASE + 5) -> Problem:
+    """Rays y = a x + b, z = c x + d in the unit cube: ``inlier_frac`` of them pass
+    within N(0, noise) (in y and z) of a common point p ~ U[0.2, 0.8]^3, the rest
+    through a uniform point of the cube; slopes a, c ~ U[-slope, slope].  Voting
+    domain [0, 1]^3 in (x, y, z); eps in every coordinate."""
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(0.2, 0.8, 3)
+    n_in = int(round(n * inlier_frac))
+    a = rng.uniform(-slope, slope, n)
+    c = rng.uniform(-slope, slope, n)
+    q = rng.uniform(0.0, 1.0, (n, 3))
+    q[:n_in] = p
+    b = q[:, 1] - a * q[:, 0]
+    d = q[:, 2] - c * q[:, 0]
+    b[:n_in] += rng.normal(0.0, noise, n_in)
+    d[:n_in] += rng.normal(0.0, noise, n_in)
+    out = np.stack([a, b, c, d])
+    perm = rng.permutation(n)
+    out = out[:, perm]
+    inliers = np.nonzero(perm < n_in)[0]
+    return Problem(RAYS3D, np.full(3, eps), np.array([0.0, 1.0, 0.0, 1.0, 0.0, 1.0]), np.ascontiguousarray(out),
+                   p.copy(), inliers, "rays3d", dict(inlier_frac=inlier_frac))
+
+
 # ---------------------------------------------------------------------------
 # Standard workloads
 # ---------------------------------------------------------------------------
@@ -320,4 +348,6 @@ def random_small(family: int, n: int, seed: int, inlier_frac: float = 0.3, **kw)
         return pose3dof(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
     if family == POSE6DOF:
         return pose6dof(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
+    if family == RAYS3D:
+        return rays3d(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
     raise ValueError(family)

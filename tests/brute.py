@@ -11,7 +11,7 @@ import itertools
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF = 1, 2, 3, 4
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D = 1, 2, 3, 4, 5
 
 
 def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.ndarray:
@@ -32,6 +32,10 @@ def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.n
         fx = w1 - (a * np.cos(yaw) - b * np.sin(yaw))
         fy = w2 - (a * np.sin(yaw) + b * np.cos(yaw))
         return np.stack([x - fx, y - fy], axis=-1)
+    if family == RAYS3D:                 # y = a x + b, z = c x + d (Sec. 4.3)
+        a, b, c, d = params
+        x, y, z = pts[:, 0:1], pts[:, 1:2], pts[:, 2:3]
+        return np.stack([y - (a * x + b), z - (c * x + d)], axis=-1)
     if family == POSE6DOF:               # calibrated camera: X = R(phi) w + (x, y, z) (Sec. 4.2.3)
         from scipy.spatial.transform import Rotation
         w = np.asarray(params[0:3], float)                    # [3, n]

@@ -28,7 +28,7 @@ import numpy as np
 import brute
 import oracle
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF = 1, 2, 3, 4
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D = 1, 2, 3, 4, 5
 
 
 def _rot(x):
@@ -49,6 +49,8 @@ def basis(family: int, x: np.ndarray) -> np.ndarray:
         return np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=-1)
     if family == POSE3DOF:          # (x, y) = w - R(yaw) (a, b)
         return np.stack([np.cos(x[..., 0]), np.sin(x[..., 0])], axis=-1)
+    if family == RAYS3D:            # y = a x + b, z = c x + d: a and c multiply x
+        return np.concatenate([x[..., 0:1], x[..., 0:1]], axis=-1)
     if family == POSE6DOF:          # t = (w, xi w, eta w, xi, eta); rows of R(phi) and z
         Rm = _rot(x[..., 0:3])
         z = x[..., 3:4]
@@ -71,6 +73,8 @@ def t_part(family: int, t: np.ndarray, x: np.ndarray) -> np.ndarray:
         a, b = t
         c, s = psi[..., 0], psi[..., 1]
         return np.stack([-(a * c - b * s), -(a * s + b * c)], axis=-1)
+    if family == RAYS3D:
+        return np.stack([t[0] * psi[..., 0], t[1] * psi[..., 1]], axis=-1)
     if family == POSE6DOF:
         t = np.asarray(t, float)
         return np.stack([psi[..., :11] @ t, psi[..., 11:] @ t], axis=-1)

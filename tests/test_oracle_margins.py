@@ -6,7 +6,7 @@ surface happens to sit inside that margin.  Here each margin is checked on its
 own, against the surface equations (tests/margins.py), on the level structures
 of the benchmark workloads (2D line eps 0.01, 3D plane eps 0.005, 3DoF camera
 0.25 m / 0.5 deg, 6DoF camera with a +-30 deg rotation prior in a 10 m box, 7
-levels):
+levels, rays in the unit cube eps 0.002):
 
 * sigma_m bounds the change of every basis function across every level's cells
   (Sec. 3.2: the essential parameters are rounded to a step scaled by how much
@@ -31,6 +31,7 @@ WORKLOADS = {
     "plane": lambda: inputs.plane3d(n=400, seed=inputs.SEED_BASE + 1),
     "pose": lambda: inputs.pose3dof(n=400, seed=inputs.SEED_BASE + 2),
     "pose6": lambda: inputs.pose6dof(n=400, seed=inputs.SEED_BASE + 4),
+    "rays": lambda: inputs.rays3d(n=400, seed=inputs.SEED_BASE + 5),
 }
 
 
@@ -53,6 +54,9 @@ def essential_samples(p, rng):
     elif p.family == inputs.POSE3DOF:
         ts = [p.params[2:, i] for i in rng.choice(p.n, 20, replace=False)]
         ts += [np.array(v, float) for v in ([50, 50], [-30, 80], [100, 0], [0, -100])]
+    elif p.family == inputs.RAYS3D:
+        ts = [p.params[[0, 2], i] for i in rng.choice(p.n, 20, replace=False)]
+        ts += [np.array(v, float) for v in ([2, -2], [0, 1], [-1.5, 0])]
     else:                      # t = (w, xi w, eta w, xi, eta), plus arbitrary coefficient vectors
         ts = []
         for i in rng.choice(p.n, 20, replace=False):

@@ -44,6 +44,10 @@ MUTANTS = {
                                     "lam[1] = fabs(t[2]);"),
     "pose_lipschitz_max_component": ("lam[0] = r;\n        lam[1] = r;",
                                      "lam[0] = fmax(fabs(t[0]), fabs(t[1]));\n        lam[1] = lam[0];"),
+    "rays_residual_slope": ("fo[1] = (f[1] + t[1] * g->dpsi[0]) - g->shift[2];",
+                            "fo[1] = (f[1] + t[0] * g->dpsi[0]) - g->shift[2];"),
+    "rays_lipschitz_one_slope": ("lam[0] = fabs(t[0]);\n        lam[1] = fabs(t[1]);",
+                                 "lam[0] = fabs(t[0]);\n        lam[1] = fabs(t[0]);"),
     "pose6_residual_row": ("double sy2 = (t[0] * d[3] + t[1] * d[4]) + t[2] * d[5];",
                            "double sy2 = (t[0] * d[0] + t[1] * d[1]) + t[2] * d[2];"),
     "pose6_rotation_sign": ("R[1] = b0 * ph[1] - a2;", "R[1] = b0 * ph[1] + a2;"),
@@ -61,6 +65,7 @@ CASES = {
     inputs.POSE3DOF: lambda s: inputs.pose3dof(n=200, inlier_frac=0.3, eps_xy=2.0, eps_yaw_deg=4.0,
                                                noise_deg=0.05, seed=s),
     inputs.POSE6DOF: lambda s: inputs.pose6dof(n=80, inlier_frac=0.3, levels=3, seed=s),
+    inputs.RAYS3D: lambda s: inputs.rays3d(n=300, inlier_frac=0.3, eps=0.03, noise=0.002, seed=s),
 }
 
 
@@ -91,6 +96,8 @@ def pins_hold(lib, fam, seed):
         free = (np.linalg.norm(p.params, axis=0).max() + 2 * st) * hL[: p.k].sum()
     elif p.family == inputs.POSE3DOF:
         free = (np.hypot(p.params[2], p.params[3]).max() + 2 * st) * hL[: p.k].sum()
+    elif p.family == inputs.RAYS3D:
+        free = (np.maximum(np.abs(p.params[0]), np.abs(p.params[2])).max() + st) * hL[: p.k].sum()
     else:
         c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
         free = ((((1.0 + c) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st) * hL[0:3].sum()
@@ -110,6 +117,7 @@ MARGIN_CASES = {
     inputs.PLANE3D_SPH: lambda: inputs.plane3d(n=200, seed=inputs.SEED_BASE + 1),
     inputs.POSE3DOF: lambda: inputs.pose3dof(n=200, seed=inputs.SEED_BASE + 2),
     inputs.POSE6DOF: lambda: inputs.pose6dof(n=200, seed=inputs.SEED_BASE + 4),
+    inputs.RAYS3D: lambda: inputs.rays3d(n=200, seed=inputs.SEED_BASE + 5),
 }
 MARGIN_T = {
     inputs.LINE2D: [np.array([1.0]), np.array([0.3])],
@@ -117,6 +125,7 @@ MARGIN_T = {
     inputs.POSE3DOF: [np.array(v, float) for v in ([50, 50], [-30, 80], [100, 0])],
     inputs.POSE6DOF: [np.array(v, float) for v in ([20, 20, 5, 20, 20, 5, -20, -20, -5, 1, -1],
                                                    [3, -14, 2, 1, -5, 0.5, 2, -9, 1, 0.4, 0.6])],
+    inputs.RAYS3D: [np.array(v, float) for v in ([2, -2], [0.3, 1.7])],
 }
 
 
@@ -155,6 +164,7 @@ def test_planted_mistake_is_caught(name):
 @pytest.mark.parametrize("name", [m for m in sorted(MUTANTS) if m.startswith(("plane_sigma", "plane_lipschitz",
                                                                                "pose_lipschitz", "pose_sigma",
                                                                                "pose6_lipschitz", "pose6_sigma",
+                                                                               "rays_lipschitz",
                                                                                "error_step"))])
 def test_margin_mistake_is_caught_by_the_margin_pins(name):
     old, new = MUTANTS[name]
