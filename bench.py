@@ -6,11 +6,12 @@ like the paper's workloads; the default is 3D plane fitting with 1,000,000
 points (2 % on a plane, eps = 0.005, (theta, phi, d) space).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                    [--impl gv|reference] [--no-fp64] [--no-cpu]
+                    [--impl gv|reference] [--no-fp64] [--no-cpu] [--no-group-stats]
 
 After the timed steps, one plain-FP64 solve of the same workload checks that the
 two precision modes give identical results and times it (the metric's
-comparison); the oracle (plain FP64 C on the host cores) is timed on a bounded
+comparison), one solve with grouping on reports the grouping's merge fraction per
+level, and the oracle (plain FP64 C on the host cores) is timed on a bounded
 sample.  Prints one JSON line (rank 0).  Under torchrun every rank solves its own copy
 of the problem (independent problems, no collective): weak scaling.
 """
@@ -38,9 +39,10 @@ METRIC = "solved problems/sec and surface-cell tests/sec: FP32+recheck vs plain 
 
 WORKLOADS = {
     "plane3d_n1e6": dict(make=lambda: inputs.plane3d(), desc="3D plane fitting, 1e6 points in the unit cube, "
-                         "2% inliers (sigma 0.001), eps_d=0.005, eps_angle=eps/sqrt3, (theta,phi,d) space"),
+                         "2% inliers (sigma 0.001), eps_d=0.005, eps_angle=eps/sqrt3, (theta,phi,d) space",
+                         group_sample=lambda: inputs.plane3d(n=10_000)),
     "pose3dof_n1e6": dict(make=lambda: inputs.pose3dof(), desc="3DoF camera voting, 1e6 matches, 1% inliers, "
-                          "eps 0.25 m / 0.5 deg, (yaw,x,y) space"),
+                          "eps 0.25 m / 0.5 deg, (yaw,x,y) space", group_sample=lambda: inputs.pose3dof(n=100_000)),
     "line2d_n1e4": dict(make=lambda: inputs.line2d(), desc="2D line fitting, 1e4 points, 10% inliers, eps 0.01, "
                         "(m,b) space"),
     "plane3d_n1e4": dict(make=lambda: inputs.plane3d(n=10_000), desc="3D plane fitting, 1e4 points (the plane "
@@ -49,13 +51,19 @@ WORKLOADS = {
                          "workload's shape at a tenth of its size; a small target for profiler captures)"),
     "pose3dof_n3e5": dict(make=lambda: inputs.pose3dof(n=300_000), desc="3DoF camera voting, 3e5 matches (a small "
                           "target for profiler captures)"),
+    "pose6dof_n5000": dict(make=lambda: inputs.pose6dof(n=5000, prior_deg=30.0), desc="6DoF calibrated-camera "
+                           "voting, 5,000 matches (250 inliers, 0.1 deg bearing noise), rotation prior +-30 deg per "
+                           "axis, 10 m translation box, 7 levels per coordinate, constant vertical tolerance "
+                           "box/128 in x and y, (phi1,phi2,phi3,z,x,y) space"),
+    "pose6dof_prior5_n5000": dict(make=lambda: inputs.pose6dof(n=5000, prior_deg=5.0), desc="6DoF calibrated-"
+                                  "camera voting as pose6dof_n5000 with a +-5 deg rotation prior"),
     "pose3dof_batch256": dict(make=lambda: inputs.pose3dof_batch(), batched=True,
                               desc="256 independent 3DoF problems, n log-uniform in [1e3, 1e6], inlier ratio "
                                    "U[0.5%, 5%]; one vote_solve_batched call per step"),
 }
 # FP32-pipe instructions per (child cell, canonical surface) test, counted from
 # the formulas of each family's residual and comparisons
-INSTR_PER_TEST = {inputs.LINE2D: 7, inputs.PLANE3D_SPH: 10, inputs.POSE3DOF: 14}
+INSTR_PER_TEST = {inputs.LINE2D: 7, inputs.PLANE3D_SPH: 10, inputs.POSE3DOF: 14, inputs.POSE6DOF: 30}
 
 
 def env_rank():
@@ -118,9 +126,14 @@ class ClockSampler:
                     reasons=reasons, samples=len(self.samples))
 
 
-def kernel_hash():
+KERNEL_SOURCES = {"k_count": ("gv_count.cu", "gv_tile.cuh", "gv_device.cuh", "gv_kernels.h"),
+                  "k_emit": ("gv_emit.cu", "gv_tile.cuh", "gv_device.cuh", "gv_kernels.h")}
+
+
+def kernel_hash(kernel: str):
+    """sha256 (first 16 hex digits) of the sources a kernel is built from."""
     h = hashlib.sha256()
-    for f in ("gv_kernels.cu", "gv_device.cuh", "gv_kernels.h"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2107_11810_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -134,7 +147,7 @@ def recorded_traffic(kernel: str, family: str, algorithmic_bytes_per_launch: flo
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    kh = kernel_hash()
+    kh = kernel_hash(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and not line.startswith("#") and parts[0] == kh and parts[1] == kernel \
@@ -272,6 +285,8 @@ def main():
                     help="skip the plain-FP64 predicate solve of the same workload that follows the timed steps "
                          "(the metric's comparison: FP32 screen + FP64 recheck vs plain FP64, identical results)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-group-stats", action="store_true",
+                    help="skip the grouped solve that reports the grouping's per-level merge fraction")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--ref-tests-per-problem", type=float, default=0.0)
     args = ap.parse_args()
@@ -347,23 +362,26 @@ def main():
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         alu_peak = sms * 128 * pk["sm_max_mhz"] * 1e6 / 1e12
         roof = dict(bound="alu", achieved=achieved, peak=alu_peak, unit="TFP32-instr/s",
-                    frac=achieved / alu_peak, kernel="k_test<count>",
+                    frac=achieved / alu_peak, kernel="k_count",
                     peak_src=f"{sms} SMs (device property) x 128 FP32 lanes x {pk['sm_max_mhz']:.0f} MHz max SM "
                              f"clock ({pk['src']}); thread instructions/s, no FMA doubling",
-                    traffic=recorded_traffic("k_test_count", inputs.FAMILY_NAMES[p.family], by / max(nl, 1)),
+                    traffic=recorded_traffic("k_count", inputs.FAMILY_NAMES[p.family], by / max(nl, 1)),
                     bytes_per_launch=by / max(nl, 1))
     else:
         achieved = by / max(nl, 1) / avg_s / 1e9
         roof = dict(bound="hbm", achieved=achieved, peak=pk["hbm_gbs"], unit="GB/s",
-                    frac=achieved / pk["hbm_gbs"], kernel=f"k_test<{dom[5:]}>", peak_src=pk["src"],
-                    traffic=recorded_traffic("k_" + dom, inputs.FAMILY_NAMES[p.family], by / max(nl, 1)),
+                    frac=achieved / pk["hbm_gbs"], kernel="k_" + dom[5:], peak_src=pk["src"],
+                    traffic=recorded_traffic("k_" + dom[5:], inputs.FAMILY_NAMES[p.family], by / max(nl, 1)),
                     bytes_per_launch=by / max(nl, 1))
     roof["share_of_step"] = kt[dom][0] / 1000.0 / total * world
     if kt["test_emit"][1]:
         e_ms, e_nl, e_by = kt["test_emit"]
-        roof["emit_kernel"] = dict(bound="hbm", achieved=e_by / (e_ms / 1000.0) / 1e9, peak=pk["hbm_gbs"],
-                                   unit="GB/s", frac=e_by / (e_ms / 1000.0) / 1e9 / pk["hbm_gbs"],
-                                   share_of_step=e_ms / 1000.0 / total * world)
+        roof["emit_kernel"] = dict(kernel="k_emit", bound="hbm", achieved=e_by / (e_ms / 1000.0) / 1e9,
+                                   peak=pk["hbm_gbs"], unit="GB/s",
+                                   frac=e_by / (e_ms / 1000.0) / 1e9 / pk["hbm_gbs"],
+                                   share_of_step=e_ms / 1000.0 / total * world,
+                                   traffic=recorded_traffic("k_emit", inputs.FAMILY_NAMES[p.family],
+                                                            e_by / max(e_nl, 1)))
     # end to end through the public API with host buffers
     pinned = torch.from_numpy(p.params).pin_memory()
     e2e_times = []
@@ -402,6 +420,36 @@ def main():
                                  speedup_fp32_screen=value / world * t64,
                                  note="one plain-FP64 solve of the same workload after the timed steps")
         s.set_option(vote.VOTE_OPT_PRECISION, 1)
+    if not args.no_group_stats:
+        # per-level merge fraction of the canonization's grouping (records in ->
+        # canonical records out): one solve with grouping on and one without, on the
+        # workload's own instance when it is small, else on the same generator with
+        # fewer surfaces (grouping hashes every record of every step: on the 1e6-point
+        # plane that is about 1.3e12 records, hours of work)
+        wg = w.get("group_sample", None)
+        pg = wg() if wg else p
+        sg = vote.Solver(pg.family, pg.eps, pg.bounds, precision=args.precision, stream=stream)
+        tg = torch.from_numpy(pg.params).cuda()
+        r0 = sg.solve(tg)
+        sg.set_option(vote.VOTE_OPT_GROUP, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rg = sg.solve(tg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ls = sg.level_stats()
+        gin, gout = ls["grouped_in"], ls["grouped_out"]
+        out["grouping"] = dict(
+            workload=f"{args.workload} generator at n={pg.n}" if wg else args.workload,
+            seconds=e0.elapsed_time(e1) / 1000.0,
+            identical_results=bool(rg["depth"] == r0["depth"] and rg["best_leaf"].tolist() == r0["best_leaf"].tolist()
+                                   and torch.equal(rg["mask"], r0["mask"])),
+            records_in=int(gin.sum()), records_out=int(gout.sum()),
+            merge_fraction=1.0 - float(gout.sum()) / max(float(gin.sum()), 1.0),
+            merge_fraction_per_level=[round(1.0 - float(o) / float(i), 6) if i else None
+                                      for i, o in zip(gin.tolist(), gout.tolist())],
+            note="VOTE_OPT_GROUP=1 after the timed steps; the timed path runs without grouping")
     if rank == 0 and not args.no_cpu:
         try:
             smp = oracle_sample(p, 16.0)

@@ -62,11 +62,25 @@ typedef enum {
  *                    surfaces x = w1 - (a cos yaw - b sin yaw),
  *                    y = w2 - (a sin yaw + b cos yaw) (camera posing with known
  *                    gravity, focal length and height; the 3DoF reduction of
- *                    the Sec. 4.2.1 formulation). */
+ *                    the Sec. 4.2.1 formulation).
+ *   VOTE_POSE6DOF    d=6 k=4: coords (phi1, phi2, phi3, z, x, y), phi the
+ *                    axis-angle vector of the rotation and (x, y, z) the
+ *                    translation of the camera frame X = R(phi) w + (x, y, z);
+ *                    input rows (w1, w2, w3, xi, eta) of a match between world
+ *                    point w and normalized image point (xi, eta); surfaces
+ *                    x = xi (r3 . w + z) - r1 . w, y = eta (r3 . w + z) - r2 . w
+ *                    (calibrated camera, Sec. 4.2.3: Sec. 4.2.2 with f = 1).
+ *                    The tolerance of x and y is a constant vertical distance;
+ *                    cells split into 64 children.
+ *   VOTE_RAYS3D      d=3 k=1: coords (x, y, z); input rows (a, b, c, d) of the
+ *                    ray y = a x + b, z = c x + d (intersection of rays in
+ *                    3-space, Sec. 4.3). */
 typedef enum {
     VOTE_LINE2D = 1,
     VOTE_PLANE3D_SPH = 2,
-    VOTE_POSE3DOF = 3
+    VOTE_POSE3DOF = 3,
+    VOTE_POSE6DOF = 4,
+    VOTE_RAYS3D = 5
 } vote_family;
 
 /* Options for vote_set_option. */
@@ -99,6 +113,10 @@ typedef enum {
                                  (default): on for n >= 131072 surfaces.  Results do
                                  not depend on it (Sec. 3.3: any valid bound may
                                  prune)                                              */
+    VOTE_OPT_SPIN_LIMIT = 12, /* polls of a bounded device-side wait (the proximity
+                                 passes' wait for their bulk copies) before the kernel
+                                 gives up and the solve returns VOTE_ETIMEOUT;
+                                 default 4194304; 0 gives up at once (test hook)     */
 } vote_option;
 
 /* Kernel classes reported by vote_get_kernel_times. */
@@ -239,9 +257,14 @@ vote_status vote_get_stats(vote_ctx *ctx, vote_stats *out);
  * VOTE_K_CLASSES entries (host). */
 vote_status vote_get_kernel_times(vote_ctx *ctx, double *ms, int64_t *launches, double *bytes);
 
-/* Per-level work of the last solve: cells[l] expanded and records[l] tested at
- * level l, for l in [0, L) (host arrays of at least L entries). */
-vote_status vote_get_level_stats(vote_ctx *ctx, int64_t *cells, int64_t *records);
+/* Per-level work of the last solve, for l in [0, L) (host arrays of at least L
+ * entries, each may be NULL): cells[l] expanded and record slots[l] tested at
+ * level l; with VOTE_OPT_GROUP on, grouped_in[l] records entered the grouping of
+ * level l (the canonization's merge of equal canonical surfaces, Sec. 3.2) and
+ * grouped_out[l] canonical records left it (both 0 with grouping off), so
+ * 1 - grouped_out/grouped_in is the level's merge fraction. */
+vote_status vote_get_level_stats(vote_ctx *ctx, int64_t *cells, int64_t *records, int64_t *grouped_in,
+                                 int64_t *grouped_out);
 
 /* UB and LB of one cell, like vote_cell_counts, for callers that cannot allocate
  * device memory: code running where cudaMalloc is not allowed or not wanted (a
@@ -264,7 +287,7 @@ vote_status vote_get_level_stats(vote_ctx *ctx, int64_t *cells, int64_t *records
  * are cleared at the start of each call): calls that may overlap on the GPU (on
  * different streams or host threads) race and must be serialised by the caller.
  * The call synchronises the stream before returning. */
-#define VOTE_NOALLOC_SCRATCH_BYTES 32768
+#define VOTE_NOALLOC_SCRATCH_BYTES 65536
 vote_status vote_cell_counts_noalloc(int family, int d, int k, const double *eps, const double *bounds,
                                      const double *surfaces, int64_t n, int level, const int64_t *coords,
                                      int64_t *ub, int64_t *lb, uint32_t *reach, void *cuda_stream);

@@ -12,7 +12,23 @@ from __future__ import annotations
 
 import torch
 
-LINE2D, PLANE3D_SPH, POSE3DOF = 1, 2, 3
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D = 1, 2, 3, 4, 5
+
+
+def rotation(phi: torch.Tensor) -> torch.Tensor:
+    """Rotation matrix of the axis-angle vector phi (Rodrigues' formula)."""
+    th2 = (phi * phi).sum()
+    K = torch.stack([torch.stack([phi.new_zeros(()), -phi[2], phi[1]]),
+                     torch.stack([phi[2], phi.new_zeros(()), -phi[0]]),
+                     torch.stack([-phi[1], phi[0], phi.new_zeros(())])])
+    if float(th2) < 1e-8:
+        a = 1.0 - th2 / 6.0
+        b = 0.5 - th2 / 24.0
+    else:
+        th = torch.sqrt(th2)
+        a = torch.sin(th) / th
+        b = (1.0 - torch.cos(th)) / th2
+    return torch.eye(3, dtype=phi.dtype) + a * K + b * (K @ K)
 
 
 def residuals(family: int, params: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
@@ -31,6 +47,15 @@ def residuals(family: int, params: torch.Tensor, p: torch.Tensor) -> torch.Tenso
         c, s = torch.cos(p[0]), torch.sin(p[0])
         rx = p[1] - (w1 - (a * c - b * s))
         ry = p[2] - (w2 - (a * s + b * c))
+        return torch.stack([rx, ry], dim=1)
+    if family == RAYS3D:                       # y = a x + b, z = c x + d
+        a, b, c, d = params[0], params[1], params[2], params[3]
+        return torch.stack([p[1] - (a * p[0] + b), p[2] - (c * p[0] + d)], dim=1)
+    if family == POSE6DOF:                     # x = xi (r3 . w + z) - r1 . w, y = eta (r3 . w + z) - r2 . w
+        X = rotation(p[0:3]) @ params[0:3]     # [3, n]
+        depth = X[2] + p[3]
+        rx = p[4] - (params[3] * depth - X[0])
+        ry = p[5] - (params[4] * depth - X[1])
         return torch.stack([rx, ry], dim=1)
     raise ValueError(family)
 

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvote.so")
-SOURCES = ["gv_kernels.cu", "gv_count.cu", "gv_emit.cu", "gv_engine.cu", "gv_softscore.cu"]
+SOURCES = ["gv_kernels.cu", "gv_count.cu", "gv_emit.cu", "gv_wide.cu", "gv_engine.cu", "gv_softscore.cu"]
 HEADERS = ["gv_device.cuh", "gv_kernels.h", "gv_tile.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

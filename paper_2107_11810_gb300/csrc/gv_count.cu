@@ -129,14 +129,14 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_COUNT) k_count(const __grid_
         acc = 0;
     };
 
-    bool failed = false;
+    int64_t gfail = -1;                                             // group whose copy did not arrive
 #pragma unroll 1
     for (int64_t g = g0; g < g1; ++g) {
         const int b = (int)((g - g0) & 1);
         if (threadIdx.x == 0 && g + 1 < g1) issue(g + 1);
-        const bool ok = mbar_wait(&s_bar[b], (unsigned)(((g - g0) >> 1) & 1), GV_SPIN_LIMIT, &c.sc->err);
+        const bool ok = mbar_wait(&s_bar[b], (unsigned)(((g - g0) >> 1) & 1), c.spin, &c.sc->err);
         if (__syncthreads_or(!ok)) {                                // uniform: a copy did not arrive
-            failed = true;
+            gfail = g;
             break;
         }
 #pragma unroll 1
@@ -283,10 +283,12 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_COUNT) k_count(const __grid_
         if (!WEIGHTED) drain();
         __syncthreads();                                            // buffer b is free again
     }
-    if (failed && threadIdx.x == 0) {
-        // a copy may still be in flight into the other buffer: wait for it (bounded)
-        // before the block's shared memory is released
-        for (int64_t g = g0; g < g1; ++g) {
+    if (gfail >= 0 && threadIdx.x == 0) {
+        // the copies of groups gfail and gfail + 1 (no later one was issued) may still
+        // be in flight: wait for them, bounded, before the block's shared memory is
+        // released
+        const int64_t ge = gfail + 2 < g1 ? gfail + 2 : g1;
+        for (int64_t g = gfail; g < ge; ++g) {
             const int b = (int)((g - g0) & 1);
             if (!mbar_wait(&s_bar[b], (unsigned)(((g - g0) >> 1) & 1), GV_SPIN_LIMIT, &c.sc->err)) break;
         }
@@ -307,6 +309,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_COUNT) k_count(const __grid_
     case FAM_LINE2D: { constexpr int FAMV = FAM_LINE2D; CALL; } break;           \
     case FAM_PLANE3D_SPH: { constexpr int FAMV = FAM_PLANE3D_SPH; CALL; } break; \
     case FAM_POSE3DOF: { constexpr int FAMV = FAM_POSE3DOF; CALL; } break;       \
+    case FAM_RAYS3D: { constexpr int FAMV = FAM_RAYS3D; CALL; } break;           \
     default: break;                                                              \
     }
 
@@ -316,6 +319,10 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_COUNT) k_count(const __grid_
 void launch_count(const Chunk &c, cudaStream_t st) {
     const int64_t nt = c.t1 - c.t0;
     if (nt <= 0) return;
+    if (c.P.d > 3) {
+        launch_count_wide(c, st);
+        return;
+    }
     const int64_t ng = (nt + kBlockTiles - 1) / kBlockTiles;
     const bool w = c.in.mult != nullptr;
 #define GV_COUNT(Q16, PREC)                                                                                   \

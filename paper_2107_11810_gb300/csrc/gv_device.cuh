@@ -17,7 +17,7 @@
 #include <cstdint>
 
 #define GV_MAXD 6
-#define GV_MAXT 5
+#define GV_MAXT 11
 #define GV_MAXL 32
 
 namespace gv {
@@ -32,6 +32,7 @@ struct Problem {
     int coord_bits;            // sum of Lj
     double lo[GV_MAXD], W[GV_MAXD], eps[GV_MAXD];
     double s_f[GV_MAXD], inv_s_f[GV_MAXD];  // per dependent coordinate
+    double inv_fact[31];       // 1/m!, from m! = m (m-1)! in FP64 (the 6DoF rotation's series)
 };
 
 struct Level {                 // tests of the children of a level-l cell
@@ -138,12 +139,15 @@ __device__ __forceinline__ uint64_t child_key(const Problem &P, uint64_t key, in
 
 // ---------------------------------------------------------------------------
 // Families.  For each: D, K (free coords), ND (dependent), LE (essential params),
-// NP (input rows), NB (basis values), NFP (record fields, padded to a power of
-// two); basis(), lift(), residual64(), partial64(), lipschitz64() (the exact FP64
-// definition), and for the FP32 screen coef() (coefficient of t_m in dependent
-// residual j for a basis change) and radius32() (the UB radius in steps).
+// NP (input rows), NB (basis values), NFP (record fields, padded so that a record
+// is 1, 2 or a multiple of 4 words); basis(), lift(), residual64(), partial64(),
+// lipschitz64() (the exact FP64 definition), and for the FP32 screen coef()
+// (coefficient of t_m in dependent residual j for a basis change), uses(j, m)
+// (whether t_m enters residual j at all) and radius32() (the UB radius in steps).
+// LINEAR_BASIS: the basis is the free coordinate itself; LINEAR_TAIL: the last
+// basis value is the last free coordinate (its change is the exact child shift).
 // ---------------------------------------------------------------------------
-enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3 };
+enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3, FAM_POSE6DOF = 4, FAM_RAYS3D = 5 };
 
 template <int FAM> struct Fam;
 
@@ -151,8 +155,9 @@ template <int FAM> struct Fam;
 // child shift is the shift itself).
 template <> struct Fam<FAM_LINE2D> {
     static constexpr int D = 2, K = 1, ND = 1, LE = 1, NP = 2, NB = 1, NFP = 2;
-    static constexpr bool LINEAR_BASIS = true;
-    __device__ static void basis(const double *c, double *psi) { psi[0] = c[0]; }
+    static constexpr bool LINEAR_BASIS = true, LINEAR_TAIL = false;
+    __host__ __device__ static constexpr bool uses(int, int) { return true; }
+    __device__ static void basis(const Problem &, const double *c, double *psi) { psi[0] = c[0]; }
     __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
                                 double *f, double *t) {
         double x = prm[i], y = prm[n + i];
@@ -179,8 +184,9 @@ template <> struct Fam<FAM_LINE2D> {
 // PLANE3D_SPH: coords (theta, phi, d); d = q . n(theta, phi).  t = q; psi = n.
 template <> struct Fam<FAM_PLANE3D_SPH> {
     static constexpr int D = 3, K = 2, ND = 1, LE = 3, NP = 3, NB = 3, NFP = 4;
-    static constexpr bool LINEAR_BASIS = false;
-    __device__ static void basis(const double *c, double *psi) {
+    static constexpr bool LINEAR_BASIS = false, LINEAR_TAIL = false;
+    __host__ __device__ static constexpr bool uses(int, int) { return true; }
+    __device__ static void basis(const Problem &, const double *c, double *psi) {
         double st, ct, sp, cp;
         vsincos(c[0], &st, &ct);
         vsincos(c[1], &sp, &cp);
@@ -221,8 +227,9 @@ template <> struct Fam<FAM_PLANE3D_SPH> {
 // y = w2 - (a sin yaw + b cos yaw).  t = (a, b); psi = (cos yaw, sin yaw).
 template <> struct Fam<FAM_POSE3DOF> {
     static constexpr int D = 3, K = 1, ND = 2, LE = 2, NP = 4, NB = 2, NFP = 4;
-    static constexpr bool LINEAR_BASIS = false;
-    __device__ static void basis(const double *c, double *psi) {
+    static constexpr bool LINEAR_BASIS = false, LINEAR_TAIL = false;
+    __host__ __device__ static constexpr bool uses(int, int) { return true; }
+    __device__ static void basis(const Problem &, const double *c, double *psi) {
         double s, co;
         vsincos(c[0], &s, &co);
         psi[0] = co;
@@ -262,12 +269,158 @@ template <> struct Fam<FAM_POSE3DOF> {
     }
 };
 
+// RAYS3D: rays in 3-space (Sec. 4.3); coords (x, y, z); y = a x + b, z = c x + d.
+// t = (a, c); psi = x (linear: its change across a child shift is the shift itself).
+template <> struct Fam<FAM_RAYS3D> {
+    static constexpr int D = 3, K = 1, ND = 2, LE = 2, NP = 4, NB = 1, NFP = 4;
+    static constexpr bool LINEAR_BASIS = true, LINEAR_TAIL = false;
+    __host__ __device__ static constexpr bool uses(int j, int m) { return j == m; }
+    __device__ static void basis(const Problem &, const double *c, double *psi) { psi[0] = c[0]; }
+    __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
+                                double *f, double *t) {
+        const double a = prm[i], b = prm[n + i], cc = prm[2 * n + i], dd = prm[3 * n + i];
+        t[0] = a;
+        t[1] = cc;
+        f[0] = dsub(dadd(dmul(a, psi[0]), b), c[1]);
+        f[1] = dsub(dadd(dmul(cc, psi[0]), dd), c[2]);
+    }
+    __device__ static void residual64(const double *f, const double *t, const double *dpsi, const double *sh,
+                                      double *fo) {
+        fo[0] = dsub(dadd(f[0], dmul(t[0], dpsi[0])), sh[1]);
+        fo[1] = dsub(dadd(f[1], dmul(t[1], dpsi[0])), sh[2]);
+    }
+    __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
+        p[0] = dadd(f[0], dmul(t[0], dpsi[0]));
+        p[1] = dadd(f[1], dmul(t[1], dpsi[0]));
+    }
+    __device__ static void lipschitz64(const double *t, double *lam) {
+        lam[0] = fabs(t[0]);
+        lam[1] = fabs(t[1]);
+    }
+    __device__ static void coef(const double *dpsi, double *g) {
+        g[0] = dpsi[0]; g[1] = 0.0;
+        g[2] = 0.0; g[3] = dpsi[0];
+    }
+    // |a| h1_x = lam_c[0] |q_a|, |c| h1_x = lam_c[1] |q_c|
+    __device__ static void radius32(const Level &lev, const float *qt, float *R) {
+        R[0] = __fmaf_rn(lev.lam_c[0], fabsf(qt[0]), lev.rc0[0]);
+        R[1] = __fmaf_rn(lev.lam_c[1], fabsf(qt[1]), lev.rc0[1]);
+    }
+};
+
+// POSE6DOF: calibrated camera (Sec. 4.2.3: the 7DoF surfaces of Sec. 4.2.2 with
+// f = 1); coords (phi1, phi2, phi3, z, x, y), X = R(phi) w + (x, y, z).  A match
+// (w, xi, eta) gives x = xi (r3 . w + z) - r1 . w and y = eta (r3 . w + z) - r2 . w,
+// affine in the basis psi = (rows of R(phi), z) with coefficients
+// t = (w, xi w, eta w, xi, eta).  R by Rodrigues' formula with its three scalar
+// functions as power series in theta^2 (no division by theta, no sin/cos).
+template <> struct Fam<FAM_POSE6DOF> {
+    static constexpr int D = 6, K = 4, ND = 2, LE = 11, NP = 5, NB = 10, NFP = 16;
+    static constexpr bool LINEAR_BASIS = false, LINEAR_TAIL = true;
+    // x uses w (with r1), xi w (r3), xi (z); y uses w (r2), eta w (r3), eta (z)
+    __host__ __device__ static constexpr bool uses(int j, int m) {
+        return m < 3 || (j == 0 ? ((m >= 3 && m < 6) || m == 9) : ((m >= 6 && m < 9) || m == 10));
+    }
+    __device__ static void rotation(const Problem &P, const double *ph, double *R) {
+        const double s = dadd(dadd(dmul(ph[0], ph[0]), dmul(ph[1], ph[1])), dmul(ph[2], ph[2]));
+        double C = 0.0, A = 0.0, B = 0.0;
+#pragma unroll
+        for (int n = 14; n >= 0; --n) {
+            const double sg = (n & 1) ? -1.0 : 1.0;
+            C = dadd(dmul(C, s), sg * P.inv_fact[2 * n]);
+            A = dadd(dmul(A, s), sg * P.inv_fact[2 * n + 1]);
+            B = dadd(dmul(B, s), sg * P.inv_fact[2 * n + 2]);
+        }
+        const double a0 = dmul(A, ph[0]), a1 = dmul(A, ph[1]), a2 = dmul(A, ph[2]);
+        const double b0 = dmul(B, ph[0]), b1 = dmul(B, ph[1]), b2 = dmul(B, ph[2]);
+        R[0] = dadd(C, dmul(b0, ph[0])); R[1] = dsub(dmul(b0, ph[1]), a2); R[2] = dadd(dmul(b0, ph[2]), a1);
+        R[3] = dadd(dmul(b1, ph[0]), a2); R[4] = dadd(C, dmul(b1, ph[1])); R[5] = dsub(dmul(b1, ph[2]), a0);
+        R[6] = dsub(dmul(b2, ph[0]), a1); R[7] = dadd(dmul(b2, ph[1]), a0); R[8] = dadd(C, dmul(b2, ph[2]));
+    }
+    __device__ static void basis(const Problem &P, const double *c, double *psi) {
+        rotation(P, c, psi);
+        psi[9] = c[3];
+    }
+    // the t-dependent parts of x and y for basis values (or their changes) p
+    __device__ static void tpart(const double *t, const double *p, double *gx, double *gy) {
+        const double sx3 = dadd(dadd(dmul(t[3], p[6]), dmul(t[4], p[7])), dmul(t[5], p[8]));
+        const double sx1 = dadd(dadd(dmul(t[0], p[0]), dmul(t[1], p[1])), dmul(t[2], p[2]));
+        const double sy3 = dadd(dadd(dmul(t[6], p[6]), dmul(t[7], p[7])), dmul(t[8], p[8]));
+        const double sy2 = dadd(dadd(dmul(t[0], p[3]), dmul(t[1], p[4])), dmul(t[2], p[5]));
+        *gx = dsub(dadd(sx3, dmul(t[9], p[9])), sx1);
+        *gy = dsub(dadd(sy3, dmul(t[10], p[9])), sy2);
+    }
+    __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
+                                double *f, double *t) {
+        const double xi = prm[3 * n + i], eta = prm[4 * n + i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double w = prm[j * n + i];
+            t[j] = w;
+            t[3 + j] = dmul(xi, w);
+            t[6 + j] = dmul(eta, w);
+        }
+        t[9] = xi;
+        t[10] = eta;
+        double gx, gy;
+        tpart(t, psi, &gx, &gy);
+        f[0] = dsub(gx, c[4]);
+        f[1] = dsub(gy, c[5]);
+    }
+    __device__ static void residual64(const double *f, const double *t, const double *dpsi, const double *sh,
+                                      double *fo) {
+        double gx, gy;
+        tpart(t, dpsi, &gx, &gy);
+        fo[0] = dsub(dadd(f[0], gx), sh[4]);
+        fo[1] = dsub(dadd(f[1], gy), sh[5]);
+    }
+    __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
+        double gx, gy;
+        tpart(t, dpsi, &gx, &gy);
+        p[0] = dadd(f[0], gx);
+        p[1] = dadd(f[1], gy);
+    }
+    // |dx/dphi_a| <= |xi w| + |w|, |dx/dz| = |xi| (and y with eta), lam[j * K + a]
+    __device__ static void lipschitz64(const double *t, double *lam) {
+        const double nw = dsqrt(dadd(dadd(dmul(t[0], t[0]), dmul(t[1], t[1])), dmul(t[2], t[2])));
+        const double nxw = dsqrt(dadd(dadd(dmul(t[3], t[3]), dmul(t[4], t[4])), dmul(t[5], t[5])));
+        const double nyw = dsqrt(dadd(dadd(dmul(t[6], t[6]), dmul(t[7], t[7])), dmul(t[8], t[8])));
+        const double lx = dadd(nxw, nw), ly = dadd(nyw, nw);
+        lam[0] = lx; lam[1] = lx; lam[2] = lx; lam[3] = fabs(t[9]);
+        lam[4] = ly; lam[5] = ly; lam[6] = ly; lam[7] = fabs(t[10]);
+    }
+    // g[j * LE + m]: coefficient of t_m in residual j for basis changes dpsi
+    __device__ static void coef(const double *dpsi, double *g) {
+#pragma unroll
+        for (int x = 0; x < ND * LE; ++x) g[x] = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            g[i] = -dpsi[i];                 // x: -r1 . w
+            g[3 + i] = dpsi[6 + i];          // x: xi w . r3
+            g[LE + i] = -dpsi[3 + i];        // y: -r2 . w
+            g[LE + 6 + i] = dpsi[6 + i];     // y: eta w . r3
+        }
+        g[9] = dpsi[9];                      // x: xi z
+        g[LE + 10] = dpsi[9];                // y: eta z
+    }
+    // s_t equal for the nine rotation coefficients and for xi, eta:
+    // |w| + |xi w| = s_t (|q_w| + |q_xiw|); lam_c: [x rotation, x z, y rotation, y z]
+    __device__ static void radius32(const Level &lev, const float *qt, float *R) {
+        const float nw = sqrtf(__fmaf_rn(qt[2], qt[2], __fmaf_rn(qt[1], qt[1], qt[0] * qt[0])));
+        const float nxw = sqrtf(__fmaf_rn(qt[5], qt[5], __fmaf_rn(qt[4], qt[4], qt[3] * qt[3])));
+        const float nyw = sqrtf(__fmaf_rn(qt[8], qt[8], __fmaf_rn(qt[7], qt[7], qt[6] * qt[6])));
+        R[0] = __fmaf_rn(lev.lam_c[0], nxw + nw, __fmaf_rn(lev.lam_c[1], fabsf(qt[9]), lev.rc0[0]));
+        R[1] = __fmaf_rn(lev.lam_c[2], nyw + nw, __fmaf_rn(lev.lam_c[3], fabsf(qt[10]), lev.rc0[1]));
+    }
+};
+
 // Width of the FP32 screen's band, from the magnitudes of one record (in steps):
-// M_j = |q_f,j| + sum_m |q_t,m| Gmax_jm + |H_j|.  The FP32 residual y takes LE fused
-// multiply-adds, one add and coefficients rounded once from FP64, so
-// |y - y_exact| <= 6 u M_j (u = 2^-24; the FP64 definition's own error is below
-// 2^-48 M_j); the FP32 radius (two approximate square roots of at most 4 ulp, two
-// multiply-adds, constants rounded once) is within 13 u R of the exact radius.
+// M_j = |q_f,j| + sum_m |q_t,m| Gmax_jm + |H_j|.  The FP32 residual y takes one fused
+// multiply-add per essential parameter that enters it (at most 7), one add and
+// coefficients rounded once from FP64, so |y - y_exact| <= 10 u M_j (u = 2^-24; the
+// FP64 definition's own error is below 2^-48 M_j); the FP32 radius (at most three
+// approximate square roots of at most 4 ulp, a few multiply-adds, constants rounded
+// once) is within 13 u R of the exact radius.
 // A comparison of |y| with R (or with the lower-bound radius) is decided in FP32
 // only when it clears kBandTest (M_j + R); a snap only when y is kBandSnap M_j away
 // from a rounding tie: both about twice the bound.

@@ -83,14 +83,14 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_EMIT) k_emit(const __grid_co
 #pragma unroll
     for (int i = 0; i < GF; ++i) G[i] = 0.0f;
     unsigned nrechk = 0, bad = 0;
-    bool failed = false;
+    int64_t gfail = -1;                                             // group whose copy did not arrive
 #pragma unroll 1
     for (int64_t g = g0; g < g1; ++g) {
         const int b = (int)((g - g0) & 1);
         if (threadIdx.x == 0 && g + 1 < g1) issue(g + 1);
-        const bool ok = mbar_wait(&s_bar[b], (unsigned)(((g - g0) >> 1) & 1), GV_SPIN_LIMIT, &c.sc->err);
+        const bool ok = mbar_wait(&s_bar[b], (unsigned)(((g - g0) >> 1) & 1), c.spin, &c.sc->err);
         if (__syncthreads_or(!ok)) {
-            failed = true;
+            gfail = g;
             break;
         }
 #pragma unroll 1
@@ -198,8 +198,12 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_EMIT) k_emit(const __grid_co
         }
         __syncthreads();                                                // buffer b is free again
     }
-    if (failed && threadIdx.x == 0) {
-        for (int64_t g = g0; g < g1; ++g) {
+    if (gfail >= 0 && threadIdx.x == 0) {
+        // the copies of groups gfail and gfail + 1 (no later one was issued) may still
+        // be in flight: wait for them, bounded, before the block's shared memory is
+        // released
+        const int64_t ge = gfail + 2 < g1 ? gfail + 2 : g1;
+        for (int64_t g = gfail; g < ge; ++g) {
             const int b = (int)((g - g0) & 1);
             if (!mbar_wait(&s_bar[b], (unsigned)(((g - g0) >> 1) & 1), GV_SPIN_LIMIT, &c.sc->err)) break;
         }
@@ -217,6 +221,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_EMIT) k_emit(const __grid_co
     case FAM_LINE2D: { constexpr int FAMV = FAM_LINE2D; CALL; } break;           \
     case FAM_PLANE3D_SPH: { constexpr int FAMV = FAM_PLANE3D_SPH; CALL; } break; \
     case FAM_POSE3DOF: { constexpr int FAMV = FAM_POSE3DOF; CALL; } break;       \
+    case FAM_RAYS3D: { constexpr int FAMV = FAM_RAYS3D; CALL; } break;           \
     default: break;                                                              \
     }
 
@@ -224,6 +229,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_EMIT) k_emit(const __grid_co
 bool launch_emit(const Chunk &c, cudaStream_t st) {
     const int64_t nt = c.t1 - c.t0;
     if (nt <= 0) return true;
+    if (c.P.d > 3) return launch_emit_wide(c, st);
     const int64_t ng = (nt + kBlockTiles - 1) / kBlockTiles;
     const int q = c.lev.q16, qn = c.lev.q16_next;
 #define GV_EMIT(QI, QO, PREC)                                                                                 \

@@ -77,7 +77,9 @@ struct vote_ctx {
     int64_t chunk_records = 1 << 25;
     uint32_t initial_lb = 0;
     int kernel_timing = 0;
-    int log = 0;               // VOTE_LOG=1: per-level counters on stderr after each solve
+    int log = 0;               // VOTE_LOG=1: per-level counters on stderr after each solve;
+                               // 2: also one line per expansion step
+    unsigned spin_limit = GV_SPIN_LIMIT;   // VOTE_OPT_SPIN_LIMIT
     int batch_workers = 4;
     int dive = 2;              // greedy dive: 0 off, 1 on, 2 on for n >= kDiveMinN
     int family = 0;
@@ -91,6 +93,7 @@ struct vote_ctx {
     int64_t klaunch[VOTE_K_CLASSES] = {};
     double kbytes[VOTE_K_CLASSES] = {};
     int64_t lv_cells[GV_MAXL] = {}, lv_recs[GV_MAXL] = {};
+    int64_t lv_gin[GV_MAXL] = {}, lv_gout[GV_MAXL] = {};  // records into / out of grouping
     int64_t trace_cap = 0;
     int64_t fault_alloc_at = 0, alloc_count = 0;
     LevelStore ls[GV_MAXL + 1];
@@ -98,7 +101,6 @@ struct vote_ctx {
     DevBuf tr_level, tr_key, tr_ub, tr_lb, surf_tmp, mask_tmp;
     DevBuf ss_partial, ss_io;  // soft score: block partials; point [d] + outputs [d] + grad_out [1]
     DevBuf g_table, g_owner, g_newpos, g_ccount, g_ccur, g_rbeg, g_rec, g_mult, g_tile;
-    int64_t grouped_away = 0;  // records merged away by grouping in the last solve
     Scalars *h_sc = nullptr;   // pinned mirror of the device scalars
     uint64_t *h_tmp = nullptr; // pinned slot for single values
     // device slot for single values: 64 bytes after the scalars block
@@ -118,6 +120,8 @@ static int family_shape(int fam, int d, int k, int *le, int *np) {
     case VOTE_LINE2D: if (d != 2 || k != 1) return 1; *le = 1; *np = 2; return 0;
     case VOTE_PLANE3D_SPH: if (d != 3 || k != 2) return 1; *le = 3; *np = 3; return 0;
     case VOTE_POSE3DOF: if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
+    case VOTE_POSE6DOF: if (d != 6 || k != 4) return 1; *le = 11; *np = 5; return 0;
+    case VOTE_RAYS3D: if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
     default: return 1;
     }
 }
@@ -135,6 +139,19 @@ static void family_sigma(int fam, const double *h, double *sigma) {
         sigma[0] = h[0];
         sigma[1] = h[0];
         break;
+    case VOTE_RAYS3D:       // a and c multiply x
+        sigma[0] = h[0];
+        sigma[1] = h[0];
+        break;
+    case VOTE_POSE6DOF: {
+        // an entry of the rotation moves by at most |d phi|_2 <= sum of the phi
+        // half-widths (its gradient has norm <= 1); z is linear
+        const double hr = (h[0] + h[1]) + h[2];
+        for (int m = 0; m < 9; ++m) sigma[m] = hr;
+        sigma[9] = h[3];
+        sigma[10] = h[3];
+        break;
+    }
     }
 }
 
@@ -154,6 +171,8 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
     Problem &P = c->P;
     std::memset(&P, 0, sizeof(P));
     P.fam = fam; P.d = d; P.k = k; P.nd = d - k; P.le = le; P.np = np;
+    P.inv_fact[0] = 1.0;
+    for (int m = 1; m < 31; ++m) P.inv_fact[m] = P.inv_fact[m - 1] / (double)m;
     P.L = 0;
     for (int j = 0; j < d; ++j) {
         double lo = bounds[2 * j], hi = bounds[2 * j + 1];
@@ -183,8 +202,8 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
         bits += P.Lj[j];
     }
     P.coord_bits = bits;
-    if (bits > 40) {
-        set_err("leaf key needs %d bits (> 40)", bits);
+    if (bits > 44) {       // the best leaf packs (UB << bits) | leaf key into 64 bits
+        set_err("leaf key needs %d bits (> 44)", bits);
         return VOTE_EUNSUPPORTED;
     }
     double h[GV_MAXL + 1][GV_MAXD];
@@ -262,8 +281,24 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
         case VOTE_POSE3DOF:      // sqrt(a^2 + b^2) h1_yaw; s_t,a = s_t,b
             for (int j = 0; j < P.nd; ++j) v.lam_c[j] = (float)(h[l + 1][0] * s_t[l][0] / P.s_f[j]);
             break;
+        case VOTE_RAYS3D:        // |a| h1_x and |c| h1_x
+            v.lam_c[0] = (float)(h[l + 1][0] * s_t[l][0] / P.s_f[0]);
+            v.lam_c[1] = (float)(h[l + 1][0] * s_t[l][1] / P.s_f[1]);
+            break;
+        case VOTE_POSE6DOF: {    // (|xi w| + |w|) sum h1_phi + |xi| h1_z (and y with eta)
+            const double hphi = (h[l + 1][0] + h[l + 1][1]) + h[l + 1][2];
+            v.lam_c[0] = (float)(hphi * s_t[l][0] / P.s_f[0]);
+            v.lam_c[1] = (float)(h[l + 1][3] * s_t[l][9] / P.s_f[0]);
+            v.lam_c[2] = (float)(hphi * s_t[l][0] / P.s_f[1]);
+            v.lam_c[3] = (float)(h[l + 1][3] * s_t[l][10] / P.s_f[1]);
+            break;
         }
-        if ((fam == VOTE_PLANE3D_SPH && s_t[l][0] != s_t[l][1]) || (fam == VOTE_POSE3DOF && s_t[l][0] != s_t[l][1])) {
+        }
+        bool equal = true;
+        if (fam == VOTE_PLANE3D_SPH || fam == VOTE_POSE3DOF) equal = s_t[l][0] == s_t[l][1];
+        if (fam == VOTE_POSE6DOF)
+            for (int m = 1; m < 9; ++m) equal &= s_t[l][m] == s_t[l][0];
+        if (!equal) {
             set_err("internal: unequal essential steps at level %d", l);
             return VOTE_EINTERNAL;
         }
@@ -280,6 +315,17 @@ static void lambda_max(int fam, const double *T, double *lam) {
         lam[1] = std::sqrt(T[0] * T[0] + T[1] * T[1]);
         break;
     case VOTE_POSE3DOF: lam[0] = lam[1] = std::sqrt(T[0] * T[0] + T[1] * T[1]); break;
+    case VOTE_RAYS3D: lam[0] = T[0]; lam[1] = T[1]; break;
+    case VOTE_POSE6DOF: {
+        const double nw = std::sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+        const double nxw = std::sqrt(T[3] * T[3] + T[4] * T[4] + T[5] * T[5]);
+        const double nyw = std::sqrt(T[6] * T[6] + T[7] * T[7] + T[8] * T[8]);
+        lam[0] = lam[1] = lam[2] = nxw + nw;
+        lam[3] = T[9];
+        lam[4] = lam[5] = lam[6] = nyw + nw;
+        lam[7] = T[10];
+        break;
+    }
     }
 }
 
@@ -353,7 +399,29 @@ static void release(vote_ctx *c, DevBuf &b) {
     b.bytes = 0;
 }
 
-static int family_nfp(int fam) { return fam == VOTE_LINE2D ? 2 : 4; }
+// record fields and basis values of a family, from its device definition
+static int family_nfp(int fam) {
+    switch (fam) {
+    case VOTE_LINE2D: return Fam<FAM_LINE2D>::NFP;
+    case VOTE_PLANE3D_SPH: return Fam<FAM_PLANE3D_SPH>::NFP;
+    case VOTE_POSE3DOF: return Fam<FAM_POSE3DOF>::NFP;
+    case VOTE_RAYS3D: return Fam<FAM_RAYS3D>::NFP;
+    default: return Fam<FAM_POSE6DOF>::NFP;
+    }
+}
+static int family_nb(int fam) {
+    switch (fam) {
+    case VOTE_LINE2D: return Fam<FAM_LINE2D>::NB;
+    case VOTE_PLANE3D_SPH: return Fam<FAM_PLANE3D_SPH>::NB;
+    case VOTE_POSE3DOF: return Fam<FAM_POSE3DOF>::NB;
+    case VOTE_RAYS3D: return Fam<FAM_RAYS3D>::NB;
+    default: return Fam<FAM_POSE6DOF>::NB;
+    }
+}
+static_assert((int)VOTE_LINE2D == FAM_LINE2D && (int)VOTE_PLANE3D_SPH == FAM_PLANE3D_SPH &&
+                  (int)VOTE_POSE3DOF == FAM_POSE3DOF && (int)VOTE_POSE6DOF == FAM_POSE6DOF &&
+                  (int)VOTE_RAYS3D == FAM_RAYS3D,
+              "family numbers");
 
 // bytes of one record of level l (its format is fixed per solve by finalize_levels)
 static int rec_bytes_at(const vote_ctx *c, int l) {
@@ -472,7 +540,7 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     nvtxRangePushA("expand_chunk");
     const int nc = (int)(c1 - c0);
     const int nfs = 1 << P.k;
-    const int NB = P.fam == VOTE_LINE2D ? 1 : (P.fam == VOTE_PLANE3D_SPH ? 3 : 2);
+    const int NB = family_nb(P.fam);
     const int gf = geo32_floats(nfs, P.nd, P.le);
     const size_t nch = (size_t)nc * ns;
     TRY(ensure(c, c->alive, nc));
@@ -518,6 +586,7 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     }
     ch.prune = c->prune;
     ch.precision = c->precision;
+    ch.spin = c->spin_limit;
 
     const int rb = rec_bytes_at(c, l);
     if (c->group && r1 - r0 > 32) {
@@ -549,12 +618,13 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
                      (uint64_t *)c->g_rbeg.p, (unsigned long long *)c->h_tmp_dev(), gv, c->stream);
         ev_mark(c, VOTE_K_GROUP);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(c->h_tmp, c->h_tmp_dev(), 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(c->h_tmp, c->h_tmp_dev(), 24, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
-        const int64_t gs = (int64_t)*c->h_tmp;
+        const int64_t gs = (int64_t)c->h_tmp[0];
         c->stats.launches += 4;
         c->kbytes[VOTE_K_GROUP] += (double)nr * (rb + 4) * 2;
-        c->grouped_away += (int64_t)nr - gs;
+        c->lv_gout[l] += (int64_t)c->h_tmp[1];
+        c->lv_gin[l] += (int64_t)c->h_tmp[2];
         ch.in = gv;
         ch.in_rbeg = (const uint64_t *)c->g_rbeg.p;
         ch.in_rcnt = (const uint32_t *)c->g_ccount.p;
@@ -597,6 +667,10 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
         S.nrecs = r0;
     }
     if (lev.leaf_children) {
+        if (c->log >= 2)
+            std::fprintf(stderr, "[vote] step %lld level %d: %lld cells, %lld tiles, count %.0f B, leaves\n",
+                         (long long)c->stats.chunks - 1, l, (long long)nc, (long long)nt,
+                         (double)nt * 32 * rb + (double)nt * ns * 4);
         c->stats.leaves += (int64_t)nc * nvalid;
         nvtxRangePop();
         return VOTE_OK;
@@ -623,6 +697,13 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
                                        (double)new_slots * rec_bytes_at(c, l + 1);
     }
     CK(cudaGetLastError());
+    if (c->log >= 2)
+        std::fprintf(stderr, "[vote] step %lld level %d: %lld cells, %lld tiles, count %.0f B, emit %.0f B, "
+                     "%lld child cells\n", (long long)c->stats.chunks - 1, l, (long long)nc, (long long)nt,
+                     (double)nt * 32 * rb + (double)nt * ns * 4,
+                     new_slots > 0 ? (double)nt * 32 * rb + (double)nt * ns * 4 +
+                                         (double)new_slots * rec_bytes_at(c, l + 1) : 0.0,
+                     (long long)new_cells);
     c->ls[l + 1].ncells = new_cells;
     c->ls[l + 1].nrecs = new_slots;
     if (new_slots > c->stats.peak_records) c->stats.peak_records = new_slots;
@@ -662,9 +743,14 @@ static void log_solve(const vote_ctx *c, vote_status st) {
                  "%lld launches, peak %lld record slots\n", c->P.fam, c->P.L, (int)st, x.seconds,
                  (long long)x.tests, (long long)x.rechecks, (long long)x.chunks, (long long)x.launches,
                  (long long)x.peak_records);
-    for (int l = 0; l < c->P.L; ++l)
-        std::fprintf(stderr, "[vote]   level %2d: %lld cells expanded, %lld record slots tested, records %s\n", l,
+    for (int l = 0; l < c->P.L; ++l) {
+        std::fprintf(stderr, "[vote]   level %2d: %lld cells expanded, %lld record slots tested, records %s", l,
                      (long long)c->lv_cells[l], (long long)c->lv_recs[l], c->lev[l].q16 ? "16-bit" : "32-bit");
+        if (c->lv_gin[l])
+            std::fprintf(stderr, ", grouping %lld -> %lld records (%.4f merged)", (long long)c->lv_gin[l],
+                         (long long)c->lv_gout[l], 1.0 - (double)c->lv_gout[l] / (double)c->lv_gin[l]);
+        std::fprintf(stderr, "\n");
+    }
 }
 
 static vote_status solve_device(vote_ctx *c, const double *surfaces, int64_t n, double *best_point,
@@ -681,8 +767,7 @@ static vote_status solve_inner(vote_ctx *c, const double *surfaces, int64_t n, d
     auto t0 = std::chrono::steady_clock::now();
     const Problem &P = c->P;
     std::memset(&c->stats, 0, sizeof(c->stats));
-    for (int l = 0; l < GV_MAXL; ++l) c->lv_cells[l] = c->lv_recs[l] = 0;
-    c->grouped_away = 0;
+    for (int l = 0; l < GV_MAXL; ++l) c->lv_cells[l] = c->lv_recs[l] = c->lv_gin[l] = c->lv_gout[l] = 0;
     c->stats.levels = P.L;
     if (n < 0 || !best_point || !depth || (n > 0 && !surfaces)) {
         set_err("invalid arguments");
@@ -833,7 +918,7 @@ vote_status vote_create(int family, int d, int k, const double *eps, const doubl
     // 3DoF prunes well and needs fine depth-first steps
     c->chunk_records = family == VOTE_PLANE3D_SPH ? (int64_t)1 << 27 : (int64_t)1 << 25;
     c->family = family;
-    if (const char *lg = std::getenv("VOTE_LOG")) c->log = std::atoi(lg) > 0;
+    if (const char *lg = std::getenv("VOTE_LOG")) c->log = std::atoi(lg) > 0 ? std::atoi(lg) : 0;
     for (int j = 0; j < d; ++j) {
         c->eps_in[j] = eps[j];
         c->bounds_in[2 * j] = bounds[2 * j];
@@ -920,6 +1005,10 @@ vote_status vote_set_option(vote_ctx *c, int key, double v) {
         if (v != 0 && v != 1 && v != 2) break;
         c->dive = (int)v;
         return VOTE_OK;
+    case VOTE_OPT_SPIN_LIMIT:
+        if (!(v >= 0 && v <= 4294967295.0)) break;
+        c->spin_limit = (unsigned)v;
+        return VOTE_OK;
 
     default:
         set_err("unknown option %d", key);
@@ -987,6 +1076,7 @@ vote_status vote_solve_batched(vote_ctx *c, const double *surfaces, const int64_
         w->chunk_records = c->chunk_records;
         w->dive = c->dive;
         w->group = c->group;
+        w->spin_limit = c->spin_limit;
         w->fault_alloc_at = 0;
     }
     std::vector<int64_t> wordoff(B + 1, 0);
@@ -1075,6 +1165,10 @@ vote_status vote_cell_counts(vote_ctx *c, const double *surfaces, int64_t n, int
 
 static vote_status ss_prepare(vote_ctx *c, const double *tol, double *inv_tol2) {
     const Problem &P = c->P;
+    if (!softscore_supported(P.fam)) {
+        set_err("the soft score is not available for family %d", P.fam);
+        return VOTE_EUNSUPPORTED;
+    }
     for (int j = 0; j < P.nd; ++j) {
         double t = tol ? tol[j] : P.eps[P.k + j];
         if (!(t > 0.0) || !std::isfinite(t)) { set_err("tol must be finite and > 0"); return VOTE_EINVAL; }
@@ -1231,11 +1325,14 @@ vote_status vote_get_kernel_times(vote_ctx *c, double *ms, int64_t *launches, do
     return VOTE_OK;
 }
 
-vote_status vote_get_level_stats(vote_ctx *c, int64_t *cells, int64_t *records) {
+vote_status vote_get_level_stats(vote_ctx *c, int64_t *cells, int64_t *records, int64_t *grouped_in,
+                                 int64_t *grouped_out) {
     if (!c) { set_err("null context"); return VOTE_EINVAL; }
     for (int l = 0; l < c->P.L; ++l) {
         if (cells) cells[l] = c->lv_cells[l];
         if (records) records[l] = c->lv_recs[l];
+        if (grouped_in) grouped_in[l] = c->lv_gin[l];
+        if (grouped_out) grouped_out[l] = c->lv_gout[l];
     }
     return VOTE_OK;
 }

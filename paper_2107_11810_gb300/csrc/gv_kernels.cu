@@ -46,7 +46,7 @@ __global__ void k_lift(Problem P, Level lev0, const double *__restrict__ prm, in
         double c[F::D], psi[F::NB], f[F::ND], t[F::LE];
 #pragma unroll
         for (int j = 0; j < F::D; ++j) c[j] = cell_center(P, lev0.h, j, 0);
-        F::basis(c, psi);
+        F::basis(P, c, psi);
         F::lift(prm, n, i, c, psi, f, t);
         uint32_t w[NW];
 #pragma unroll
@@ -102,9 +102,15 @@ __device__ __forceinline__ void child_dpsi(const Problem &P, const Level &lev, u
         cch[j] = cell_center(P, lev.h1, j, ic);
     }
     double psi_ch[F::NB];
-    F::basis(cch, psi_ch);
+    F::basis(P, cch, psi_ch);
 #pragma unroll
     for (int m = 0; m < F::NB; ++m) dpsi[m] = dsub(psi_ch[m], psi_par[m]);
+    if constexpr (F::LINEAR_TAIL) {
+        // the last basis value is the last free coordinate: its change is the exact shift
+        constexpr int j = F::K - 1;
+        const bool split = (lev.split_mask >> j) & 1;
+        dpsi[F::NB - 1] = split ? (((fs >> j) & 1) ? lev.h1[j] : -lev.h1[j]) : 0.0;
+    }
     }
 }
 
@@ -114,7 +120,7 @@ __device__ __forceinline__ void parent_psi(const Problem &P, const Level &lev, u
     double cpar[F::D];
 #pragma unroll
     for (int j = 0; j < F::K; ++j) cpar[j] = cell_center(P, lev.h, j, cell_coord(P, key, lev.l, j));
-    if (!F::LINEAR_BASIS) F::basis(cpar, psi);
+    if (!F::LINEAR_BASIS) F::basis(P, cpar, psi);
 }
 
 // One thread per (cell, free-coordinate child slot fs); the 2^k threads of a cell
@@ -337,46 +343,47 @@ __global__ void k_next_tiles(CellView next, RecView out, int64_t ncells) {
 }
 
 // Output positions of the emit pass.  A block takes 32 consecutive tiles;
-// warp s handles child slot s with one lane per tile: a segmented scan over the
+// warp w handles child slots w, w + 8, ... with one lane per tile: a segmented scan over the
 // tiles (segments = runs of one cell) gives every tile its offset inside the run,
 // the run's last lane reserves the run's records in the child with one atomic on
 // the child's cursor, and the run's base is broadcast back.  tdst[tile][s] = first
 // slot of the tile's records in child s, or ~0 when the tile writes none there.
 template <int NS>
 __global__ void __launch_bounds__(256) k_tile_dst(Chunk c) {
-    const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
-    if (s >= NS) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int NWARP = NS < 8 ? NS : 8;
+    if (w >= NWARP) return;
     const int64_t t = c.t0 + (int64_t)blockIdx.x * 32 + lane;
     const bool in = t < c.t1;
-    int cl = -1;
-    unsigned n = 0;
-    int ci = -1;
-    if (in) {
-        cl = c.tinfo[t - c.t0].x;
-        if (cl >= 0) {
-            ci = c.child_idx[(size_t)cl * NS + s];
-            if (ci >= 0) n = __popc(c.ballot[(size_t)(t - c.t0) * NS + s]);
-        }
-    }
+    const int cl = in ? c.tinfo[t - c.t0].x : -1;
     // segments: maximal runs of lanes with the same cell
     const int prev = __shfl_up_sync(kFull, cl, 1);
     const unsigned heads = __ballot_sync(kFull, lane == 0 || prev != cl);
     const int next = __shfl_down_sync(kFull, cl, 1);
     const unsigned tails = __ballot_sync(kFull, lane == 31 || next != cl);
     const int head = 31 - __clz(heads & ((2u << lane) - 1u));          // this lane's segment head
-    // inclusive scan of n inside the segment
-    unsigned x = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(kFull, x, o);
-        if (lane - o >= head) x += y;
-    }
-    unsigned long long base = 0;
-    if (((tails >> lane) & 1) && cl >= 0 && ci >= 0 && x)
-        base = c.next_cells.rbeg[ci] + atomicAdd(&c.cursor[(size_t)cl * NS + s], x);
     const int tail = __ffs(tails & ~((1u << lane) - 1u)) - 1;          // this lane's segment tail
-    base = __shfl_sync(kFull, base, tail);
-    if (in) c.tdst[(size_t)(t - c.t0) * NS + s] = n ? base + (x - n) : ~0ull;
+#pragma unroll 1
+    for (int s = w; s < NS; s += NWARP) {
+        unsigned n = 0;
+        int ci = -1;
+        if (cl >= 0) {
+            ci = c.child_idx[(size_t)cl * NS + s];
+            if (ci >= 0) n = __popc(c.ballot[(size_t)(t - c.t0) * NS + s]);
+        }
+        // inclusive scan of n inside the segment
+        unsigned x = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(kFull, x, o);
+            if (lane - o >= head) x += y;
+        }
+        unsigned long long base = 0;
+        if (((tails >> lane) & 1) && cl >= 0 && ci >= 0 && x)
+            base = c.next_cells.rbeg[ci] + atomicAdd(&c.cursor[(size_t)cl * NS + s], x);
+        base = __shfl_sync(kFull, base, tail);
+        if (in) c.tdst[(size_t)(t - c.t0) * NS + s] = n ? base + (x - n) : ~0ull;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -412,7 +419,7 @@ __global__ void __launch_bounds__(256) k_replay(Problem P, const Level *__restri
         double c[F::D], psi[F::NB], f[F::ND], t[F::LE];
 #pragma unroll
         for (int j = 0; j < F::D; ++j) c[j] = cell_center(P, levs[0].h, j, 0);
-        F::basis(c, psi);
+        F::basis(P, c, psi);
         F::lift(prm, n, i, c, psi, f, t);
         reached = true;
         for (int l = 0; l < lam; ++l) {
@@ -509,18 +516,39 @@ __global__ void k_group_insert(Chunk c, uint32_t *table, uint32_t tmask, uint32_
 }
 
 // exclusive scan of per-cell record counts rounded up to whole tiles (one block of
-// 256 threads): start[i], *total = slots used
-__global__ void __launch_bounds__(256) k_scan_slots(const uint32_t *cnt, uint64_t *start, int64_t n,
-                                                    unsigned long long *total) {
-    unsigned long long carry = 0;
+// 256 threads): start[i]; total[0] = slots used, total[1] = sum of cnt, total[2] =
+// sum of in_cnt (the cells' record counts before grouping)
+__global__ void __launch_bounds__(256) k_scan_slots(const uint32_t *cnt, const uint32_t *in_cnt, uint64_t *start,
+                                                    int64_t n, unsigned long long *total) {
+    unsigned long long carry = 0, recs = 0, recs_in = 0;
     for (int64_t base = 0; base < n; base += 256) {
         int64_t i = base + threadIdx.x;
         unsigned long long v = i < n ? (cnt[i] + 31u) & ~31u : 0u, t;
         unsigned long long e = block_excl_scan(v, &t);
         if (i < n) start[i] = carry + e;
         carry += t;
+        if (i < n) {
+            recs += cnt[i];
+            recs_in += in_cnt[i];
+        }
     }
-    if (threadIdx.x == 0 && total) *total = carry;
+    for (int o = 16; o > 0; o >>= 1) {
+        recs += __shfl_xor_sync(0xffffffffu, recs, o);
+        recs_in += __shfl_xor_sync(0xffffffffu, recs_in, o);
+    }
+    __shared__ unsigned long long s_r[8], s_ri[8];
+    if ((threadIdx.x & 31) == 0) {
+        s_r[threadIdx.x >> 5] = recs;
+        s_ri[threadIdx.x >> 5] = recs_in;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0;
+        for (int w = 0; w < 8; ++w) a += s_r[w], b += s_ri[w];
+        total[0] = carry;
+        total[1] = a;
+        total[2] = b;
+    }
 }
 
 template <int FAM, bool Q16>
@@ -558,6 +586,8 @@ static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs
     case FAM_LINE2D: { constexpr int FAMV = FAM_LINE2D; CALL; } break;           \
     case FAM_PLANE3D_SPH: { constexpr int FAMV = FAM_PLANE3D_SPH; CALL; } break; \
     case FAM_POSE3DOF: { constexpr int FAMV = FAM_POSE3DOF; CALL; } break;       \
+    case FAM_RAYS3D: { constexpr int FAMV = FAM_RAYS3D; CALL; } break;           \
+    case FAM_POSE6DOF: { constexpr int FAMV = FAM_POSE6DOF; CALL; } break;       \
     default: break;                                                 \
     }
 
@@ -618,7 +648,8 @@ void launch_tile_dst(const Chunk &c, cudaStream_t st) {
     if (nt <= 0) return;
     const int ns = 1 << c.P.d;
     if (ns == 4) k_tile_dst<4><<<blocks_for(nt, 32), 32 * 4, 0, st>>>(c);
-    else k_tile_dst<8><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
+    else if (ns == 8) k_tile_dst<8><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
+    else k_tile_dst<64><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
 }
 
 void launch_child_lbmax(const Chunk &c, cudaStream_t st) {
@@ -626,7 +657,8 @@ void launch_child_lbmax(const Chunk &c, cudaStream_t st) {
     int64_t n = (int64_t)c.nc * ns;
     if (n <= 0) return;
     if (ns == 4) k_child_lbmax<4><<<blocks_for(n, 256), 256, 0, st>>>(c);
-    else k_child_lbmax<8><<<blocks_for(n, 256), 256, 0, st>>>(c);
+    else if (ns == 8) k_child_lbmax<8><<<blocks_for(n, 256), 256, 0, st>>>(c);
+    else k_child_lbmax<64><<<blocks_for(n, 256), 256, 0, st>>>(c);
 }
 
 void launch_child_alloc(const Chunk &c, uint32_t *keepflag, uint32_t *recn, unsigned long long *bsums,
@@ -637,11 +669,13 @@ void launch_child_alloc(const Chunk &c, uint32_t *keepflag, uint32_t *recn, unsi
     unsigned nb = blocks_for(n, 256);
     unsigned long long *ba = bsums, *bb = bsums + nb;
     if (ns == 4) k_child_mark<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
-    else k_child_mark<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else if (ns == 8) k_child_mark<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else k_child_mark<64><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     if (c.lev.leaf_children) return;
     k_scan_sums<<<1, 256, 0, st>>>(ba, bb, (int)nb, c.sc);
     if (ns == 4) k_child_write<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
-    else k_child_write<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else if (ns == 8) k_child_write<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else k_child_write<64><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
 }
 
 void launch_group(const Chunk &c, uint32_t *table, uint32_t tmask, uint32_t *owner, uint32_t *ccount,
@@ -655,7 +689,7 @@ void launch_group(const Chunk &c, uint32_t *table, uint32_t tmask, uint32_t *own
     } else {
         GV_DISPATCH(c.P.fam, (k_group_insert<FAMV, false><<<g, 256, 0, st>>>(c, table, tmask, owner, ccount)));
     }
-    k_scan_slots<<<1, 256, 0, st>>>(ccount, grbeg, c.nc, total);
+    k_scan_slots<<<1, 256, 0, st>>>(ccount, c.in_rcnt + c.in_c0, grbeg, c.nc, total);
     if (c.lev.q16) {
         GV_DISPATCH(c.P.fam, (k_group_place<FAMV, true><<<g, 256, 0, st>>>(c, owner, grbeg, ccur, newpos, out)));
     } else {

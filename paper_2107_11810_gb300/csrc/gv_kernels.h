@@ -80,6 +80,7 @@ struct Chunk {
     Trace trace;
     int prune;
     int precision;           // 0 = FP64, 1 = FP32 screen + FP64 recheck
+    unsigned spin;           // polls of a bounded wait for a bulk copy before giving up
 };
 
 // Size in floats of one cell's screen geometry: G[2^k][ND][LE] and, per (j, m), the
@@ -101,6 +102,9 @@ void launch_persistent(const void *kern, size_t smem, int64_t groups, const Chun
 // per tile of the chunk: tinfo (after k_cell_geo has set alive)
 void launch_tile_info(const Chunk &c, cudaStream_t st);
 void launch_count(const Chunk &c, cudaStream_t st);
+// the count and emit passes of families with 64 child slots (gv_wide.cu)
+void launch_count_wide(const Chunk &c, cudaStream_t st);
+bool launch_emit_wide(const Chunk &c, cudaStream_t st);
 // after the children are laid out: the next level's tile -> cell table for cells
 // [0, ncells) and every tile's output positions (tdst)
 void launch_next_tiles(const Chunk &c, int64_t ncells, cudaStream_t st);
@@ -119,7 +123,8 @@ void launch_replay(const Problem &P, const Level *levs_dev, const PathStep *path
 // Grouping of a chunk's records (c.in, tiles [c.t0, c.t1), cells c.in_rbeg/in_rcnt)
 // into out (cells indexed 0..nc-1 by chunk-local index): table [tmask + 1] zeroed;
 // owner, newpos [32 (t1 - t0)]; ccount, ccur [nc] zeroed; grbeg [nc] receives the
-// canonical records' first slots (32-aligned), ccount their counts; *total = slots used.
+// canonical records' first slots (32-aligned), ccount their counts; total[0] = slots
+// used, total[1] = canonical records, total[2] = records that entered the grouping.
 void launch_group(const Chunk &c, uint32_t *table, uint32_t tmask, uint32_t *owner, uint32_t *ccount,
                   uint32_t *ccur, uint32_t *newpos, uint64_t *grbeg, unsigned long long *total, RecView out,
                   cudaStream_t st);
@@ -131,6 +136,7 @@ void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uin
                       const double *inv_tol2, int nd, const double *grad_out, double *grad_prm, double *partial,
                       double *out, cudaStream_t st);
 int softscore_partial_doubles();
+bool softscore_supported(int fam);
 
 // words of one record of a family in the 16- or 32-bit format
 __host__ __device__ constexpr int rec_words(int nfp, bool q16) { return q16 ? nfp / 2 : nfp; }

@@ -67,6 +67,81 @@ template <> struct SoftFam<FAM_POSE3DOF> {     // r_x = x - (w1 - (a c - b s)), 
     }
 };
 
+// r_x = x - (xi (r3 . w + z) - r1 . w), r_y = y - (eta (r3 . w + z) - r2 . w) with
+// R = R(phi) (Rodrigues); d(R w)/d phi_a = (J e_a) x (R w), J = I + B [phi]x +
+// C [phi]x^2 the rotation's left Jacobian, B = (1 - cos th)/th^2, C = (th - sin th)/th^3.
+template <> struct SoftFam<FAM_POSE6DOF> {
+    static constexpr int D = 6, ND = 2, NP = 5;
+    __device__ static void eval(const double *prm, int64_t n, int64_t i, const double *p, double *r, double *dp,
+                                double *dq) {
+        const double w[3] = {prm[i], prm[n + i], prm[2 * n + i]};
+        const double xi = prm[3 * n + i], eta = prm[4 * n + i];
+        const double f0 = p[0], f1 = p[1], f2 = p[2];
+        const double th2 = f0 * f0 + f1 * f1 + f2 * f2;
+        double A, B, C;
+        if (th2 < 1e-8) {            // series: the closed forms lose accuracy near 0
+            A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+            B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+            C = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+        } else {
+            const double th = sqrt(th2);
+            double sn, cs;
+            sincos(th, &sn, &cs);
+            A = sn / th;
+            B = (1.0 - cs) / th2;
+            C = (th - sn) / (th2 * th);
+        }
+        // R = I + A K + B K^2, K = [phi]x, K^2 = phi phi^T - th2 I
+        double Rm[9];
+        const double ph[3] = {f0, f1, f2};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Rm[3 * a + b] = B * ph[a] * ph[b] + (a == b ? 1.0 - B * th2 : 0.0);
+        Rm[1] -= A * f2; Rm[2] += A * f1;
+        Rm[3] += A * f2; Rm[5] -= A * f0;
+        Rm[6] -= A * f1; Rm[7] += A * f0;
+        double X[3];
+        for (int a = 0; a < 3; ++a) X[a] = Rm[3 * a] * w[0] + Rm[3 * a + 1] * w[1] + Rm[3 * a + 2] * w[2];
+        const double Dz = X[2] + p[3];
+        r[0] = p[4] - (xi * Dz - X[0]);
+        r[1] = p[5] - (eta * Dz - X[1]);
+        for (int a = 0; a < 3; ++a) {
+            // u = J e_a = e_a + B (phi x e_a) + C (phi x (phi x e_a))
+            double e[3] = {0.0, 0.0, 0.0};
+            e[a] = 1.0;
+            const double c1[3] = {ph[1] * e[2] - ph[2] * e[1], ph[2] * e[0] - ph[0] * e[2], ph[0] * e[1] - ph[1] * e[0]};
+            const double c2[3] = {ph[1] * c1[2] - ph[2] * c1[1], ph[2] * c1[0] - ph[0] * c1[2],
+                                  ph[0] * c1[1] - ph[1] * c1[0]};
+            double u[3];
+            for (int b = 0; b < 3; ++b) u[b] = e[b] + B * c1[b] + C * c2[b];
+            const double dX[3] = {u[1] * X[2] - u[2] * X[1], u[2] * X[0] - u[0] * X[2], u[0] * X[1] - u[1] * X[0]};
+            dp[a] = -(xi * dX[2] - dX[0]);
+            dp[D + a] = -(eta * dX[2] - dX[1]);
+        }
+        dp[3] = -xi; dp[4] = 1.0; dp[5] = 0.0;
+        dp[D + 3] = -eta; dp[D + 4] = 0.0; dp[D + 5] = 1.0;
+        for (int b = 0; b < 3; ++b) {
+            dq[b] = -(xi * Rm[6 + b] - Rm[b]);
+            dq[NP + b] = -(eta * Rm[6 + b] - Rm[3 + b]);
+        }
+        dq[3] = -Dz; dq[4] = 0.0;
+        dq[NP + 3] = 0.0; dq[NP + 4] = -Dz;
+    }
+};
+
+template <> struct SoftFam<FAM_RAYS3D> {       // r_y = y - (a x + b), r_z = z - (c x + d)
+    static constexpr int D = 3, ND = 2, NP = 4;
+    __device__ static void eval(const double *prm, int64_t n, int64_t i, const double *p, double *r, double *dp,
+                                double *dq) {
+        const double a = prm[i], b = prm[n + i], c = prm[2 * n + i], d = prm[3 * n + i];
+        r[0] = p[1] - (a * p[0] + b);
+        r[1] = p[2] - (c * p[0] + d);
+        dp[0] = -a; dp[1] = 1.0; dp[2] = 0.0;
+        dp[3] = -c; dp[4] = 0.0; dp[5] = 1.0;
+        dq[0] = -p[0]; dq[1] = -1.0; dq[2] = 0.0; dq[3] = 0.0;
+        dq[4] = 0.0; dq[5] = 0.0; dq[6] = -p[0]; dq[7] = -1.0;
+    }
+};
+
 struct SoftArgs {
     const double *prm;
     int64_t n;
@@ -164,7 +239,7 @@ void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uin
     a.partial = partial;
     for (int j = 0; j < nd; ++j) a.inv_tol2[j] = inv_tol2[j];
     int nb = ss_blocks(n);
-    int d = fam == FAM_LINE2D ? 2 : 3;
+    int d = fam == FAM_LINE2D ? 2 : (fam == FAM_POSE6DOF ? 6 : 3);
     switch (fam) {
     case FAM_LINE2D:
         if (bwd) k_softscore<FAM_LINE2D, true><<<nb, kSsThreads, 0, st>>>(a);
@@ -178,10 +253,23 @@ void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uin
         if (bwd) k_softscore<FAM_POSE3DOF, true><<<nb, kSsThreads, 0, st>>>(a);
         else k_softscore<FAM_POSE3DOF, false><<<nb, kSsThreads, 0, st>>>(a);
         break;
+    case FAM_RAYS3D:
+        if (bwd) k_softscore<FAM_RAYS3D, true><<<nb, kSsThreads, 0, st>>>(a);
+        else k_softscore<FAM_RAYS3D, false><<<nb, kSsThreads, 0, st>>>(a);
+        break;
+    case FAM_POSE6DOF:
+        if (bwd) k_softscore<FAM_POSE6DOF, true><<<nb, kSsThreads, 0, st>>>(a);
+        else k_softscore<FAM_POSE6DOF, false><<<nb, kSsThreads, 0, st>>>(a);
+        break;
     }
     k_softscore_final<<<1, 32, 0, st>>>(partial, nb, bwd ? d : 1, out);
 }
 
 int softscore_partial_doubles() { return kSsBlocks * GV_MAXD; }
+
+bool softscore_supported(int fam) {
+    return fam == FAM_LINE2D || fam == FAM_PLANE3D_SPH || fam == FAM_POSE3DOF || fam == FAM_POSE6DOF ||
+           fam == FAM_RAYS3D;
+}
 
 }  // namespace gv

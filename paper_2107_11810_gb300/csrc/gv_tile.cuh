@@ -7,6 +7,8 @@
 // tiles w, w + kWarps, ... (so that each step of the block reads consecutive
 // memory).
 #pragma once
+#include <type_traits>
+
 #include "gv_kernels.h"
 
 namespace gv {
@@ -205,12 +207,17 @@ __device__ __forceinline__ int test64(const Level &lev, const double *f, const d
     return ub | (lb << 1);
 }
 
+// pass masks: one bit per child slot
+template <int FAM>
+using SlotMask = typename std::conditional<((1 << Fam<FAM>::D) > 32), unsigned long long, unsigned>::type;
+
 // UB/LB pass masks of one record (integer fields) against every child slot, exactly
 // as the definition evaluates them.  g64: the cell's basis changes [2^k][NB].
 template <int FAM>
 __device__ __forceinline__ void eval64(const Problem &P, const Level &lev, const int *qf, const int *qt,
-                                       const double *g64, unsigned &ubm, unsigned &lbm) {
+                                       const double *g64, SlotMask<FAM> &ubm, SlotMask<FAM> &lbm) {
     using F = Fam<FAM>;
+    using Mask = SlotMask<FAM>;
     constexpr int NS = 1 << F::D, NFS = 1 << F::K;
     double f[F::ND], t[F::LE], R[F::ND];
 #pragma unroll
@@ -235,8 +242,8 @@ __device__ __forceinline__ void eval64(const Problem &P, const Level &lev, const
                 ub &= a <= R[j];
                 lb &= a <= lev.rlb[j];
             }
-            ubm |= (unsigned)ub << s;
-            lbm |= (unsigned)lb << s;
+            ubm |= (Mask)ub << s;
+            lbm |= (Mask)lb << s;
         }
     }
 }
@@ -244,14 +251,15 @@ __device__ __forceinline__ void eval64(const Problem &P, const Level &lev, const
 // Record words passed by value to the out-of-line FP64 helpers below (so that the
 // caller's arrays stay in registers).
 struct RecWords {
-    uint32_t w[4];
+    uint32_t w[16];
 };
 
 template <int NW>
 __device__ __forceinline__ RecWords rec_words_of(const uint32_t *w) {
+    static_assert(NW <= 16, "record words");
     RecWords r;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) r.w[i] = i < NW ? w[i] : 0u;
+    for (int i = 0; i < 16; ++i) r.w[i] = i < NW ? w[i] : 0u;
     return r;
 }
 
@@ -265,9 +273,29 @@ __device__ __noinline__ uint2 eval64_words(const Problem *P, const Level *lev, R
     for (int j = 0; j < F::ND; ++j) qf[j] = field_i<Q16>(rw.w, j);
 #pragma unroll
     for (int m = 0; m < F::LE; ++m) qt[m] = field_i<Q16>(rw.w, F::ND + m);
-    unsigned ubm, lbm;
+    SlotMask<FAM> ubm, lbm;
     eval64<FAM>(*P, *lev, qf, qt, g64, ubm, lbm);
-    return make_uint2(ubm, lbm);
+    if constexpr (sizeof(SlotMask<FAM>) == 8) {
+        // families with more than 32 child slots use eval64_words_wide
+        return make_uint2(0u, 0u);
+    } else {
+        return make_uint2(ubm, lbm);
+    }
+}
+
+// The same for families with more than 32 child slots: x = UB mask, y = LB mask.
+template <int FAM, bool Q16>
+__device__ __noinline__ ulonglong2 eval64_words_wide(const Problem *P, const Level *lev, RecWords rw,
+                                                    const double *g64) {
+    using F = Fam<FAM>;
+    int qf[F::ND], qt[F::LE];
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) qf[j] = field_i<Q16>(rw.w, j);
+#pragma unroll
+    for (int m = 0; m < F::LE; ++m) qt[m] = field_i<Q16>(rw.w, F::ND + m);
+    SlotMask<FAM> ubm, lbm;
+    eval64<FAM>(*P, *lev, qf, qt, g64, ubm, lbm);
+    return make_ulonglong2((unsigned long long)ubm, (unsigned long long)lbm);
 }
 
 // Exact FP64 snap of one record's free parameters at the centre of child s, out of
@@ -305,7 +333,8 @@ __device__ __forceinline__ void partial32(const float *qf, const float *qt, cons
     for (int j = 0; j < F::ND; ++j) {
         float v = qf[j];
 #pragma unroll
-        for (int m = 0; m < F::LE; ++m) v = __fmaf_rn(qt[m], G[(fs * F::ND + j) * F::LE + m], v);
+        for (int m = 0; m < F::LE; ++m)
+            if (F::uses(j, m)) v = __fmaf_rn(qt[m], G[(fs * F::ND + j) * F::LE + m], v);
         u[j] = v;
     }
 }
@@ -320,7 +349,8 @@ __device__ __forceinline__ void magnitudes(const float *qf, const float *qt, con
     for (int j = 0; j < F::ND; ++j) {
         float v = fabsf(qf[j]) + hs[j];
 #pragma unroll
-        for (int m = 0; m < F::LE; ++m) v = __fmaf_ru(fabsf(qt[m]), Gmax[j * F::LE + m], v);
+        for (int m = 0; m < F::LE; ++m)
+            if (F::uses(j, m)) v = __fmaf_ru(fabsf(qt[m]), Gmax[j * F::LE + m], v);
         M[j] = v;
     }
 }

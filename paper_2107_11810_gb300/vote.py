@@ -14,7 +14,7 @@ import threading
 
 import numpy as np
 
-from .inputs import LINE2D, PLANE3D_SPH, POSE3DOF, FAMILY_DK
+from .inputs import LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, FAMILY_DK
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libvote.so")
@@ -24,11 +24,11 @@ _lib = None
 VOTE_OPT_PRECISION, VOTE_OPT_PRUNE, VOTE_OPT_CHUNK_RECORDS = 1, 2, 3
 VOTE_OPT_TRACE_CAP, VOTE_OPT_GROUP, VOTE_OPT_FAULT_ALLOC_AT = 4, 5, 6
 VOTE_OPT_INITIAL_LB, VOTE_OPT_KERNEL_TIMING, VOTE_OPT_BATCH_WORKERS = 7, 8, 10
-VOTE_OPT_DIVE = 11
+VOTE_OPT_DIVE, VOTE_OPT_SPIN_LIMIT = 11, 12
 KERNEL_CLASSES = ["lift", "cell_geo", "test_count", "test_emit", "children", "replay", "group", "spare"]
 STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
           5: "VOTE_ETIMEOUT", 6: "VOTE_EUNSUPPORTED", 7: "VOTE_EINTERNAL"}
-NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4}
+NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4, POSE6DOF: 5, RAYS3D: 4}
 EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
            "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_get_kernel_times",
            "vote_get_level_stats", "vote_cell_counts_noalloc", "vote_softscore_fwd", "vote_softscore_bwd",
@@ -73,7 +73,7 @@ def load(path: str | None = None):
             lib.vote_get_trace.argtypes = [P, i64, P, P, P, P, P]
             lib.vote_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
             lib.vote_get_kernel_times.argtypes = [P, P, P, P]
-            lib.vote_get_level_stats.argtypes = [P, P, P]
+            lib.vote_get_level_stats.argtypes = [P, P, P, P, P]
             lib.vote_cell_counts_noalloc.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P]
             lib.vote_softscore_fwd.argtypes = [P, P, i64, P, P, P, P]
             lib.vote_softscore_bwd.argtypes = [P, P, i64, P, P, P, P, P, P]
@@ -243,13 +243,15 @@ class Solver:
         _check(self.lib.vote_get_kernel_times(self.h, _ptr(ms), _ptr(nl), _ptr(by)))
         return {k: (float(ms[i]), int(nl[i]), float(by[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
-    def level_stats(self):
-        """(cells[l], records[l]) expanded / tested per level in the last solve."""
+    def level_stats(self) -> dict:
+        """Per level of the last solve: cells expanded, record slots tested, and with
+        grouping on the records entering the grouping and the canonical records
+        leaving it (merge fraction = 1 - grouped_out / grouped_in)."""
         L, _ = self.levels()
-        cells = np.zeros(max(L, 1), np.int64)
-        recs = np.zeros(max(L, 1), np.int64)
-        _check(self.lib.vote_get_level_stats(self.h, _ptr(cells), _ptr(recs)))
-        return cells[:L], recs[:L]
+        a = {k: np.zeros(max(L, 1), np.int64) for k in ("cells", "records", "grouped_in", "grouped_out")}
+        _check(self.lib.vote_get_level_stats(self.h, _ptr(a["cells"]), _ptr(a["records"]), _ptr(a["grouped_in"]),
+                                             _ptr(a["grouped_out"])))
+        return {k: v[:L] for k, v in a.items()}
 
     def stats(self) -> dict:
         s = Stats()

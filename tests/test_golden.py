@@ -1,6 +1,5 @@
 """Golden fixtures (tests/golden/, written by tests/golden/make_golden.py from the
 oracle): the oracle reproduces them, and so does the CUDA path (GPU)."""
-import glob
 import json
 import os
 
@@ -8,8 +7,10 @@ import numpy as np
 import pytest
 
 import oracle
+from golden.make_golden import CASES
 
-FIXTURES = sorted(glob.glob(os.path.join(os.path.dirname(__file__), "golden", "*.json")))
+# the fixtures tests/golden/make_golden.py writes (inputs stored with them)
+FIXTURES = sorted(os.path.join(os.path.dirname(__file__), "golden", name + ".json") for name, _, _ in CASES)
 
 
 class Fixture:

@@ -5,8 +5,14 @@
   tests), so sampled outputs it can compute one by one are compared: the best
   leaf's count and inlier set by replaying every surface from the root, and
   random cells at several levels; plus the planted-plane lower bound.
+- 3D plane fitting at the workload's eps (0.005, L = 12) with 1e4 points: a complete
+  oracle solve (multi-core), stored with the hash of its input by
+  tests/golden/make_full_eps.py; bit-exact in both precision modes.
 - Batched 3DoF: the first problems completely, every problem's best leaf by replay.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -24,6 +30,30 @@ def _lib():
         pytest.skip("no CUDA device")
     from paper_2107_11810_gb300 import build
     build.build()
+
+
+def test_plane3d_full_eps_1e4_bit_exact_against_the_oracle():
+    from golden import make_full_eps
+    from paper_2107_11810_gb300 import vote
+    with open(os.path.join(os.path.dirname(__file__), "golden", make_full_eps.NAME + ".json")) as f:
+        gold = json.load(f)
+    p = inputs.plane3d(**gold["kwargs"])
+    assert p.eps[2] == 0.005
+    if make_full_eps.params_sha256(p.params) == gold["params_sha256"]:
+        want = dict(depth=gold["depth"], best_leaf=np.array(gold["best_leaf"]),
+                    best_point=np.array([float.fromhex(x) for x in gold["best_point"]]),
+                    mask=np.array(gold["mask"], np.uint32))
+    else:                       # this platform generated other input bits: ask the oracle itself
+        want = oracle.solve_parallel(p.family, p.eps, p.bounds, p.params)
+    t = torch.from_numpy(p.params).cuda()
+    for precision in (1, 0):
+        s = vote.Solver(p.family, p.eps, p.bounds, precision=precision)
+        r = s.solve(t)
+        assert s.levels()[0] == 12
+        assert r["depth"] == want["depth"]
+        assert np.array_equal(r["best_leaf"], want["best_leaf"])
+        assert np.array_equal(r["best_point"], want["best_point"])
+        assert np.array_equal(vote.mask_words_to_numpy(r["mask"]), want["mask"])
 
 
 def test_pose3dof_1e6_bit_exact_against_the_oracle():

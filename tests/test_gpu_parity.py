@@ -55,10 +55,12 @@ def small(family, n, seed):
         return inputs.line2d(n=n, inlier_frac=0.2, eps=0.02, seed=seed)
     if family == inputs.PLANE3D_SPH:
         return inputs.plane3d(n=n, inlier_frac=0.2, eps=0.06, sigma=0.002, seed=seed)
+    if family == inputs.RAYS3D:
+        return inputs.rays3d(n=n, inlier_frac=0.2, eps=0.02, noise=0.002, seed=seed)
     return inputs.pose3dof(n=n, inlier_frac=0.2, eps_xy=1.0, eps_yaw_deg=2.0, noise_deg=0.05, seed=seed)
 
 
-FAMS = [inputs.LINE2D, inputs.PLANE3D_SPH, inputs.POSE3DOF]
+FAMS = [inputs.LINE2D, inputs.PLANE3D_SPH, inputs.POSE3DOF, inputs.RAYS3D]
 
 
 @pytest.mark.parametrize("family", FAMS)

@@ -22,6 +22,8 @@ CASES = [
     (inputs.LINE2D, lambda: inputs.line2d(n=3001, seed=41), [0.02]),
     (inputs.PLANE3D_SPH, lambda: inputs.plane3d(n=5003, seed=42), [0.01]),
     (inputs.POSE3DOF, lambda: inputs.pose3dof(n=4007, seed=43), [0.5, 0.5]),
+    (inputs.POSE6DOF, lambda: inputs.pose6dof(n=1503, prior_deg=5.0, levels=5, seed=44), [0.1, 0.1]),
+    (inputs.RAYS3D, lambda: inputs.rays3d(n=4001, seed=45), [0.01, 0.01]),
 ]
 
 

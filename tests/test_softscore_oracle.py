@@ -58,7 +58,8 @@ def test_exact_inliers_sum_of_weights_and_plane_double_cover():
 def test_oracle_gradients_match_central_differences():
     for fam, mk, tol in [(ss.LINE2D, lambda: inputs.line2d(n=200, seed=4), [0.05]),
                          (ss.PLANE3D_SPH, lambda: inputs.plane3d(n=200, seed=5), [0.05]),
-                         (ss.POSE3DOF, lambda: inputs.pose3dof(n=200, seed=6), [2.0, 2.0])]:
+                         (ss.POSE3DOF, lambda: inputs.pose3dof(n=200, seed=6), [2.0, 2.0]),
+                         (ss.POSE6DOF, lambda: inputs.pose6dof(n=200, seed=7), [0.5, 0.5])]:
         prob = mk()
         prm = torch.from_numpy(prob.params.copy()).requires_grad_(True)
         p = torch.tensor(prob.truth, dtype=torch.float64) + 0.003
@@ -79,3 +80,26 @@ def test_oracle_gradients_match_central_differences():
             with torch.no_grad():
                 fd = (ss.softscore(fam, prm + e, p, w, tol) - ss.softscore(fam, prm - e, p, w, tol)) / (2 * h)
             assert abs(float(fd) - float(gq[m, i])) <= 1e-6 * max(1.0, abs(float(fd)))
+
+
+def test_pose6_residuals_equal_the_textbook_projection():
+    # x - F_x = X_1 - xi X_3 with X = R w + t the point in the camera frame (scipy's
+    # rotation, independent of the oracle's): zero for a noise-free match
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(8)
+    phi, t = np.array([0.4, -0.7, 0.2]), np.array([2.0, 3.0, 6.0])
+    R = Rotation.from_rotvec(phi).as_matrix()
+    w = rng.uniform(0, 5, size=(20, 3))
+    X = w @ R.T + t
+    xi, eta = X[:, 0] / X[:, 2], X[:, 1] / X[:, 2]
+    prm = torch.from_numpy(np.stack([w[:, 0], w[:, 1], w[:, 2], xi, eta]))
+    p = torch.tensor([*phi, t[2], t[0], t[1]], dtype=torch.float64)
+    r = ss.residuals(ss.POSE6DOF, prm, p)
+    assert float(r.abs().max()) < 1e-12
+    s = ss.softscore(ss.POSE6DOF, prm, p, torch.ones(20, dtype=torch.float64), [0.1, 0.1])
+    assert abs(float(s) - 20.0) < 1e-9
+    # a perturbed image point: the residual is the lateral offset X_3 (xi' - xi)
+    prm2 = prm.clone()
+    prm2[3] = prm2[3] + 0.01
+    r2 = ss.residuals(ss.POSE6DOF, prm2, p)
+    assert np.allclose(r2[:, 0].numpy(), -0.01 * X[:, 2], atol=1e-12)
