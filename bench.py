@@ -57,13 +57,16 @@ WORKLOADS = {
                            "box/128 in x and y, (phi1,phi2,phi3,z,x,y) space"),
     "pose6dof_prior5_n5000": dict(make=lambda: inputs.pose6dof(n=5000, prior_deg=5.0), desc="6DoF calibrated-"
                                   "camera voting as pose6dof_n5000 with a +-5 deg rotation prior"),
+    "rays3d_n1e5": dict(make=lambda: inputs.rays3d(), desc="rays in 3-space, 1e5 rays (2% through a common "
+                        "point, N(0, 0.0005) offsets), slopes U[-2,2], unit cube, eps 0.002, (x,y,z) space"),
     "pose3dof_batch256": dict(make=lambda: inputs.pose3dof_batch(), batched=True,
                               desc="256 independent 3DoF problems, n log-uniform in [1e3, 1e6], inlier ratio "
                                    "U[0.5%, 5%]; one vote_solve_batched call per step"),
 }
 # FP32-pipe instructions per (child cell, canonical surface) test, counted from
 # the formulas of each family's residual and comparisons
-INSTR_PER_TEST = {inputs.LINE2D: 7, inputs.PLANE3D_SPH: 10, inputs.POSE3DOF: 14, inputs.POSE6DOF: 30}
+INSTR_PER_TEST = {inputs.LINE2D: 7, inputs.PLANE3D_SPH: 10, inputs.POSE3DOF: 14, inputs.POSE6DOF: 30,
+                  inputs.RAYS3D: 10}
 
 
 def env_rank():
@@ -475,7 +478,8 @@ def main():
 
 # tests per full problem measured by the GPU path (used to scale the reference
 # arm's oracle sample to problems/s); refreshed from bench runs
-REF_TESTS = {"plane3d_n1e6": 1.0476383009996e13, "pose3dof_n1e6": 3.030014590e9, "line2d_n1e4": 8.324422e6}
+REF_TESTS = {"plane3d_n1e6": 1.0476383009996e13, "pose3dof_n1e6": 3.0e9, "line2d_n1e4": 8.324422e6,
+             "pose6dof_n5000": 6.136e11, "pose6dof_prior5_n5000": 9.504e9, "rays3d_n1e5": 1.027e8}
 
 if __name__ == "__main__":
     main()

@@ -91,8 +91,10 @@ typedef enum {
     VOTE_OPT_CHUNK_RECORDS = 3, /* records processed per expansion step; default 2^27
                                  for planes (their pruning hardly depends on the
                                  step size, so larger steps only save per-step
-                                 overhead), 2^25 for the other families (finer
-                                 depth-first steps keep their pruning effective)    */
+                                 overhead), 2^25 for the other families with d = 2
+                                 or 3 (finer depth-first steps keep their pruning
+                                 effective), 2^23 for d = 4 or 5 and 2^21 for d = 6
+                                 (a step's children can hold 2^d times its records) */
     VOTE_OPT_TRACE_CAP = 4,   /* >0: record (level, coords, UB, LB) of every tested
                                  child, up to this many entries (debug; default 0)   */
     VOTE_OPT_GROUP = 5,       /* merging of identical canonical surfaces:

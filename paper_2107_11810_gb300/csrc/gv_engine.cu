@@ -916,7 +916,10 @@ vote_status vote_create(int family, int d, int k, const double *eps, const doubl
     // step size measured fastest on GB300 (1e6-surface workloads): planes keep almost
     // every cell above the bound, so larger steps only remove per-step overhead;
     // 3DoF prunes well and needs fine depth-first steps
-    c->chunk_records = family == VOTE_PLANE3D_SPH ? (int64_t)1 << 27 : (int64_t)1 << 25;
+    // a step's children can hold 2^d times its records: 64-child families take
+    // smaller steps so that the next level's records stay within a few GB
+    c->chunk_records = family == VOTE_PLANE3D_SPH ? (int64_t)1 << 27
+                       : (d >= 6 ? (int64_t)1 << 21 : (d >= 4 ? (int64_t)1 << 23 : (int64_t)1 << 25));
     c->family = family;
     if (const char *lg = std::getenv("VOTE_LOG")) c->log = std::atoi(lg) > 0 ? std::atoi(lg) : 0;
     for (int j = 0; j < d; ++j) {

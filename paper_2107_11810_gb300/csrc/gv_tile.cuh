@@ -3,9 +3,10 @@
 // (canonical record, child cell) pair).
 //
 // Work unit: a tile of 32 consecutive records of one cell, one record per lane of
-// a warp.  A block of kWarps warps takes kBlockTiles consecutive tiles, warp w the
-// tiles w, w + kWarps, ... (so that each step of the block reads consecutive
-// memory).
+// a warp.  A block of kWarps warps takes groups of kBlockTiles consecutive tiles,
+// warp w the kTW consecutive tiles w kTW .. w kTW + kTW - 1 of each group (so that
+// a warp's run of tiles of one cell stays together and its counters are flushed
+// once per run).
 #pragma once
 #include <type_traits>
 

@@ -1,11 +1,11 @@
 // gv_wide.cu -- the proximity test's count and emit passes for families whose
-// cells split into 64 children (POSE6DOF: all six coordinates split, Algorithm 2's
-// 2^d sub-boxes).  The same tests as gv_count.cu and gv_emit.cu (the surface-box
-// test of Sec. 3.2 with the FP32 screen and FP64 recheck, and the snap of the child
-// records for the next level), laid out for 64 child slots: a lane keeps the
-// counters and the ballot of child slots lane and lane + 32, and the screen's
-// coefficients of the 16 free child slots are read from the cell's geometry
-// through the cache (they are the same for every lane of a warp).
+// cells split into 16, 32 or 64 children (d = 4, 5, 6: Algorithm 2's 2^d
+// sub-boxes).  The same tests as gv_count.cu and gv_emit.cu (the surface-box test
+// of Sec. 3.2 with the FP32 screen and FP64 recheck, and the snap of the child
+// records for the next level), laid out for many child slots: lane s % 32 keeps the
+// counters and the ballot of child slot s, and the screen's coefficients of the
+// free child slots are read from the cell's geometry through the cache (they are
+// the same for every lane of a warp).
 //
 // Each warp takes a contiguous range of the chunk's tiles (so runs of tiles of one
 // cell stay together) and reads its records with plain loads; there are no
@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(256) k_count_wide(const __grid_constant__ Chun
     using F = Fam<FAM>;
     using Mask = SlotMask<FAM>;
     constexpr int NS = 1 << F::D, NFS = 1 << F::K, NDS = 1 << F::ND, ND = F::ND, LE = F::LE;
-    static_assert(NS == 64, "two child slots per lane");
+    static_assert(NS >= 16 && NS <= 64, "16 to 64 child slots");
+    constexpr int SPL = NS > 32 ? NS / 32 : 1;                     // child slots per lane
     constexpr int NW = rec_words(F::NFP, Q16);
     constexpr int GF = geo32_floats(NFS, ND, LE);
     const int lane = threadIdx.x & 31;
@@ -39,14 +40,17 @@ __global__ void __launch_bounds__(256) k_count_wide(const __grid_constant__ Chun
 #pragma unroll
     for (int s = 0; s < NS; ++s) nvslot += !(s & ~smask);
 
-    // counters of the current run of tiles of one cell, for slots lane and lane + 32
-    unsigned cu[2] = {0u, 0u}, cl[2] = {0u, 0u}, cn[2] = {0u, 0u};
+    // counters of the current run of tiles of one cell, for slots lane + 32 h
+    unsigned cu[SPL], cl[SPL], cn[SPL];
+#pragma unroll
+    for (int h = 0; h < SPL; ++h) cu[h] = cl[h] = cn[h] = 0u;
     int run = -1;
     unsigned ntest = 0, nrechk = 0, nrec = 0;
     auto flush = [&]() {
         if (run < 0) return;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < SPL; ++h) {
+            if (lane + 32 * h >= NS) break;
             uint32_t *bc = c.cnt + ((size_t)run * NS + lane + 32 * h) * 3;
             if (cu[h]) atomicAdd(bc, cu[h]);
             if (cl[h]) atomicAdd(bc + 1, cl[h]);
@@ -75,7 +79,9 @@ __global__ void __launch_bounds__(256) k_count_wide(const __grid_constant__ Chun
         const uint32_t mult = WEIGHTED ? (act ? c.in.mult[r] : 0u) : 1u;
         const float *G = c.geo32 + (size_t)cell * GF;
         const double *g64 = c.geo64 + (size_t)cell * NFS * F::NB;
-        unsigned bw[2] = {0u, 0u};                                  // ballots of slots lane, lane + 32
+        unsigned bw[SPL];                                           // ballots of slots lane + 32 h
+#pragma unroll
+        for (int h = 0; h < SPL; ++h) bw[h] = 0u;
         // child slot s: the warp's ballots and sums go to lane s % 32
         auto count = [&](int s, bool ub, bool lb) {
             const unsigned bu = __ballot_sync(kFull, ub);
@@ -174,8 +180,9 @@ __global__ void __launch_bounds__(256) k_count_wide(const __grid_constant__ Chun
         }
         // the tile's ballots, one word per child slot
         uint32_t *bp = c.ballot + (size_t)tt * NS;
-        bp[lane] = bw[0];
-        bp[32 + lane] = bw[1];
+#pragma unroll
+        for (int h = 0; h < SPL; ++h)
+            if (lane + 32 * h < NS) bp[lane + 32 * h] = bw[h];
     }
     flush();
     ntest = __reduce_add_sync(kFull, lane == 0 ? ntest : 0u);
@@ -192,7 +199,7 @@ template <int FAM, bool QI16, bool QO16, int PREC>
 __global__ void __launch_bounds__(256) k_emit_wide(const __grid_constant__ Chunk c) {
     using F = Fam<FAM>;
     constexpr int NS = 1 << F::D, NFS = 1 << F::K, NDS = 1 << F::ND, ND = F::ND, LE = F::LE, NFP = F::NFP;
-    static_assert(NS == 64 && ND <= 2, "two child slots per lane, two dependent coordinates");
+    static_assert(NS >= 16 && NS <= 64 && ND <= 2, "16 to 64 child slots, two dependent coordinates");
     constexpr int NWI = rec_words(NFP, QI16), NWO = rec_words(NFP, QO16);
     constexpr int GF = geo32_floats(NFS, ND, LE);
     const int lane = threadIdx.x & 31;
@@ -214,8 +221,10 @@ __global__ void __launch_bounds__(256) k_emit_wide(const __grid_constant__ Chunk
         if (cell < 0) continue;                                     // uniform
         const uint32_t *bp = c.ballot + (size_t)tt * NS;
         const unsigned long long *dp = c.tdst + (size_t)tt * NS;
-        const unsigned balA = bp[lane], balB = bp[32 + lane];
-        const unsigned long long dA = dp[lane], dB = dp[32 + lane];
+        // slots lane (A) and lane + 32 (B)
+        const bool hasA = lane < NS, hasB = lane + 32 < NS;
+        const unsigned balA = hasA ? bp[lane] : 0u, balB = hasB ? bp[32 + lane] : 0u;
+        const unsigned long long dA = hasA ? dp[lane] : ~0ull, dB = hasB ? dp[32 + lane] : ~0ull;
         // child slots this tile writes (bit s of vA: slot s, of vB: slot 32 + s)
         const unsigned vA = __ballot_sync(kFull, dA != ~0ull && balA != 0u);
         const unsigned vB = __ballot_sync(kFull, dB != ~0ull && balB != 0u);
@@ -333,10 +342,15 @@ static unsigned wide_blocks(int64_t nt) {
     return (unsigned)(want < need ? want : need);
 }
 
+#define GV_DISPATCH_WIDE(fam, CALL)                                            \
+    switch (fam) {                                                             \
+    case FAM_POSE6DOF: { constexpr int FAMV = FAM_POSE6DOF; CALL; } break;     \
+    default: break;                                                            \
+    }
+
 void launch_count_wide(const Chunk &c, cudaStream_t st) {
     const int64_t nt = c.t1 - c.t0;
-    if (nt <= 0 || c.P.fam != FAM_POSE6DOF) return;
-    constexpr int FAMV = FAM_POSE6DOF;
+    if (nt <= 0) return;
     const unsigned g = wide_blocks(nt);
     const bool w = c.in.mult != nullptr;
 #define GV_COUNT_WIDE(Q16, PREC)                                                         \
@@ -344,28 +358,33 @@ void launch_count_wide(const Chunk &c, cudaStream_t st) {
         if (w) k_count_wide<FAMV, Q16, PREC, true><<<g, 256, 0, st>>>(c);               \
         else k_count_wide<FAMV, Q16, PREC, false><<<g, 256, 0, st>>>(c);                \
     }
-    if (c.precision == 0) GV_COUNT_WIDE(false, 0)
-    else if (c.lev.q16) GV_COUNT_WIDE(true, 1)
-    else GV_COUNT_WIDE(false, 1)
+    if (c.precision == 0) {
+        GV_DISPATCH_WIDE(c.P.fam, GV_COUNT_WIDE(false, 0));
+    } else if (c.lev.q16) {
+        GV_DISPATCH_WIDE(c.P.fam, GV_COUNT_WIDE(true, 1));
+    } else {
+        GV_DISPATCH_WIDE(c.P.fam, GV_COUNT_WIDE(false, 1));
+    }
 #undef GV_COUNT_WIDE
 }
 
 bool launch_emit_wide(const Chunk &c, cudaStream_t st) {
     const int64_t nt = c.t1 - c.t0;
     if (nt <= 0) return true;
-    if (c.P.fam != FAM_POSE6DOF) return false;
-    constexpr int FAMV = FAM_POSE6DOF;
     const unsigned g = wide_blocks(nt);
     const int q = c.lev.q16, qn = c.lev.q16_next;
+    bool known = false;
+    GV_DISPATCH_WIDE(c.P.fam, (known = FAMV > 0));
+    if (!known) return false;
     if (c.precision == 0) {
         if (q || qn) return false;                  // plain FP64 mode keeps 32-bit records
-        k_emit_wide<FAMV, false, false, 0><<<g, 256, 0, st>>>(c);
+        GV_DISPATCH_WIDE(c.P.fam, (k_emit_wide<FAMV, false, false, 0><<<g, 256, 0, st>>>(c)));
     } else if (q && qn) {
-        k_emit_wide<FAMV, true, true, 1><<<g, 256, 0, st>>>(c);
+        GV_DISPATCH_WIDE(c.P.fam, (k_emit_wide<FAMV, true, true, 1><<<g, 256, 0, st>>>(c)));
     } else if (!q && qn) {
-        k_emit_wide<FAMV, false, true, 1><<<g, 256, 0, st>>>(c);
+        GV_DISPATCH_WIDE(c.P.fam, (k_emit_wide<FAMV, false, true, 1><<<g, 256, 0, st>>>(c)));
     } else if (!q && !qn) {
-        k_emit_wide<FAMV, false, false, 1><<<g, 256, 0, st>>>(c);
+        GV_DISPATCH_WIDE(c.P.fam, (k_emit_wide<FAMV, false, false, 1><<<g, 256, 0, st>>>(c)));
     } else {
         return false;                               // 16-bit to 32-bit: never chosen
     }

@@ -24,6 +24,9 @@ Surface parameters are FP64, structure-of-arrays ``params[P, n]``:
   y = eta (r3 . w + z) - r2 . w.
 * ``RAYS3D``      (intersection of rays in 3-space, Sec. 4.3): P = 4, rows (a, b, c, d)
   of the ray y = a x + b, z = c x + d; voting space (x, y, z).
+* ``POINTSET2D``  (point-set similarity alignment, Sec. 4.4): P = 4, rows (px, py, qx, qy)
+  of a hypothetical correspondence p -> q under q_x = a p_x + b p_y + c,
+  q_y = -b p_x + a p_y + d; voting space (c, d, a, b).
 """
 from __future__ import annotations
 
@@ -32,10 +35,11 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D = 1, 2, 3, 4, 5
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D = 1, 2, 3, 4, 5, 6
 FAMILY_NAMES = {LINE2D: "LINE2D", PLANE3D_SPH: "PLANE3D_SPH", POSE3DOF: "POSE3DOF", POSE6DOF: "POSE6DOF",
-                RAYS3D: "RAYS3D"}
-FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1), POSE6DOF: (6, 4), RAYS3D: (3, 1)}
+                RAYS3D: "RAYS3D", POINTSET2D: "POINTSET2D"}
+FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1), POSE6DOF: (6, 4), RAYS3D: (3, 1),
+             POINTSET2D: (4, 2)}
 SEED_BASE = 2107118100
 
 
@@ -327,6 +331,39 @@ def rays3d(n: int = 100_000, inlier_frac: float = 0.02, eps: float = 0.002, nois
                    p.copy(), inliers, "rays3d", dict(inlier_frac=inlier_frac))
 
 
+def pointset2d(m: int = 200, outlier_frac: float = 0.0, eps: float = 0.01, noise: float = 0.002,
+               seed: int = SEED_BASE + 6) -> Problem:
+    """Two point sets of m points without known correspondences: A uniform in the
+    annulus 0.25 <= |p| <= 1, B = s R A + t (+ N(0, noise)) with s ~ U[0.5, 1.5],
+    rotation angle ~ U[-60, 60] deg, t ~ U[-1, 1]^2, and a fraction of B replaced by
+    uniform points of [-2.5, 2.5]^2.  Every pair (p in A, q in B) is a surface
+    (n = m^2); the m true pairs are the inliers.  Voting domain c, d in [-2, 2]
+    (translation), a = s cos theta in [0.25, 1.75], b = s sin theta in [-1.5, 1.5]
+    (the domain leaves out scale 0, where every pair with one q agrees); eps in
+    every coordinate."""
+    rng = np.random.default_rng(seed)
+    r = np.sqrt(rng.uniform(0.25 ** 2, 1.0, m))
+    ang = rng.uniform(0.0, 2 * math.pi, m)
+    A = np.stack([r * np.cos(ang), r * np.sin(ang)], axis=1)
+    s, th = rng.uniform(0.5, 1.5), rng.uniform(-math.pi / 3, math.pi / 3)
+    a, b = s * math.cos(th), s * math.sin(th)
+    t = rng.uniform(-1.0, 1.0, 2)
+    B = np.stack([a * A[:, 0] + b * A[:, 1] + t[0], -b * A[:, 0] + a * A[:, 1] + t[1]], axis=1)
+    B += rng.normal(0.0, noise, B.shape)
+    n_out = int(round(m * outlier_frac))
+    out_idx = rng.choice(m, n_out, replace=False)
+    B[out_idx] = rng.uniform(-2.5, 2.5, (n_out, 2))
+    P = np.repeat(A, m, axis=0)
+    Q = np.tile(B, (m, 1))
+    params = np.stack([P[:, 0], P[:, 1], Q[:, 0], Q[:, 1]])
+    truth_pairs = np.arange(m) * m + np.arange(m)
+    keep = np.ones(m, bool)
+    keep[out_idx] = False
+    return Problem(POINTSET2D, np.full(4, eps), np.array([-2.0, 2.0, -2.0, 2.0, 0.25, 1.75, -1.5, 1.5]),
+                   np.ascontiguousarray(params), np.array([t[0], t[1], a, b]), truth_pairs[keep], "pointset2d",
+                   dict(m=m, scale=s, theta=th))
+
+
 # ---------------------------------------------------------------------------
 # Standard workloads
 # ---------------------------------------------------------------------------
@@ -350,4 +387,6 @@ def random_small(family: int, n: int, seed: int, inlier_frac: float = 0.3, **kw)
         return pose6dof(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
     if family == RAYS3D:
         return rays3d(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
+    if family == POINTSET2D:
+        return pointset2d(m=max(1, int(round(math.sqrt(n)))), seed=seed, **kw)
     raise ValueError(family)
