@@ -67,7 +67,8 @@
 #define GVO_MAXT 11
 #define GVO_MAXL 40
 
-enum { GVO_LINE2D = 1, GVO_PLANE3D_SPH = 2, GVO_POSE3DOF = 3, GVO_POSE6DOF = 4, GVO_RAYS3D = 5 };
+enum { GVO_LINE2D = 1, GVO_PLANE3D_SPH = 2, GVO_POSE3DOF = 3, GVO_POSE6DOF = 4, GVO_RAYS3D = 5,
+       GVO_POINTSET2D = 6 };
 enum { GVO_NO_MERGE = 1, GVO_NO_PRUNE = 2, GVO_REVERSE = 4 };
 
 /* ------------------------------------------------------------------------- */
@@ -190,6 +191,7 @@ static int family_shape(int fam, int d, int k, int *le, int *np)
     case GVO_POSE3DOF:    if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
     case GVO_POSE6DOF:    if (d != 6 || k != 4) return 1; *le = 11; *np = 5; return 0;
     case GVO_RAYS3D:      if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
+    case GVO_POINTSET2D:  if (d != 4 || k != 2) return 1; *le = 2; *np = 4; return 0;
     default: return 1;
     }
 }
@@ -216,6 +218,10 @@ static void family_sigma(const gvo_problem *p, const double *h, double *sigma)
         sigma[0] = h[0];
         sigma[1] = h[0];
         break;
+    case GVO_POINTSET2D:  /* u, v multiply c in one equation and d in the other */
+        sigma[0] = h[0] > h[1] ? h[0] : h[1];
+        sigma[1] = sigma[0];
+        break;
     case GVO_POSE6DOF: {  /* F = sum_m t_m psi_m with psi = entries of R(phi) and z */
         /* An entry R_ki of R(phi) has gradient e_k . (J e_a x R e_i) along phi_a, J the
          * rotation's Jacobian (operator norm 1), so |grad R_ki| <= 1 and the entry moves
@@ -232,7 +238,7 @@ static void family_sigma(const gvo_problem *p, const double *h, double *sigma)
 /* number of basis values psi of a family */
 static int family_nb(int fam, int le)
 {
-    return fam == GVO_POSE6DOF ? 10 : (fam == GVO_RAYS3D ? 1 : le);
+    return fam == GVO_POSE6DOF ? 10 : (fam == GVO_RAYS3D ? 1 : le);   /* point sets: (c, d), le = 2 */
 }
 
 static double pow2_floor(double x)  /* 2^floor(log2 x), exact */
@@ -302,7 +308,8 @@ static double cell_center(const gvo_problem *p, int l, int j, int64_t i)
 
 /* ------------------------------------------------------------------------- */
 /* Families (Sec. 3 Eq. 2 line duality; Sec. 4.1 plane fitting; 3DoF posing;   */
-/* Sec. 4.2.3 calibrated 6DoF posing; Sec. 4.3 rays in 3-space).              */
+/* Sec. 4.2.3 calibrated 6DoF posing; Sec. 4.3 rays in 3-space; Sec. 4.4      */
+/* point-set similarity alignment).                                           */
 /* ------------------------------------------------------------------------- */
 
 /* Rotation matrix (row-major) of the axis-angle vector ph, theta = |ph|, by
@@ -339,6 +346,10 @@ static void family_basis(const gvo_problem *p, int l, const int64_t *i, double *
         break;
     case GVO_RAYS3D:
         psi[0] = cell_center(p, l, 0, i[0]);                  /* x */
+        break;
+    case GVO_POINTSET2D:
+        psi[0] = cell_center(p, l, 0, i[0]);                  /* c */
+        psi[1] = cell_center(p, l, 1, i[1]);                  /* d */
         break;
     case GVO_PLANE3D_SPH: {
         double th = cell_center(p, l, 0, i[0]);
@@ -404,6 +415,20 @@ static void family_lift(const gvo_problem *p, const double *params, int64_t n, i
         r->f[1] = (cc * psi[0] + dd) - c[2];
         break;
     }
+    case GVO_POINTSET2D: {
+        /* correspondence p -> q under q_x = a p_x + b p_y + c, q_y = -b p_x + a p_y + d
+         * (Sec. 4.4): a = g_a - u c - v d, b = g_b - v c + u d with u = p_x/|p|^2,
+         * v = p_y/|p|^2, g_a = (p . q)/|p|^2, g_b = (p_y q_x - p_x q_y)/|p|^2 */
+        double px = params[0 * n + i], py = params[1 * n + i];
+        double qx = params[2 * n + i], qy = params[3 * n + i];
+        double n2 = px * px + py * py;
+        double u = px / n2, v = py / n2;
+        double ga = (px * qx + py * qy) / n2, gb = (py * qx - px * qy) / n2;
+        r->t[0] = u; r->t[1] = v;
+        r->f[0] = ((ga - u * psi[0]) - v * psi[1]) - c[2];
+        r->f[1] = ((gb - v * psi[0]) + u * psi[1]) - c[3];
+        break;
+    }
     case GVO_POSE6DOF: {
         /* match (w, xi, eta): x = xi (r3 . w + z) - r1 . w, y = eta (r3 . w + z) - r2 . w
          * (Sec. 4.2.2 with f = 1, Sec. 4.2.3).  Affine in the basis (rows of R, z) with
@@ -459,8 +484,8 @@ static void child_geometry(const gvo_problem *p, int l, const int64_t *i, const 
             g->shift[j] = 0.0;
         }
     }
-    if (p->fam == GVO_LINE2D || p->fam == GVO_RAYS3D) {
-        g->dpsi[0] = g->shift[0];       /* psi is linear: exact shift */
+    if (p->fam == GVO_LINE2D || p->fam == GVO_RAYS3D || p->fam == GVO_POINTSET2D) {
+        for (int m = 0; m < p->nb; ++m) g->dpsi[m] = g->shift[m];   /* psi is linear: exact shift */
     } else {
         double psi_child[GVO_MAXT];
         family_basis(p, l + 1, g->ci, psi_child);
@@ -487,6 +512,10 @@ static void family_residual(const gvo_problem *p, const double *f, const double 
     case GVO_RAYS3D:
         fo[0] = (f[0] + t[0] * g->dpsi[0]) - g->shift[1];
         fo[1] = (f[1] + t[1] * g->dpsi[0]) - g->shift[2];
+        break;
+    case GVO_POINTSET2D:
+        fo[0] = (f[0] - (t[0] * g->dpsi[0] + t[1] * g->dpsi[1])) - g->shift[2];
+        fo[1] = (f[1] - (t[1] * g->dpsi[0] - t[0] * g->dpsi[1])) - g->shift[3];
         break;
     case GVO_POSE6DOF: {
         const double *d = g->dpsi;
@@ -521,6 +550,12 @@ static void family_lipschitz(const gvo_problem *p, const double *t, double *lam)
     case GVO_RAYS3D:                        /* dy/dx = a, dz/dx = c */
         lam[0] = fabs(t[0]);
         lam[1] = fabs(t[1]);
+        break;
+    case GVO_POINTSET2D:                    /* da/dc = -u, da/dd = -v, db/dc = -v, db/dd = u */
+        lam[0] = fabs(t[0]);
+        lam[1] = fabs(t[1]);
+        lam[2] = fabs(t[1]);
+        lam[3] = fabs(t[0]);
         break;
     case GVO_POSE6DOF: {
         /* d/dphi_a of e_k . R v is e_k . (J e_a x R v), at most |v| (J of norm 1):

@@ -11,7 +11,7 @@ import itertools
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D = 1, 2, 3, 4, 5
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D = 1, 2, 3, 4, 5, 6
 
 
 def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.ndarray:
@@ -32,6 +32,13 @@ def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.n
         fx = w1 - (a * np.cos(yaw) - b * np.sin(yaw))
         fy = w2 - (a * np.sin(yaw) + b * np.cos(yaw))
         return np.stack([x - fx, y - fy], axis=-1)
+    if family == POINTSET2D:             # (a, b) solving q = [[a, b], [-b, a]] p + (c, d) (Sec. 4.4)
+        px, py, qx, qy = params
+        c, d, a, b = pts[:, 0:1], pts[:, 1:2], pts[:, 2:3], pts[:, 3:4]
+        n2 = px * px + py * py
+        sa = (px * (qx - c) + py * (qy - d)) / n2
+        sb = (py * (qx - c) - px * (qy - d)) / n2
+        return np.stack([a - sa, b - sb], axis=-1)
     if family == RAYS3D:                 # y = a x + b, z = c x + d (Sec. 4.3)
         a, b, c, d = params
         x, y, z = pts[:, 0:1], pts[:, 1:2], pts[:, 2:3]

@@ -28,7 +28,7 @@ import numpy as np
 import brute
 import oracle
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D = 1, 2, 3, 4, 5
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D = 1, 2, 3, 4, 5, 6
 
 
 def _rot(x):
@@ -51,6 +51,9 @@ def basis(family: int, x: np.ndarray) -> np.ndarray:
         return np.stack([np.cos(x[..., 0]), np.sin(x[..., 0])], axis=-1)
     if family == RAYS3D:            # y = a x + b, z = c x + d: a and c multiply x
         return np.concatenate([x[..., 0:1], x[..., 0:1]], axis=-1)
+    if family == POINTSET2D:        # a = g_a - u c - v d, b = g_b - v c + u d; t = (u, v)
+        c, d = x[..., 0:1], x[..., 1:2]
+        return np.concatenate([-c, -d, d, -c], axis=-1)
     if family == POSE6DOF:          # t = (w, xi w, eta w, xi, eta); rows of R(phi) and z
         Rm = _rot(x[..., 0:3])
         z = x[..., 3:4]
@@ -75,6 +78,9 @@ def t_part(family: int, t: np.ndarray, x: np.ndarray) -> np.ndarray:
         return np.stack([-(a * c - b * s), -(a * s + b * c)], axis=-1)
     if family == RAYS3D:
         return np.stack([t[0] * psi[..., 0], t[1] * psi[..., 1]], axis=-1)
+    if family == POINTSET2D:
+        t = np.asarray(t, float)
+        return np.stack([psi[..., :2] @ t, psi[..., 2:] @ t], axis=-1)
     if family == POSE6DOF:
         t = np.asarray(t, float)
         return np.stack([psi[..., :11] @ t, psi[..., 11:] @ t], axis=-1)
@@ -105,8 +111,8 @@ def check_sigma(p, cells_per_level=4, points=100_000, seed=0, lib=None):
     worst = []
     for l in range(lv["L"]):
         sig = oracle.sigma(p.family, lv["h"][l], lib=lib)
-        if p.family == POSE6DOF:
-            sig = np.concatenate([sig, sig])          # x-equation and y-equation functions
+        if p.family in (POSE6DOF, POINTSET2D):
+            sig = np.concatenate([sig, sig])          # the two dependent equations' functions
         w = 0.0
         for _ in range(cells_per_level):
             ci = random_cell(lv["Lj"], l, rng)

@@ -46,8 +46,11 @@ MUTANTS = {
                                      "lam[0] = fmax(fabs(t[0]), fabs(t[1]));\n        lam[1] = lam[0];"),
     "rays_residual_slope": ("fo[1] = (f[1] + t[1] * g->dpsi[0]) - g->shift[2];",
                             "fo[1] = (f[1] + t[0] * g->dpsi[0]) - g->shift[2];"),
-    "rays_lipschitz_one_slope": ("lam[0] = fabs(t[0]);\n        lam[1] = fabs(t[1]);",
-                                 "lam[0] = fabs(t[0]);\n        lam[1] = fabs(t[0]);"),
+    "rays_lipschitz_one_slope": ("dz/dx = c */\n        lam[0] = fabs(t[0]);\n        lam[1] = fabs(t[1]);",
+                                 "dz/dx = c */\n        lam[0] = fabs(t[0]);\n        lam[1] = fabs(t[0]);"),
+    "points_residual_sign": ("fo[1] = (f[1] - (t[1] * g->dpsi[0] - t[0] * g->dpsi[1])) - g->shift[3];",
+                             "fo[1] = (f[1] - (t[1] * g->dpsi[0] + t[0] * g->dpsi[1])) - g->shift[3];"),
+    "points_sigma_one_axis": ("sigma[0] = h[0] > h[1] ? h[0] : h[1];", "sigma[0] = h[1] * 0.5;"),
     "pose6_residual_row": ("double sy2 = (t[0] * d[3] + t[1] * d[4]) + t[2] * d[5];",
                            "double sy2 = (t[0] * d[0] + t[1] * d[1]) + t[2] * d[2];"),
     "pose6_rotation_sign": ("R[1] = b0 * ph[1] - a2;", "R[1] = b0 * ph[1] + a2;"),
@@ -66,6 +69,7 @@ CASES = {
                                                noise_deg=0.05, seed=s),
     inputs.POSE6DOF: lambda s: inputs.pose6dof(n=80, inlier_frac=0.3, levels=3, seed=s),
     inputs.RAYS3D: lambda s: inputs.rays3d(n=300, inlier_frac=0.3, eps=0.03, noise=0.002, seed=s),
+    inputs.POINTSET2D: lambda s: inputs.pointset2d(m=14, eps=0.08, noise=0.002, seed=s),
 }
 
 
@@ -98,6 +102,8 @@ def pins_hold(lib, fam, seed):
         free = (np.hypot(p.params[2], p.params[3]).max() + 2 * st) * hL[: p.k].sum()
     elif p.family == inputs.RAYS3D:
         free = (np.maximum(np.abs(p.params[0]), np.abs(p.params[2])).max() + st) * hL[: p.k].sum()
+    elif p.family == inputs.POINTSET2D:
+        free = ((1.0 / np.hypot(p.params[0], p.params[1])).max() + st) * hL[: p.k].sum()
     else:
         c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
         free = ((((1.0 + c) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st) * hL[0:3].sum()
@@ -118,6 +124,7 @@ MARGIN_CASES = {
     inputs.POSE3DOF: lambda: inputs.pose3dof(n=200, seed=inputs.SEED_BASE + 2),
     inputs.POSE6DOF: lambda: inputs.pose6dof(n=200, seed=inputs.SEED_BASE + 4),
     inputs.RAYS3D: lambda: inputs.rays3d(n=200, seed=inputs.SEED_BASE + 5),
+    inputs.POINTSET2D: lambda: inputs.pointset2d(m=15, seed=inputs.SEED_BASE + 6),
 }
 MARGIN_T = {
     inputs.LINE2D: [np.array([1.0]), np.array([0.3])],
@@ -126,6 +133,7 @@ MARGIN_T = {
     inputs.POSE6DOF: [np.array(v, float) for v in ([20, 20, 5, 20, 20, 5, -20, -20, -5, 1, -1],
                                                    [3, -14, 2, 1, -5, 0.5, 2, -9, 1, 0.4, 0.6])],
     inputs.RAYS3D: [np.array(v, float) for v in ([2, -2], [0.3, 1.7])],
+    inputs.POINTSET2D: [np.array(v, float) for v in ([4, 0], [1.5, -2.5])],
 }
 
 
@@ -164,7 +172,7 @@ def test_planted_mistake_is_caught(name):
 @pytest.mark.parametrize("name", [m for m in sorted(MUTANTS) if m.startswith(("plane_sigma", "plane_lipschitz",
                                                                                "pose_lipschitz", "pose_sigma",
                                                                                "pose6_lipschitz", "pose6_sigma",
-                                                                               "rays_lipschitz",
+                                                                               "rays_lipschitz", "points_sigma",
                                                                                "error_step"))])
 def test_margin_mistake_is_caught_by_the_margin_pins(name):
     old, new = MUTANTS[name]
