@@ -74,13 +74,19 @@ typedef enum {
  *                    cells split into 64 children.
  *   VOTE_RAYS3D      d=3 k=1: coords (x, y, z); input rows (a, b, c, d) of the
  *                    ray y = a x + b, z = c x + d (intersection of rays in
- *                    3-space, Sec. 4.3). */
+ *                    3-space, Sec. 4.3).
+ *   VOTE_POINTSET2D  d=4 k=2: coords (c, d, a, b); input rows (px, py, qx, qy) of a
+ *                    hypothetical correspondence p -> q under q_x = a p_x + b p_y
+ *                    + c, q_y = -b p_x + a p_y + d (point-set similarity
+ *                    alignment, Sec. 4.4); surfaces a = (p . (q - (c, d)))/|p|^2,
+ *                    b = (p_y (q_x - c) - p_x (q_y - d))/|p|^2; 16 children. */
 typedef enum {
     VOTE_LINE2D = 1,
     VOTE_PLANE3D_SPH = 2,
     VOTE_POSE3DOF = 3,
     VOTE_POSE6DOF = 4,
-    VOTE_RAYS3D = 5
+    VOTE_RAYS3D = 5,
+    VOTE_POINTSET2D = 6
 } vote_family;
 
 /* Options for vote_set_option. */

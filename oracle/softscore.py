@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import torch
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D = 1, 2, 3, 4, 5
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D = 1, 2, 3, 4, 5, 6
 
 
 def rotation(phi: torch.Tensor) -> torch.Tensor:
@@ -48,6 +48,11 @@ def residuals(family: int, params: torch.Tensor, p: torch.Tensor) -> torch.Tenso
         rx = p[1] - (w1 - (a * c - b * s))
         ry = p[2] - (w2 - (a * s + b * c))
         return torch.stack([rx, ry], dim=1)
+    if family == POINTSET2D:                   # (a, b) solving q = [[a, b], [-b, a]] p + (c, d)
+        px, py, qx, qy = params[0], params[1], params[2], params[3]
+        n2 = px * px + py * py
+        ex, ey = qx - p[0], qy - p[1]
+        return torch.stack([p[2] - (px * ex + py * ey) / n2, p[3] - (py * ex - px * ey) / n2], dim=1)
     if family == RAYS3D:                       # y = a x + b, z = c x + d
         a, b, c, d = params[0], params[1], params[2], params[3]
         return torch.stack([p[1] - (a * p[0] + b), p[2] - (c * p[0] + d)], dim=1)

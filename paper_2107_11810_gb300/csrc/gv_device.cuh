@@ -66,6 +66,7 @@ __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a,
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 
 // ---------------------------------------------------------------------------
 // sin / cos of cell-centre angles: Cody-Waite reduction by pi/2 with a three-part
@@ -147,7 +148,7 @@ __device__ __forceinline__ uint64_t child_key(const Problem &P, uint64_t key, in
 // LINEAR_BASIS: the basis is the free coordinate itself; LINEAR_TAIL: the last
 // basis value is the last free coordinate (its change is the exact child shift).
 // ---------------------------------------------------------------------------
-enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3, FAM_POSE6DOF = 4, FAM_RAYS3D = 5 };
+enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3, FAM_POSE6DOF = 4, FAM_RAYS3D = 5, FAM_POINTSET2D = 6 };
 
 template <int FAM> struct Fam;
 
@@ -305,6 +306,58 @@ template <> struct Fam<FAM_RAYS3D> {
     __device__ static void radius32(const Level &lev, const float *qt, float *R) {
         R[0] = __fmaf_rn(lev.lam_c[0], fabsf(qt[0]), lev.rc0[0]);
         R[1] = __fmaf_rn(lev.lam_c[1], fabsf(qt[1]), lev.rc0[1]);
+    }
+};
+
+// POINTSET2D: point-set similarity alignment (Sec. 4.4); coords (c, d, a, b) with
+// q_x = a p_x + b p_y + c, q_y = -b p_x + a p_y + d.  A correspondence p -> q gives
+// a = g_a - u c - v d and b = g_b - v c + u d, u = p_x/|p|^2, v = p_y/|p|^2; t = (u, v),
+// psi = (c, d) (linear: their changes across a child shift are the shifts).
+template <> struct Fam<FAM_POINTSET2D> {
+    static constexpr int D = 4, K = 2, ND = 2, LE = 2, NP = 4, NB = 2, NFP = 4;
+    static constexpr bool LINEAR_BASIS = true, LINEAR_TAIL = false;
+    __host__ __device__ static constexpr bool uses(int, int) { return true; }
+    __device__ static void basis(const Problem &, const double *c, double *psi) {
+        psi[0] = c[0];
+        psi[1] = c[1];
+    }
+    __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
+                                double *f, double *t) {
+        const double px = prm[i], py = prm[n + i], qx = prm[2 * n + i], qy = prm[3 * n + i];
+        const double n2 = dadd(dmul(px, px), dmul(py, py));
+        const double u = ddiv(px, n2), v = ddiv(py, n2);
+        const double ga = ddiv(dadd(dmul(px, qx), dmul(py, qy)), n2);
+        const double gb = ddiv(dsub(dmul(py, qx), dmul(px, qy)), n2);
+        t[0] = u;
+        t[1] = v;
+        f[0] = dsub(dsub(dsub(ga, dmul(u, psi[0])), dmul(v, psi[1])), c[2]);
+        f[1] = dsub(dadd(dsub(gb, dmul(v, psi[0])), dmul(u, psi[1])), c[3]);
+    }
+    __device__ static void residual64(const double *f, const double *t, const double *dpsi, const double *sh,
+                                      double *fo) {
+        fo[0] = dsub(dsub(f[0], dadd(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1]))), sh[2]);
+        fo[1] = dsub(dsub(f[1], dsub(dmul(t[1], dpsi[0]), dmul(t[0], dpsi[1]))), sh[3]);
+    }
+    __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
+        p[0] = dsub(f[0], dadd(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1])));
+        p[1] = dsub(f[1], dsub(dmul(t[1], dpsi[0]), dmul(t[0], dpsi[1])));
+    }
+    // da/dc = -u, da/dd = -v, db/dc = -v, db/dd = u
+    __device__ static void lipschitz64(const double *t, double *lam) {
+        lam[0] = fabs(t[0]);
+        lam[1] = fabs(t[1]);
+        lam[2] = fabs(t[1]);
+        lam[3] = fabs(t[0]);
+    }
+    __device__ static void coef(const double *dpsi, double *g) {
+        g[0] = -dpsi[0]; g[1] = -dpsi[1];      // a: -(u dc + v dd)
+        g[2] = dpsi[1]; g[3] = -dpsi[0];       // b: -(v dc - u dd)
+    }
+    // lam_c: [a with |u|, a with |v|, b with |v|, b with |u|]
+    __device__ static void radius32(const Level &lev, const float *qt, float *R) {
+        const float au = fabsf(qt[0]), av = fabsf(qt[1]);
+        R[0] = __fmaf_rn(lev.lam_c[0], au, __fmaf_rn(lev.lam_c[1], av, lev.rc0[0]));
+        R[1] = __fmaf_rn(lev.lam_c[2], av, __fmaf_rn(lev.lam_c[3], au, lev.rc0[1]));
     }
 };
 

@@ -88,9 +88,12 @@ __device__ __forceinline__ void child_dpsi(const Problem &P, const Level &lev, u
                                            const double *psi_par, double *dpsi) {
     using F = Fam<FAM>;
     if constexpr (F::LINEAR_BASIS) {
-        // psi is the free coordinate itself: its change is the exact child shift
-        bool split = (lev.split_mask >> 0) & 1;
-        dpsi[0] = split ? ((fs & 1) ? lev.h1[0] : -lev.h1[0]) : 0.0;
+        // psi is the free coordinates themselves: their changes are the exact child shifts
+#pragma unroll
+        for (int m = 0; m < F::NB; ++m) {
+            const bool split = (lev.split_mask >> m) & 1;
+            dpsi[m] = split ? (((fs >> m) & 1) ? lev.h1[m] : -lev.h1[m]) : 0.0;
+        }
         return;
     } else {
     double cch[F::D];
@@ -588,6 +591,7 @@ static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs
     case FAM_POSE3DOF: { constexpr int FAMV = FAM_POSE3DOF; CALL; } break;       \
     case FAM_RAYS3D: { constexpr int FAMV = FAM_RAYS3D; CALL; } break;           \
     case FAM_POSE6DOF: { constexpr int FAMV = FAM_POSE6DOF; CALL; } break;       \
+    case FAM_POINTSET2D: { constexpr int FAMV = FAM_POINTSET2D; CALL; } break;   \
     default: break;                                                 \
     }
 
@@ -649,6 +653,7 @@ void launch_tile_dst(const Chunk &c, cudaStream_t st) {
     const int ns = 1 << c.P.d;
     if (ns == 4) k_tile_dst<4><<<blocks_for(nt, 32), 32 * 4, 0, st>>>(c);
     else if (ns == 8) k_tile_dst<8><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
+    else if (ns == 16) k_tile_dst<16><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
     else k_tile_dst<64><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
 }
 
@@ -658,6 +663,7 @@ void launch_child_lbmax(const Chunk &c, cudaStream_t st) {
     if (n <= 0) return;
     if (ns == 4) k_child_lbmax<4><<<blocks_for(n, 256), 256, 0, st>>>(c);
     else if (ns == 8) k_child_lbmax<8><<<blocks_for(n, 256), 256, 0, st>>>(c);
+    else if (ns == 16) k_child_lbmax<16><<<blocks_for(n, 256), 256, 0, st>>>(c);
     else k_child_lbmax<64><<<blocks_for(n, 256), 256, 0, st>>>(c);
 }
 
@@ -670,11 +676,13 @@ void launch_child_alloc(const Chunk &c, uint32_t *keepflag, uint32_t *recn, unsi
     unsigned long long *ba = bsums, *bb = bsums + nb;
     if (ns == 4) k_child_mark<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else if (ns == 8) k_child_mark<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else if (ns == 16) k_child_mark<16><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else k_child_mark<64><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     if (c.lev.leaf_children) return;
     k_scan_sums<<<1, 256, 0, st>>>(ba, bb, (int)nb, c.sc);
     if (ns == 4) k_child_write<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else if (ns == 8) k_child_write<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else if (ns == 16) k_child_write<16><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else k_child_write<64><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
 }
 

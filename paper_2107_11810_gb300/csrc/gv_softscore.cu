@@ -142,6 +142,30 @@ template <> struct SoftFam<FAM_RAYS3D> {       // r_y = y - (a x + b), r_z = z -
     }
 };
 
+// r_a = a - (p_x (q_x - c) + p_y (q_y - d)) / |p|^2, r_b = b - (p_y (q_x - c) - p_x (q_y - d)) / |p|^2
+template <> struct SoftFam<FAM_POINTSET2D> {
+    static constexpr int D = 4, ND = 2, NP = 4;
+    __device__ static void eval(const double *prm, int64_t n, int64_t i, const double *p, double *r, double *dp,
+                                double *dq) {
+        const double px = prm[i], py = prm[n + i], qx = prm[2 * n + i], qy = prm[3 * n + i];
+        const double N = px * px + py * py, ex = qx - p[0], ey = qy - p[1];
+        const double A = px * ex + py * ey, B = py * ex - px * ey;
+        r[0] = p[2] - A / N;
+        r[1] = p[3] - B / N;
+        dp[0] = px / N; dp[1] = py / N; dp[2] = 1.0; dp[3] = 0.0;
+        dp[4] = py / N; dp[5] = -px / N; dp[6] = 0.0; dp[7] = 1.0;
+        const double N2 = N * N;
+        dq[0] = -(ex / N - A * 2.0 * px / N2);
+        dq[1] = -(ey / N - A * 2.0 * py / N2);
+        dq[2] = -(px / N);
+        dq[3] = -(py / N);
+        dq[4] = -(-ey / N - B * 2.0 * px / N2);
+        dq[5] = -(ex / N - B * 2.0 * py / N2);
+        dq[6] = -(py / N);
+        dq[7] = -(-px / N);
+    }
+};
+
 struct SoftArgs {
     const double *prm;
     int64_t n;
@@ -239,7 +263,7 @@ void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uin
     a.partial = partial;
     for (int j = 0; j < nd; ++j) a.inv_tol2[j] = inv_tol2[j];
     int nb = ss_blocks(n);
-    int d = fam == FAM_LINE2D ? 2 : (fam == FAM_POSE6DOF ? 6 : 3);
+    int d = fam == FAM_LINE2D ? 2 : (fam == FAM_POSE6DOF ? 6 : (fam == FAM_POINTSET2D ? 4 : 3));
     switch (fam) {
     case FAM_LINE2D:
         if (bwd) k_softscore<FAM_LINE2D, true><<<nb, kSsThreads, 0, st>>>(a);
@@ -252,6 +276,10 @@ void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uin
     case FAM_POSE3DOF:
         if (bwd) k_softscore<FAM_POSE3DOF, true><<<nb, kSsThreads, 0, st>>>(a);
         else k_softscore<FAM_POSE3DOF, false><<<nb, kSsThreads, 0, st>>>(a);
+        break;
+    case FAM_POINTSET2D:
+        if (bwd) k_softscore<FAM_POINTSET2D, true><<<nb, kSsThreads, 0, st>>>(a);
+        else k_softscore<FAM_POINTSET2D, false><<<nb, kSsThreads, 0, st>>>(a);
         break;
     case FAM_RAYS3D:
         if (bwd) k_softscore<FAM_RAYS3D, true><<<nb, kSsThreads, 0, st>>>(a);
@@ -269,7 +297,7 @@ int softscore_partial_doubles() { return kSsBlocks * GV_MAXD; }
 
 bool softscore_supported(int fam) {
     return fam == FAM_LINE2D || fam == FAM_PLANE3D_SPH || fam == FAM_POSE3DOF || fam == FAM_POSE6DOF ||
-           fam == FAM_RAYS3D;
+           fam == FAM_RAYS3D || fam == FAM_POINTSET2D;
 }
 
 }  // namespace gv

@@ -345,6 +345,7 @@ static unsigned wide_blocks(int64_t nt) {
 #define GV_DISPATCH_WIDE(fam, CALL)                                            \
     switch (fam) {                                                             \
     case FAM_POSE6DOF: { constexpr int FAMV = FAM_POSE6DOF; CALL; } break;     \
+    case FAM_POINTSET2D: { constexpr int FAMV = FAM_POINTSET2D; CALL; } break; \
     default: break;                                                            \
     }
 

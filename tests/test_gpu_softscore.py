@@ -24,6 +24,7 @@ CASES = [
     (inputs.POSE3DOF, lambda: inputs.pose3dof(n=4007, seed=43), [0.5, 0.5]),
     (inputs.POSE6DOF, lambda: inputs.pose6dof(n=1503, prior_deg=5.0, levels=5, seed=44), [0.1, 0.1]),
     (inputs.RAYS3D, lambda: inputs.rays3d(n=4001, seed=45), [0.01, 0.01]),
+    (inputs.POINTSET2D, lambda: inputs.pointset2d(m=60, eps=0.02, seed=46), [0.02, 0.02]),
 ]
 
 
