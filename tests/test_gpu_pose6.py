@@ -4,9 +4,10 @@
 Depth, best leaf, best point and inlier mask must be bit-exact in both precision
 modes; the per-cell UB/LB trace of an unpruned search equals the oracle's; with
 grouping and with small expansion steps the results do not change.  The
-configuration-size reading (5,000 matches, 250 inliers, a +-5 deg rotation prior,
-10 m translation box, 7 levels) is compared with a complete oracle solve stored by
-tests/golden/make_full_eps.py (or recomputed when the input bits differ).
+configuration (5,000 matches, 250 inliers, a +-30 deg rotation prior, 10 m
+translation box, 7 levels) and the same with a +-5 deg prior are compared with
+complete oracle solves stored by tests/golden/make_full_eps.py (or recomputed when
+the input bits differ).
 """
 import json
 import os
@@ -107,11 +108,12 @@ def test_cell_counts_replay_equals_oracle():
             assert np.array_equal(v.mask_words_to_numpy(reach), oreach)
 
 
-def test_configuration_size_bit_exact_against_the_oracle():
+@pytest.mark.parametrize("name", ["pose6dof_prior5_n5000", "pose6dof_n5000"])
+def test_configuration_size_bit_exact_against_the_oracle(name):
     from golden import make_full_eps
     from paper_2107_11810_gb300 import vote
-    case = make_full_eps.CASES["pose6dof_prior5_n5000"]
-    with open(os.path.join(os.path.dirname(__file__), "golden", "pose6dof_prior5_n5000.json")) as f:
+    case = make_full_eps.CASES[name]
+    with open(os.path.join(os.path.dirname(__file__), "golden", name + ".json")) as f:
         gold = json.load(f)
     p = case["make"]()
     if make_full_eps.params_sha256(p.params) == gold["params_sha256"]:
