@@ -68,7 +68,7 @@
 #define GVO_MAXL 40
 
 enum { GVO_LINE2D = 1, GVO_PLANE3D_SPH = 2, GVO_POSE3DOF = 3, GVO_POSE6DOF = 4, GVO_RAYS3D = 5,
-       GVO_POINTSET2D = 6 };
+       GVO_POINTSET2D = 6, GVO_AFFINE4D = 7 };
 enum { GVO_NO_MERGE = 1, GVO_NO_PRUNE = 2, GVO_REVERSE = 4 };
 
 /* ------------------------------------------------------------------------- */
@@ -192,6 +192,7 @@ static int family_shape(int fam, int d, int k, int *le, int *np)
     case GVO_POSE6DOF:    if (d != 6 || k != 4) return 1; *le = 11; *np = 5; return 0;
     case GVO_RAYS3D:      if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
     case GVO_POINTSET2D:  if (d != 4 || k != 2) return 1; *le = 2; *np = 4; return 0;
+    case GVO_AFFINE4D:    if (d != 4 || k != 3) return 1; *le = 3; *np = 4; return 0;
     default: return 1;
     }
 }
@@ -221,6 +222,11 @@ static void family_sigma(const gvo_problem *p, const double *h, double *sigma)
     case GVO_POINTSET2D:  /* u, v multiply c in one equation and d in the other */
         sigma[0] = h[0] > h[1] ? h[0] : h[1];
         sigma[1] = sigma[0];
+        break;
+    case GVO_AFFINE4D:    /* b = x4 - sum_i x_i a_i: x_i multiplies a_i */
+        sigma[0] = h[0];
+        sigma[1] = h[1];
+        sigma[2] = h[2];
         break;
     case GVO_POSE6DOF: {  /* F = sum_m t_m psi_m with psi = entries of R(phi) and z */
         /* An entry R_ki of R(phi) has gradient e_k . (J e_a x R e_i) along phi_a, J the
@@ -309,7 +315,7 @@ static double cell_center(const gvo_problem *p, int l, int j, int64_t i)
 /* ------------------------------------------------------------------------- */
 /* Families (Sec. 3 Eq. 2 line duality; Sec. 4.1 plane fitting; 3DoF posing;   */
 /* Sec. 4.2.3 calibrated 6DoF posing; Sec. 4.3 rays in 3-space; Sec. 4.4      */
-/* point-set similarity alignment).                                           */
+/* point-set similarity alignment; Sec. 4.1 affine hyperplanes in 4-space).   */
 /* ------------------------------------------------------------------------- */
 
 /* Rotation matrix (row-major) of the axis-angle vector ph, theta = |ph|, by
@@ -350,6 +356,9 @@ static void family_basis(const gvo_problem *p, int l, const int64_t *i, double *
     case GVO_POINTSET2D:
         psi[0] = cell_center(p, l, 0, i[0]);                  /* c */
         psi[1] = cell_center(p, l, 1, i[1]);                  /* d */
+        break;
+    case GVO_AFFINE4D:
+        for (int j = 0; j < 3; ++j) psi[j] = cell_center(p, l, j, i[j]);   /* a_1, a_2, a_3 */
         break;
     case GVO_PLANE3D_SPH: {
         double th = cell_center(p, l, 0, i[0]);
@@ -413,6 +422,13 @@ static void family_lift(const gvo_problem *p, const double *params, int64_t n, i
         r->t[0] = a; r->t[1] = cc;
         r->f[0] = (a * psi[0] + b) - c[1];
         r->f[1] = (cc * psi[0] + dd) - c[2];
+        break;
+    }
+    case GVO_AFFINE4D: {                    /* point x -> dual hyperplane b = x4 - a . (x1, x2, x3) */
+        double x1 = params[0 * n + i], x2 = params[1 * n + i], x3 = params[2 * n + i];
+        double x4 = params[3 * n + i];
+        r->t[0] = x1; r->t[1] = x2; r->t[2] = x3;
+        r->f[0] = (((x4 - x1 * psi[0]) - x2 * psi[1]) - x3 * psi[2]) - c[3];
         break;
     }
     case GVO_POINTSET2D: {
@@ -484,7 +500,7 @@ static void child_geometry(const gvo_problem *p, int l, const int64_t *i, const 
             g->shift[j] = 0.0;
         }
     }
-    if (p->fam == GVO_LINE2D || p->fam == GVO_RAYS3D || p->fam == GVO_POINTSET2D) {
+    if (p->fam == GVO_LINE2D || p->fam == GVO_RAYS3D || p->fam == GVO_POINTSET2D || p->fam == GVO_AFFINE4D) {
         for (int m = 0; m < p->nb; ++m) g->dpsi[m] = g->shift[m];   /* psi is linear: exact shift */
     } else {
         double psi_child[GVO_MAXT];
@@ -512,6 +528,9 @@ static void family_residual(const gvo_problem *p, const double *f, const double 
     case GVO_RAYS3D:
         fo[0] = (f[0] + t[0] * g->dpsi[0]) - g->shift[1];
         fo[1] = (f[1] + t[1] * g->dpsi[0]) - g->shift[2];
+        break;
+    case GVO_AFFINE4D:
+        fo[0] = (f[0] - ((t[0] * g->dpsi[0] + t[1] * g->dpsi[1]) + t[2] * g->dpsi[2])) - g->shift[3];
         break;
     case GVO_POINTSET2D:
         fo[0] = (f[0] - (t[0] * g->dpsi[0] + t[1] * g->dpsi[1])) - g->shift[2];
@@ -550,6 +569,11 @@ static void family_lipschitz(const gvo_problem *p, const double *t, double *lam)
     case GVO_RAYS3D:                        /* dy/dx = a, dz/dx = c */
         lam[0] = fabs(t[0]);
         lam[1] = fabs(t[1]);
+        break;
+    case GVO_AFFINE4D:                      /* db/da_i = -x_i */
+        lam[0] = fabs(t[0]);
+        lam[1] = fabs(t[1]);
+        lam[2] = fabs(t[2]);
         break;
     case GVO_POINTSET2D:                    /* da/dc = -u, da/dd = -v, db/dc = -v, db/dd = u */
         lam[0] = fabs(t[0]);

@@ -11,7 +11,7 @@ import itertools
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D = 1, 2, 3, 4, 5, 6
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D = 1, 2, 3, 4, 5, 6, 7
 
 
 def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.ndarray:
@@ -32,6 +32,9 @@ def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.n
         fx = w1 - (a * np.cos(yaw) - b * np.sin(yaw))
         fy = w2 - (a * np.sin(yaw) + b * np.cos(yaw))
         return np.stack([x - fx, y - fy], axis=-1)
+    if family == AFFINE4D:               # hyperplane x4 = a . x + b in dual form (Sec. 4.1)
+        x = np.asarray(params[0:3], float)
+        return (pts[:, 3:4] - (params[3][None, :] - pts[:, 0:3] @ x))[..., None]
     if family == POINTSET2D:             # (a, b) solving q = [[a, b], [-b, a]] p + (c, d) (Sec. 4.4)
         px, py, qx, qy = params
         c, d, a, b = pts[:, 0:1], pts[:, 1:2], pts[:, 2:3], pts[:, 3:4]

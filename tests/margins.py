@@ -28,7 +28,7 @@ import numpy as np
 import brute
 import oracle
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D = 1, 2, 3, 4, 5, 6
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D = 1, 2, 3, 4, 5, 6, 7
 
 
 def _rot(x):
@@ -51,6 +51,8 @@ def basis(family: int, x: np.ndarray) -> np.ndarray:
         return np.stack([np.cos(x[..., 0]), np.sin(x[..., 0])], axis=-1)
     if family == RAYS3D:            # y = a x + b, z = c x + d: a and c multiply x
         return np.concatenate([x[..., 0:1], x[..., 0:1]], axis=-1)
+    if family == AFFINE4D:          # b = x4 - sum_i x_i a_i: t_i multiplies -a_i
+        return -x[..., 0:3].copy()
     if family == POINTSET2D:        # a = g_a - u c - v d, b = g_b - v c + u d; t = (u, v)
         c, d = x[..., 0:1], x[..., 1:2]
         return np.concatenate([-c, -d, d, -c], axis=-1)
@@ -81,6 +83,8 @@ def t_part(family: int, t: np.ndarray, x: np.ndarray) -> np.ndarray:
     if family == POINTSET2D:
         t = np.asarray(t, float)
         return np.stack([psi[..., :2] @ t, psi[..., 2:] @ t], axis=-1)
+    if family == AFFINE4D:
+        return (psi @ np.asarray(t, float))[..., None]
     if family == POSE6DOF:
         t = np.asarray(t, float)
         return np.stack([psi[..., :11] @ t, psi[..., 11:] @ t], axis=-1)

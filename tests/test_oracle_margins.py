@@ -6,7 +6,7 @@ surface happens to sit inside that margin.  Here each margin is checked on its
 own, against the surface equations (tests/margins.py), on the level structures
 of the benchmark workloads (2D line eps 0.01, 3D plane eps 0.005, 3DoF camera
 0.25 m / 0.5 deg, 6DoF camera with a +-30 deg rotation prior in a 10 m box, 7
-levels, rays in the unit cube eps 0.002, point sets eps 0.01):
+levels, rays in the unit cube eps 0.002, point sets eps 0.01, affine hyperplanes in 4-space eps 0.01):
 
 * sigma_m bounds the change of every basis function across every level's cells
   (Sec. 3.2: the essential parameters are rounded to a step scaled by how much
@@ -33,6 +33,7 @@ WORKLOADS = {
     "pose6": lambda: inputs.pose6dof(n=400, seed=inputs.SEED_BASE + 4),
     "rays": lambda: inputs.rays3d(n=400, seed=inputs.SEED_BASE + 5),
     "points": lambda: inputs.pointset2d(m=20, seed=inputs.SEED_BASE + 6),
+    "affine": lambda: inputs.affine4d(n=400, seed=inputs.SEED_BASE + 7),
 }
 
 
@@ -58,6 +59,9 @@ def essential_samples(p, rng):
     elif p.family == inputs.RAYS3D:
         ts = [p.params[[0, 2], i] for i in rng.choice(p.n, 20, replace=False)]
         ts += [np.array(v, float) for v in ([2, -2], [0, 1], [-1.5, 0])]
+    elif p.family == inputs.AFFINE4D:
+        ts = [p.params[0:3, i] for i in rng.choice(p.n, 20, replace=False)]
+        ts += [np.array(v, float) for v in ([1, 1, 1], [1, -1, 0], [0, 0, 1])]
     elif p.family == inputs.POINTSET2D:         # t = p / |p|^2
         ts = []
         for i in rng.choice(p.n, 20, replace=False):

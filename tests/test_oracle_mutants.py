@@ -51,6 +51,8 @@ MUTANTS = {
     "points_residual_sign": ("fo[1] = (f[1] - (t[1] * g->dpsi[0] - t[0] * g->dpsi[1])) - g->shift[3];",
                              "fo[1] = (f[1] - (t[1] * g->dpsi[0] + t[0] * g->dpsi[1])) - g->shift[3];"),
     "points_sigma_one_axis": ("sigma[0] = h[0] > h[1] ? h[0] : h[1];", "sigma[0] = h[1] * 0.5;"),
+    "affine_residual_index": ("+ t[2] * g->dpsi[2])) - g->shift[3];", "+ t[2] * g->dpsi[1])) - g->shift[3];"),
+    "affine_sigma_one_axis": ("sigma[2] = h[2];\n        break;", "sigma[2] = h[0] * 0.25;\n        break;"),
     "pose6_residual_row": ("double sy2 = (t[0] * d[3] + t[1] * d[4]) + t[2] * d[5];",
                            "double sy2 = (t[0] * d[0] + t[1] * d[1]) + t[2] * d[2];"),
     "pose6_rotation_sign": ("R[1] = b0 * ph[1] - a2;", "R[1] = b0 * ph[1] + a2;"),
@@ -70,6 +72,7 @@ CASES = {
     inputs.POSE6DOF: lambda s: inputs.pose6dof(n=80, inlier_frac=0.3, levels=3, seed=s),
     inputs.RAYS3D: lambda s: inputs.rays3d(n=300, inlier_frac=0.3, eps=0.03, noise=0.002, seed=s),
     inputs.POINTSET2D: lambda s: inputs.pointset2d(m=14, eps=0.08, noise=0.002, seed=s),
+    inputs.AFFINE4D: lambda s: inputs.affine4d(n=150, inlier_frac=0.3, eps=0.15, noise=0.005, seed=s),
 }
 
 
@@ -104,6 +107,8 @@ def pins_hold(lib, fam, seed):
         free = (np.maximum(np.abs(p.params[0]), np.abs(p.params[2])).max() + st) * hL[: p.k].sum()
     elif p.family == inputs.POINTSET2D:
         free = ((1.0 / np.hypot(p.params[0], p.params[1])).max() + st) * hL[: p.k].sum()
+    elif p.family == inputs.AFFINE4D:
+        free = (np.abs(p.params[0:3]).max() + st) * hL[: p.k].sum()
     else:
         c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
         free = ((((1.0 + c) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st) * hL[0:3].sum()
@@ -125,6 +130,7 @@ MARGIN_CASES = {
     inputs.POSE6DOF: lambda: inputs.pose6dof(n=200, seed=inputs.SEED_BASE + 4),
     inputs.RAYS3D: lambda: inputs.rays3d(n=200, seed=inputs.SEED_BASE + 5),
     inputs.POINTSET2D: lambda: inputs.pointset2d(m=15, seed=inputs.SEED_BASE + 6),
+    inputs.AFFINE4D: lambda: inputs.affine4d(n=200, seed=inputs.SEED_BASE + 7),
 }
 MARGIN_T = {
     inputs.LINE2D: [np.array([1.0]), np.array([0.3])],
@@ -134,6 +140,7 @@ MARGIN_T = {
                                                    [3, -14, 2, 1, -5, 0.5, 2, -9, 1, 0.4, 0.6])],
     inputs.RAYS3D: [np.array(v, float) for v in ([2, -2], [0.3, 1.7])],
     inputs.POINTSET2D: [np.array(v, float) for v in ([4, 0], [1.5, -2.5])],
+    inputs.AFFINE4D: [np.array(v, float) for v in ([1, 1, 1], [0.2, -0.9, 0.5])],
 }
 
 
@@ -172,7 +179,7 @@ def test_planted_mistake_is_caught(name):
 @pytest.mark.parametrize("name", [m for m in sorted(MUTANTS) if m.startswith(("plane_sigma", "plane_lipschitz",
                                                                                "pose_lipschitz", "pose_sigma",
                                                                                "pose6_lipschitz", "pose6_sigma",
-                                                                               "rays_lipschitz", "points_sigma",
+                                                                               "rays_lipschitz", "points_sigma", "affine_sigma",
                                                                                "error_step"))])
 def test_margin_mistake_is_caught_by_the_margin_pins(name):
     old, new = MUTANTS[name]

@@ -17,8 +17,8 @@ import brute
 import oracle
 from paper_2107_11810_gb300 import inputs
 
-L2, PL, P3, P6, RY, PS = (oracle.LINE2D, oracle.PLANE3D_SPH, oracle.POSE3DOF, oracle.POSE6DOF, oracle.RAYS3D,
-                          oracle.POINTSET2D)
+L2, PL, P3, P6, RY, PS, AF = (oracle.LINE2D, oracle.PLANE3D_SPH, oracle.POSE3DOF, oracle.POSE6DOF,
+                              oracle.RAYS3D, oracle.POINTSET2D, oracle.AFFINE4D)
 
 
 def small_plane(n, seed, eps=0.08, frac=0.3):
@@ -47,6 +47,10 @@ def small_points(m, seed, eps=0.08):
     return inputs.pointset2d(m=m, eps=eps, noise=0.002, seed=seed)
 
 
+def small_affine(n, seed, eps=0.15, frac=0.3):
+    return inputs.affine4d(n=n, inlier_frac=frac, eps=eps, noise=0.005, seed=seed)
+
+
 CASES = [
     ("line", lambda s: small_line(300, s, eps=0.02)),
     ("plane", lambda s: small_plane(120, s)),
@@ -54,6 +58,7 @@ CASES = [
     ("pose6", lambda s: small_pose6(80, s)),
     ("rays", lambda s: small_rays(300, s)),
     ("points", lambda s: small_points(14, s)),
+    ("affine", lambda s: small_affine(150, s)),
 ]
 
 
@@ -161,6 +166,8 @@ def relaxed_eps(p, lv):
         lam = np.maximum(np.abs(p.params[0]), np.abs(p.params[2])).max() + st
     elif p.family == PS:       # |u| = |v| bound: 1/|p|
         lam = (1.0 / np.hypot(p.params[0], p.params[1])).max() + st
+    elif p.family == AF:       # |db/da_i| = |x_i| <= 1
+        lam = np.abs(p.params[0:3]).max() + st
     else:          # |dF/dphi_a| <= (1 + max(|xi|, |eta|)) |w|, |dF/dz| <= max(|xi|, |eta|)
         c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
         lam_phi = ((1.0 + c) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st
@@ -249,7 +256,8 @@ def test_trace_counts_equal_replay_and_monotone(name, mk):
 
 def test_empty_input():
     for mk in (lambda: small_line(10, 1), lambda: small_plane(10, 1), lambda: small_pose(10, 1),
-               lambda: small_pose6(10, 1), lambda: small_rays(10, 1), lambda: small_points(3, 1)):
+               lambda: small_pose6(10, 1), lambda: small_rays(10, 1), lambda: small_points(3, 1),
+               lambda: small_affine(10, 1)):
         p = mk()
         r = oracle.solve(p.family, p.eps, p.bounds, p.params[:, :0])
         assert r["depth"] == 0
