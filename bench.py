@@ -62,6 +62,8 @@ WORKLOADS = {
     "pointset2d_m300": dict(make=lambda: inputs.pointset2d(m=300), desc="point-set similarity alignment, two sets of "
                             "300 points (B = s R A + t + N(0, 0.002)), all 90,000 pairs as surfaces, eps 0.01, "
                             "(c,d,a,b) space"),
+    "affine4d_n1e4": dict(make=lambda: inputs.affine4d(), desc="hyperplane fitting in 4-space (affine form), 1e4 "
+                          "points, 5% on a hyperplane (N(0, 0.002) in x4), eps 0.02, (a1,a2,a3,b) space"),
     "pose3dof_batch256": dict(make=lambda: inputs.pose3dof_batch(), batched=True,
                               desc="256 independent 3DoF problems, n log-uniform in [1e3, 1e6], inlier ratio "
                                    "U[0.5%, 5%]; one vote_solve_batched call per step"),
@@ -69,7 +71,7 @@ WORKLOADS = {
 # FP32-pipe instructions per (child cell, canonical surface) test, counted from
 # the formulas of each family's residual and comparisons
 INSTR_PER_TEST = {inputs.LINE2D: 7, inputs.PLANE3D_SPH: 10, inputs.POSE3DOF: 14, inputs.POSE6DOF: 30,
-                  inputs.RAYS3D: 10, inputs.POINTSET2D: 10}
+                  inputs.RAYS3D: 10, inputs.POINTSET2D: 10, inputs.AFFINE4D: 10}
 
 
 def env_rank():

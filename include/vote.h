@@ -79,14 +79,19 @@ typedef enum {
  *                    hypothetical correspondence p -> q under q_x = a p_x + b p_y
  *                    + c, q_y = -b p_x + a p_y + d (point-set similarity
  *                    alignment, Sec. 4.4); surfaces a = (p . (q - (c, d)))/|p|^2,
- *                    b = (p_y (q_x - c) - p_x (q_y - d))/|p|^2; 16 children. */
+ *                    b = (p_y (q_x - c) - p_x (q_y - d))/|p|^2; 16 children.
+ *   VOTE_AFFINE4D    d=4 k=3: coords (a1, a2, a3, b); input rows (x1, x2, x3, x4)
+ *                    of points of 4-space; surface b = x4 - (a1 x1 + a2 x2 + a3 x3)
+ *                    (hyperplane fitting in the affine form, Sec. 4.1);
+ *                    16 children. */
 typedef enum {
     VOTE_LINE2D = 1,
     VOTE_PLANE3D_SPH = 2,
     VOTE_POSE3DOF = 3,
     VOTE_POSE6DOF = 4,
     VOTE_RAYS3D = 5,
-    VOTE_POINTSET2D = 6
+    VOTE_POINTSET2D = 6,
+    VOTE_AFFINE4D = 7
 } vote_family;
 
 /* Options for vote_set_option. */

@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import torch
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D = 1, 2, 3, 4, 5, 6
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D = 1, 2, 3, 4, 5, 6, 7
 
 
 def rotation(phi: torch.Tensor) -> torch.Tensor:
@@ -48,6 +48,8 @@ def residuals(family: int, params: torch.Tensor, p: torch.Tensor) -> torch.Tenso
         rx = p[1] - (w1 - (a * c - b * s))
         ry = p[2] - (w2 - (a * s + b * c))
         return torch.stack([rx, ry], dim=1)
+    if family == AFFINE4D:                     # b = x4 - a . (x1, x2, x3)
+        return (p[3] - (params[3] - (p[0] * params[0] + p[1] * params[1] + p[2] * params[2])))[:, None]
     if family == POINTSET2D:                   # (a, b) solving q = [[a, b], [-b, a]] p + (c, d)
         px, py, qx, qy = params[0], params[1], params[2], params[3]
         n2 = px * px + py * py

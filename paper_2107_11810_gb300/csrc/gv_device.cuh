@@ -148,7 +148,8 @@ __device__ __forceinline__ uint64_t child_key(const Problem &P, uint64_t key, in
 // LINEAR_BASIS: the basis is the free coordinate itself; LINEAR_TAIL: the last
 // basis value is the last free coordinate (its change is the exact child shift).
 // ---------------------------------------------------------------------------
-enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3, FAM_POSE6DOF = 4, FAM_RAYS3D = 5, FAM_POINTSET2D = 6 };
+enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3, FAM_POSE6DOF = 4, FAM_RAYS3D = 5, FAM_POINTSET2D = 6,
+       FAM_AFFINE4D = 7 };
 
 template <int FAM> struct Fam;
 
@@ -306,6 +307,53 @@ template <> struct Fam<FAM_RAYS3D> {
     __device__ static void radius32(const Level &lev, const float *qt, float *R) {
         R[0] = __fmaf_rn(lev.lam_c[0], fabsf(qt[0]), lev.rc0[0]);
         R[1] = __fmaf_rn(lev.lam_c[1], fabsf(qt[1]), lev.rc0[1]);
+    }
+};
+
+// AFFINE4D: hyperplanes x4 = a . (x1, x2, x3) + b in the affine form (Sec. 4.1,
+// d = 4); coords (a1, a2, a3, b), dual surface b = x4 - a . x.  t = (x1, x2, x3);
+// psi = (a1, a2, a3) (linear: their changes across a child shift are the shifts).
+template <> struct Fam<FAM_AFFINE4D> {
+    static constexpr int D = 4, K = 3, ND = 1, LE = 3, NP = 4, NB = 3, NFP = 4;
+    static constexpr bool LINEAR_BASIS = true, LINEAR_TAIL = false;
+    __host__ __device__ static constexpr bool uses(int, int) { return true; }
+    __device__ static void basis(const Problem &, const double *c, double *psi) {
+        psi[0] = c[0];
+        psi[1] = c[1];
+        psi[2] = c[2];
+    }
+    __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
+                                double *f, double *t) {
+        const double x1 = prm[i], x2 = prm[n + i], x3 = prm[2 * n + i], x4 = prm[3 * n + i];
+        t[0] = x1;
+        t[1] = x2;
+        t[2] = x3;
+        f[0] = dsub(dsub(dsub(dsub(x4, dmul(x1, psi[0])), dmul(x2, psi[1])), dmul(x3, psi[2])), c[3]);
+    }
+    __device__ static double tsum(const double *t, const double *dpsi) {
+        return dadd(dadd(dmul(t[0], dpsi[0]), dmul(t[1], dpsi[1])), dmul(t[2], dpsi[2]));
+    }
+    __device__ static void residual64(const double *f, const double *t, const double *dpsi, const double *sh,
+                                      double *fo) {
+        fo[0] = dsub(dsub(f[0], tsum(t, dpsi)), sh[3]);
+    }
+    __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
+        p[0] = dsub(f[0], tsum(t, dpsi));
+    }
+    __device__ static void lipschitz64(const double *t, double *lam) {
+        lam[0] = fabs(t[0]);
+        lam[1] = fabs(t[1]);
+        lam[2] = fabs(t[2]);
+    }
+    __device__ static void coef(const double *dpsi, double *g) {
+        g[0] = -dpsi[0];
+        g[1] = -dpsi[1];
+        g[2] = -dpsi[2];
+    }
+    // sum_i |x_i| h1_i = sum_i lam_c[i] |q_i|
+    __device__ static void radius32(const Level &lev, const float *qt, float *R) {
+        R[0] = __fmaf_rn(lev.lam_c[0], fabsf(qt[0]),
+                         __fmaf_rn(lev.lam_c[1], fabsf(qt[1]), __fmaf_rn(lev.lam_c[2], fabsf(qt[2]), lev.rc0[0])));
     }
 };
 

@@ -123,6 +123,7 @@ static int family_shape(int fam, int d, int k, int *le, int *np) {
     case VOTE_POSE6DOF: if (d != 6 || k != 4) return 1; *le = 11; *np = 5; return 0;
     case VOTE_RAYS3D: if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
     case VOTE_POINTSET2D: if (d != 4 || k != 2) return 1; *le = 2; *np = 4; return 0;
+    case VOTE_AFFINE4D: if (d != 4 || k != 3) return 1; *le = 3; *np = 4; return 0;
     default: return 1;
     }
 }
@@ -143,6 +144,11 @@ static void family_sigma(int fam, const double *h, double *sigma) {
     case VOTE_RAYS3D:       // a and c multiply x
         sigma[0] = h[0];
         sigma[1] = h[0];
+        break;
+    case VOTE_AFFINE4D:     // x_i multiplies a_i
+        sigma[0] = h[0];
+        sigma[1] = h[1];
+        sigma[2] = h[2];
         break;
     case VOTE_POINTSET2D:   // u, v multiply c in one equation and d in the other
         sigma[0] = h[0] > h[1] ? h[0] : h[1];
@@ -290,6 +296,9 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
             v.lam_c[0] = (float)(h[l + 1][0] * s_t[l][0] / P.s_f[0]);
             v.lam_c[1] = (float)(h[l + 1][0] * s_t[l][1] / P.s_f[1]);
             break;
+        case VOTE_AFFINE4D:      // sum_i |x_i| h1_i
+            for (int m = 0; m < 3; ++m) v.lam_c[m] = (float)(h[l + 1][m] * s_t[l][m] / P.s_f[0]);
+            break;
         case VOTE_POINTSET2D:    // a: |u| h1_c + |v| h1_d; b: |v| h1_c + |u| h1_d
             v.lam_c[0] = (float)(h[l + 1][0] * s_t[l][0] / P.s_f[0]);
             v.lam_c[1] = (float)(h[l + 1][1] * s_t[l][1] / P.s_f[0]);
@@ -328,6 +337,7 @@ static void lambda_max(int fam, const double *T, double *lam) {
     case VOTE_POSE3DOF: lam[0] = lam[1] = std::sqrt(T[0] * T[0] + T[1] * T[1]); break;
     case VOTE_RAYS3D: lam[0] = T[0]; lam[1] = T[1]; break;
     case VOTE_POINTSET2D: lam[0] = T[0]; lam[1] = T[1]; lam[2] = T[1]; lam[3] = T[0]; break;
+    case VOTE_AFFINE4D: lam[0] = T[0]; lam[1] = T[1]; lam[2] = T[2]; break;
     case VOTE_POSE6DOF: {
         const double nw = std::sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
         const double nxw = std::sqrt(T[3] * T[3] + T[4] * T[4] + T[5] * T[5]);
@@ -419,6 +429,7 @@ static int family_nfp(int fam) {
     case VOTE_POSE3DOF: return Fam<FAM_POSE3DOF>::NFP;
     case VOTE_RAYS3D: return Fam<FAM_RAYS3D>::NFP;
     case VOTE_POINTSET2D: return Fam<FAM_POINTSET2D>::NFP;
+    case VOTE_AFFINE4D: return Fam<FAM_AFFINE4D>::NFP;
     default: return Fam<FAM_POSE6DOF>::NFP;
     }
 }
@@ -429,12 +440,14 @@ static int family_nb(int fam) {
     case VOTE_POSE3DOF: return Fam<FAM_POSE3DOF>::NB;
     case VOTE_RAYS3D: return Fam<FAM_RAYS3D>::NB;
     case VOTE_POINTSET2D: return Fam<FAM_POINTSET2D>::NB;
+    case VOTE_AFFINE4D: return Fam<FAM_AFFINE4D>::NB;
     default: return Fam<FAM_POSE6DOF>::NB;
     }
 }
 static_assert((int)VOTE_LINE2D == FAM_LINE2D && (int)VOTE_PLANE3D_SPH == FAM_PLANE3D_SPH &&
                   (int)VOTE_POSE3DOF == FAM_POSE3DOF && (int)VOTE_POSE6DOF == FAM_POSE6DOF &&
-                  (int)VOTE_RAYS3D == FAM_RAYS3D && (int)VOTE_POINTSET2D == FAM_POINTSET2D,
+                  (int)VOTE_RAYS3D == FAM_RAYS3D && (int)VOTE_POINTSET2D == FAM_POINTSET2D &&
+                  (int)VOTE_AFFINE4D == FAM_AFFINE4D,
               "family numbers");
 
 // bytes of one record of level l (its format is fixed per solve by finalize_levels)

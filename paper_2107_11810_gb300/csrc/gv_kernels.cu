@@ -592,6 +592,7 @@ static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs
     case FAM_RAYS3D: { constexpr int FAMV = FAM_RAYS3D; CALL; } break;           \
     case FAM_POSE6DOF: { constexpr int FAMV = FAM_POSE6DOF; CALL; } break;       \
     case FAM_POINTSET2D: { constexpr int FAMV = FAM_POINTSET2D; CALL; } break;   \
+    case FAM_AFFINE4D: { constexpr int FAMV = FAM_AFFINE4D; CALL; } break;       \
     default: break;                                                 \
     }
 

@@ -142,6 +142,18 @@ template <> struct SoftFam<FAM_RAYS3D> {       // r_y = y - (a x + b), r_z = z -
     }
 };
 
+// r = b - (x4 - a . x)
+template <> struct SoftFam<FAM_AFFINE4D> {
+    static constexpr int D = 4, ND = 1, NP = 4;
+    __device__ static void eval(const double *prm, int64_t n, int64_t i, const double *p, double *r, double *dp,
+                                double *dq) {
+        const double x1 = prm[i], x2 = prm[n + i], x3 = prm[2 * n + i], x4 = prm[3 * n + i];
+        r[0] = p[3] - (x4 - ((p[0] * x1 + p[1] * x2) + p[2] * x3));
+        dp[0] = x1; dp[1] = x2; dp[2] = x3; dp[3] = 1.0;
+        dq[0] = p[0]; dq[1] = p[1]; dq[2] = p[2]; dq[3] = -1.0;
+    }
+};
+
 // r_a = a - (p_x (q_x - c) + p_y (q_y - d)) / |p|^2, r_b = b - (p_y (q_x - c) - p_x (q_y - d)) / |p|^2
 template <> struct SoftFam<FAM_POINTSET2D> {
     static constexpr int D = 4, ND = 2, NP = 4;
@@ -263,7 +275,7 @@ void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uin
     a.partial = partial;
     for (int j = 0; j < nd; ++j) a.inv_tol2[j] = inv_tol2[j];
     int nb = ss_blocks(n);
-    int d = fam == FAM_LINE2D ? 2 : (fam == FAM_POSE6DOF ? 6 : (fam == FAM_POINTSET2D ? 4 : 3));
+    int d = fam == FAM_LINE2D ? 2 : (fam == FAM_POSE6DOF ? 6 : ((fam == FAM_POINTSET2D || fam == FAM_AFFINE4D) ? 4 : 3));
     switch (fam) {
     case FAM_LINE2D:
         if (bwd) k_softscore<FAM_LINE2D, true><<<nb, kSsThreads, 0, st>>>(a);
@@ -276,6 +288,10 @@ void launch_softscore(int fam, bool bwd, const double *prm, int64_t n, const uin
     case FAM_POSE3DOF:
         if (bwd) k_softscore<FAM_POSE3DOF, true><<<nb, kSsThreads, 0, st>>>(a);
         else k_softscore<FAM_POSE3DOF, false><<<nb, kSsThreads, 0, st>>>(a);
+        break;
+    case FAM_AFFINE4D:
+        if (bwd) k_softscore<FAM_AFFINE4D, true><<<nb, kSsThreads, 0, st>>>(a);
+        else k_softscore<FAM_AFFINE4D, false><<<nb, kSsThreads, 0, st>>>(a);
         break;
     case FAM_POINTSET2D:
         if (bwd) k_softscore<FAM_POINTSET2D, true><<<nb, kSsThreads, 0, st>>>(a);
@@ -297,7 +313,7 @@ int softscore_partial_doubles() { return kSsBlocks * GV_MAXD; }
 
 bool softscore_supported(int fam) {
     return fam == FAM_LINE2D || fam == FAM_PLANE3D_SPH || fam == FAM_POSE3DOF || fam == FAM_POSE6DOF ||
-           fam == FAM_RAYS3D || fam == FAM_POINTSET2D;
+           fam == FAM_RAYS3D || fam == FAM_POINTSET2D || fam == FAM_AFFINE4D;
 }
 
 }  // namespace gv

@@ -346,6 +346,7 @@ static unsigned wide_blocks(int64_t nt) {
     switch (fam) {                                                             \
     case FAM_POSE6DOF: { constexpr int FAMV = FAM_POSE6DOF; CALL; } break;     \
     case FAM_POINTSET2D: { constexpr int FAMV = FAM_POINTSET2D; CALL; } break; \
+    case FAM_AFFINE4D: { constexpr int FAMV = FAM_AFFINE4D; CALL; } break;     \
     default: break;                                                            \
     }
 

@@ -27,6 +27,9 @@ Surface parameters are FP64, structure-of-arrays ``params[P, n]``:
 * ``POINTSET2D``  (point-set similarity alignment, Sec. 4.4): P = 4, rows (px, py, qx, qy)
   of a hypothetical correspondence p -> q under q_x = a p_x + b p_y + c,
   q_y = -b p_x + a p_y + d; voting space (c, d, a, b).
+* ``AFFINE4D``    (hyperplane fitting in the affine form, Sec. 4.1, d = 4): P = 4, rows
+  (x1, x2, x3, x4) of points; voting space (a1, a2, a3, b) with the dual hyperplane
+  b = x4 - (a1 x1 + a2 x2 + a3 x3).
 """
 from __future__ import annotations
 
@@ -35,11 +38,11 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D = 1, 2, 3, 4, 5, 6
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D = 1, 2, 3, 4, 5, 6, 7
 FAMILY_NAMES = {LINE2D: "LINE2D", PLANE3D_SPH: "PLANE3D_SPH", POSE3DOF: "POSE3DOF", POSE6DOF: "POSE6DOF",
-                RAYS3D: "RAYS3D", POINTSET2D: "POINTSET2D"}
+                RAYS3D: "RAYS3D", POINTSET2D: "POINTSET2D", AFFINE4D: "AFFINE4D"}
 FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1), POSE6DOF: (6, 4), RAYS3D: (3, 1),
-             POINTSET2D: (4, 2)}
+             POINTSET2D: (4, 2), AFFINE4D: (4, 3)}
 SEED_BASE = 2107118100
 
 
@@ -364,6 +367,29 @@ def pointset2d(m: int = 200, outlier_frac: float = 0.0, eps: float = 0.01, noise
                    dict(m=m, scale=s, theta=th))
 
 
+def affine4d(n: int = 10_000, inlier_frac: float = 0.05, eps: float = 0.02, noise: float = 0.002,
+             seed: int = SEED_BASE + 7) -> Problem:
+    """Points of R^4: (x1, x2, x3) uniform in [0, 1]^3; ``inlier_frac`` of them on a
+    hyperplane x4 = a . (x1, x2, x3) + b (a ~ U[-1, 1]^3, b ~ U[0, 1]) plus
+    N(0, noise) in x4, the rest with x4 ~ U[-1, 2] (a spread wider than a band of
+    width 2 eps holds by chance).  Voting domain a in [-1, 1]^3, b in [-4, 5]; eps
+    in every coordinate."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-1.0, 1.0, 3)
+    b = rng.uniform(0.0, 1.0)
+    n_in = int(round(n * inlier_frac))
+    x = rng.uniform(0.0, 1.0, (n, 3))
+    x4 = rng.uniform(-1.0, 2.0, n)
+    x4[:n_in] = x[:n_in] @ a + b + rng.normal(0.0, noise, n_in)
+    out = np.concatenate([x.T, x4[None]], axis=0)
+    perm = rng.permutation(n)
+    out = out[:, perm]
+    inliers = np.nonzero(perm < n_in)[0]
+    return Problem(AFFINE4D, np.full(4, eps), np.array([-1.0, 1.0, -1.0, 1.0, -1.0, 1.0, -4.0, 5.0]),
+                   np.ascontiguousarray(out), np.concatenate([a, [b]]), inliers, "affine4d",
+                   dict(inlier_frac=inlier_frac))
+
+
 # ---------------------------------------------------------------------------
 # Standard workloads
 # ---------------------------------------------------------------------------
@@ -389,4 +415,6 @@ def random_small(family: int, n: int, seed: int, inlier_frac: float = 0.3, **kw)
         return rays3d(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
     if family == POINTSET2D:
         return pointset2d(m=max(1, int(round(math.sqrt(n)))), seed=seed, **kw)
+    if family == AFFINE4D:
+        return affine4d(n=n, inlier_frac=inlier_frac, seed=seed, **kw)
     raise ValueError(family)

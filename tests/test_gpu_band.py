@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-FAMS = [inputs.LINE2D, inputs.PLANE3D_SPH, inputs.POSE3DOF, inputs.RAYS3D, inputs.POINTSET2D]
+FAMS = [inputs.LINE2D, inputs.PLANE3D_SPH, inputs.POSE3DOF, inputs.RAYS3D, inputs.POINTSET2D, inputs.AFFINE4D]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -51,6 +51,9 @@ def dyadic_problem(family, seed):
         return p, np.round(p.params * 64.0) / 64.0
     if family == inputs.POINTSET2D:
         p = inputs.pointset2d(m=50, eps=2.0 ** -5, noise=0.002, seed=seed)
+        return p, np.round(p.params * 64.0) / 64.0
+    if family == inputs.AFFINE4D:
+        p = inputs.affine4d(n=1500, inlier_frac=0.3, eps=2.0 ** -3, noise=0.005, seed=seed)
         return p, np.round(p.params * 64.0) / 64.0
     p = inputs.pose3dof(n=3000, inlier_frac=0.3, eps_xy=1.0, eps_yaw_deg=2.0, noise_deg=0.05, seed=seed)
     q = p.params.copy()

@@ -57,12 +57,14 @@ def small(family, n, seed):
         return inputs.plane3d(n=n, inlier_frac=0.2, eps=0.06, sigma=0.002, seed=seed)
     if family == inputs.RAYS3D:
         return inputs.rays3d(n=n, inlier_frac=0.2, eps=0.02, noise=0.002, seed=seed)
+    if family == inputs.AFFINE4D:
+        return inputs.affine4d(n=n, inlier_frac=0.3, eps=0.1, noise=0.005, seed=seed)
     if family == inputs.POINTSET2D:          # n ~ m^2 correspondences
         return inputs.pointset2d(m=max(1, int(round(n ** 0.5))), eps=0.05, noise=0.002, seed=seed)
     return inputs.pose3dof(n=n, inlier_frac=0.2, eps_xy=1.0, eps_yaw_deg=2.0, noise_deg=0.05, seed=seed)
 
 
-FAMS = [inputs.LINE2D, inputs.PLANE3D_SPH, inputs.POSE3DOF, inputs.RAYS3D, inputs.POINTSET2D]
+FAMS = [inputs.LINE2D, inputs.PLANE3D_SPH, inputs.POSE3DOF, inputs.RAYS3D, inputs.POINTSET2D, inputs.AFFINE4D]
 
 
 @pytest.mark.parametrize("family", FAMS)
@@ -106,6 +108,8 @@ def test_full_trace_without_pruning_equals_oracle(family):
     p = small(family, 300 if family != inputs.PLANE3D_SPH else 60, 5)
     if family == inputs.POINTSET2D:          # 16 children per cell: fewer levels keep the trace small
         p = inputs.pointset2d(m=10, eps=0.2, noise=0.002, seed=5)
+    if family == inputs.AFFINE4D:
+        p = inputs.affine4d(n=60, inlier_frac=0.3, eps=0.3, noise=0.005, seed=5)
     cap = 4_000_000
     o = oracle.solve(p.family, p.eps, p.bounds, p.params, flags=oracle.NO_PRUNE, trace_cap=cap)
     g = gpu_solve(p, 1, prune=False, trace_cap=cap)

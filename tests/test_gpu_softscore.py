@@ -25,6 +25,7 @@ CASES = [
     (inputs.POSE6DOF, lambda: inputs.pose6dof(n=1503, prior_deg=5.0, levels=5, seed=44), [0.1, 0.1]),
     (inputs.RAYS3D, lambda: inputs.rays3d(n=4001, seed=45), [0.01, 0.01]),
     (inputs.POINTSET2D, lambda: inputs.pointset2d(m=60, eps=0.02, seed=46), [0.02, 0.02]),
+    (inputs.AFFINE4D, lambda: inputs.affine4d(n=3001, eps=0.1, seed=47), [0.05]),
 ]
 
 

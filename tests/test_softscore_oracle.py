@@ -61,7 +61,8 @@ def test_oracle_gradients_match_central_differences():
                          (ss.POSE3DOF, lambda: inputs.pose3dof(n=200, seed=6), [2.0, 2.0]),
                          (ss.POSE6DOF, lambda: inputs.pose6dof(n=200, seed=7), [0.5, 0.5]),
                          (ss.RAYS3D, lambda: inputs.rays3d(n=200, seed=9), [0.05, 0.05]),
-                         (ss.POINTSET2D, lambda: inputs.pointset2d(m=15, seed=10), [0.05, 0.05])]:
+                         (ss.POINTSET2D, lambda: inputs.pointset2d(m=15, seed=10), [0.05, 0.05]),
+                         (ss.AFFINE4D, lambda: inputs.affine4d(n=200, seed=11), [0.05])]:
         prob = mk()
         prm = torch.from_numpy(prob.params.copy()).requires_grad_(True)
         p = torch.tensor(prob.truth, dtype=torch.float64) + 0.003
