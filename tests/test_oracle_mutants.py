@@ -24,7 +24,8 @@ import oracle
 from paper_2107_11810_gb300 import inputs
 
 MUTANTS = {
-    "plane_sign": ("t[1] * g->dpsi[1]) + t[2] * g->dpsi[2]", "t[1] * g->dpsi[1]) - t[2] * g->dpsi[2]"),
+    "plane_sign": ("(f[0] + ((t[0] * g->dpsi[0] + t[1] * g->dpsi[1]) + t[2] * g->dpsi[2]))",
+                   "(f[0] + ((t[0] * g->dpsi[0] + t[1] * g->dpsi[1]) - t[2] * g->dpsi[2]))"),
     "pose_index": ("fo[1] = (f[1] - (t[0] * g->dpsi[1] + t[1] * g->dpsi[0]))",
                    "fo[1] = (f[1] - (t[0] * g->dpsi[0] + t[1] * g->dpsi[1]))"),
     "line_residual_sign": ("fo[0] = (f[0] - t[0] * g->dpsi[0]) - g->shift[1];",
