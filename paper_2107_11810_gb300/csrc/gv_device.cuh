@@ -15,6 +15,7 @@
 // scaling of an FP64 value rounded once to FP32) and H_j the child shift in steps.
 #pragma once
 #include <cstdint>
+#include <cstring>
 
 #define GV_MAXD 6
 #define GV_MAXT 11
@@ -50,6 +51,9 @@ struct Level {                 // tests of the children of a level-l cell
     double gscale[GV_MAXD][GV_MAXT];  // s_t,m / s_f,j (a power of two)
     // FP32 screen constants, in units of s_f,j (dependent coordinate j)
     float Hs[GV_MAXD];         // h1 of dependent coordinate j
+    float Hs_lo[GV_MAXD];      // h1 / s_f,j - Hs rounded to FP32 (the double-float tier's low part)
+    int hs_exp;                // every split Hs is FP32-exact and a multiple of 2^hs_exp (<= 0), else
+                               // -1000
     float rc0[GV_MAXD];        // (eps_j + h1_j + A1_j): the radius without its Lipschitz term
     float lam_c[4];            // family-specific scale of the Lipschitz term (see Fam::radius32)
     float rho2;                // family-specific ratio of essential steps (planes: (s_t,z / s_t,x)^2)
@@ -113,6 +117,22 @@ __device__ __forceinline__ void vsincos(double x, double *sn, double *cs) {
     case 2: *sn = -ts; *cs = -tc; break;
     default: *sn = -tc; *cs = ts; break;
     }
+}
+
+// Exponent of the lowest set bit of a finite nonzero x: x is an odd multiple of
+// 2^lowbit_exp(x).
+__host__ __device__ __forceinline__ int lowbit_exp(double x) {
+    unsigned long long b;
+    memcpy(&b, &x, 8);
+    const int e = (int)((b >> 52) & 0x7ff);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (e) m |= 1ull << 52;
+    int z = 0;
+    while (!(m & 1ull)) {
+        m >>= 1;
+        ++z;
+    }
+    return (e ? e : 1) - 1075 + z;
 }
 
 // ---------------------------------------------------------------------------
@@ -528,5 +548,15 @@ template <> struct Fam<FAM_POSE6DOF> {
 constexpr float kU32 = 5.9604645e-08f;
 constexpr float kBandTest = 24.0f * kU32;
 constexpr float kBandSnap = 12.0f * kU32;
+// The double-float tier (a residual the FP32 screen left undecided, recomputed as
+// an unevaluated sum hi + lo of FP32 values with error-free products and sums,
+// Dekker 1971 / Knuth TAOCP 4.2.2): coefficients G64 = G + G_lo to 2^-48 relative,
+// at most 2 (LE + 1) roundings of a low part bounded by (LE + 6) u M_j, so its
+// value is within 2^-39 M_j + 2^-25 of the exact residual; the FP64 definition is
+// within 24 * 2^-53 M_j of it.  A snap is taken from the double-float value when it
+// is kBandDF M_j + kBandDFAbs away from a rounding tie (about 8 times both bounds;
+// kBandDFAbs also covers FP32 underflow of G_lo and of the product errors).
+constexpr float kBandDF = 1.4551915e-11f;      // 2^-36
+constexpr float kBandDFAbs = 9.5367432e-07f;   // 2^-20
 
 }  // namespace gv

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_EMIT) k_emit(const __grid_co
     float G[GF];
 #pragma unroll
     for (int i = 0; i < GF; ++i) G[i] = 0.0f;
-    unsigned nrechk = 0, bad = 0;
+    unsigned nrechk = 0, ndf = 0, bad = 0;
     int64_t gfail = -1;                                             // group whose copy did not arrive
 #pragma unroll 1
     for (int64_t g = g0; g < g1; ++g) {
@@ -136,12 +136,21 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_EMIT) k_emit(const __grid_co
                 }
             }
             const uint32_t mult = c.out.mult ? c.in.mult[r] : 1u;
-            float es[ND];                                               // the snap's band (steps)
+            float es[ND], bd[ND];                                       // the snaps' bands (steps)
+            bool xs[ND];                                                // FP32 residual exact
             if (PREC == 1) {
                 float M[ND];
+                // every term a multiple of 2^ex and M below 2^(24 + ex): the FP32 residual, and
+                // the definition's FP64 one, are exact, so a tie rounds to even in both
+                const int ex = min(__float2int_rn(G[GF - 1]), lev.hs_exp);
+                const float tq = ex > -100 ? __int_as_float((127 + 24 + ex) << 23) : 0.0f;
                 magnitudes<FAM>(qf, qt, G + NFS * ND * LE, hs, M);
 #pragma unroll
-                for (int j = 0; j < ND; ++j) es[j] = 0.5f - kBandSnap * M[j];
+                for (int j = 0; j < ND; ++j) {
+                    es[j] = 0.5f - kBandSnap * M[j];
+                    bd[j] = __fmaf_ru(kBandDF, M[j], kBandDFAbs);
+                    xs[j] = M[j] < tq;
+                }
             }
 #pragma unroll
             for (int fs = 0; fs < NFS; ++fs) {
@@ -165,19 +174,28 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_EMIT) k_emit(const __grid_co
                             const float y = ((ds >> j) & 1) ? u[j] - hs[j] : u[j] + hs[j];
                             if constexpr (QO16) {
                                 const float t = y + kMagic16;
-                                done &= fabsf(y - (t - kMagic16)) < es[j] && fabsf(y) < 32767.0f;
+                                done &= (fabsf(y - (t - kMagic16)) < es[j] || xs[j]) && fabsf(y) < 32767.0f;
                                 fb[j] = __float_as_uint(t);
                             } else {
                                 const float t = y + kMagic;
-                                done &= fabsf(y - (t - kMagic)) < es[j] && fabsf(y) < 4.0e6f;
+                                done &= (fabsf(y - (t - kMagic)) < es[j] || xs[j]) && fabsf(y) < 4.0e6f;
                                 fb[j] = (uint32_t)(__float_as_int(t) - 0x4B400000);
                             }
                         }
-                        nrechk += !done;
                     }
                     if (!done) {
-                        const int3 q = snap64_words<FAM, QI16>(&c.P, &c.lev, rec_words_of<NWI>(w), g64, s);
-                        bad |= (unsigned)(q.z != 0);
+                        int3 q = make_int3(0, 0, 0);
+                        if constexpr (PREC == 1) {                              // the double-float tier
+                            q = snap_df_words<FAM, QI16>(&c.lev, rec_words_of<NWI>(w), c.geo32 + (size_t)cl * GF,
+                                                         c.geo32lo + (size_t)cl * (NFS * ND * LE), s, bd[0],
+                                                         bd[ND - 1], QO16 ? 32767.0f : 1.0e9f);
+                            ++ndf;
+                        }
+                        if (!q.z) {                                             // the FP64 definition
+                            q = snap64_words<FAM, QI16>(&c.P, &c.lev, rec_words_of<NWI>(w), g64, s);
+                            bad |= (unsigned)(q.z != 0);
+                            nrechk += PREC == 1;
+                        }
                         const int qn[2] = {q.x, q.y};
 #pragma unroll
                         for (int j = 0; j < ND; ++j) {
@@ -209,9 +227,11 @@ __global__ void __launch_bounds__(256, GV_MINBLOCKS_EMIT) k_emit(const __grid_co
         }
     }
     nrechk = __reduce_add_sync(kFull, nrechk);
+    ndf = __reduce_add_sync(kFull, ndf);
     bad = __reduce_or_sync(kFull, bad);
     if (lane == 0) {
         if (nrechk) atomicAdd(&c.sc->rechecks, (unsigned long long)nrechk);
+        if (ndf) atomicAdd(&c.sc->rechecks_df, (unsigned long long)ndf);
         if (bad) atomicOr(&c.sc->err, bad << 1);
     }
 }

@@ -97,7 +97,7 @@ struct vote_ctx {
     int64_t trace_cap = 0;
     int64_t fault_alloc_at = 0, alloc_count = 0;
     LevelStore ls[GV_MAXL + 1];
-    DevBuf levs_dev, path, scal, alive, geo64, geo32, cnt, tinfo, ballot, tdst, child_idx, cursor, keepflag, recn, bsums;
+    DevBuf levs_dev, path, scal, alive, geo64, geo32, geo32lo, cnt, tinfo, ballot, tdst, child_idx, cursor, keepflag, recn, bsums;
     DevBuf tr_level, tr_key, tr_ub, tr_lb, surf_tmp, mask_tmp;
     DevBuf ss_partial, ss_io;  // soft score: block partials; point [d] + outputs [d] + grad_out [1]
     DevBuf g_table, g_owner, g_newpos, g_ccount, g_ccur, g_rbeg, g_rec, g_mult, g_tile;
@@ -276,6 +276,12 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
             // FP32 screen constants in steps of s_f,j (rounding is covered by its band)
             for (int m = 0; m < le; ++m) v.gscale[j][m] = s_t[l][m] / P.s_f[j];
             v.Hs[j] = (float)(h[l + 1][k + j] / P.s_f[j]);
+            v.Hs_lo[j] = (float)(h[l + 1][k + j] / P.s_f[j] - (double)v.Hs[j]);
+            if (l < P.Lj[k + j]) {              // the dependent coordinate splits: its shift enters
+                const double hs = h[l + 1][k + j] / P.s_f[j];
+                if ((double)v.Hs[j] != hs) v.hs_exp = kNoExp;
+                else if (v.hs_exp > kNoExp && hs != 0.0) v.hs_exp = std::min(v.hs_exp, lowbit_exp(hs));
+            }
             v.rc0[j] = (float)((v.Rbase[j] + v.A1[j]) / P.s_f[j]);
             v.Lc[j] = (float)(v.rlb[j] / P.s_f[j]);
         }
@@ -573,6 +579,7 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     TRY(ensure(c, c->alive, nc));
     TRY(ensure(c, c->geo64, (size_t)nc * nfs * NB * 8));
     TRY(ensure(c, c->geo32, (size_t)nc * gf * 4));
+    TRY(ensure(c, c->geo32lo, (size_t)nc * nfs * P.nd * P.le * 4));
     TRY(ensure(c, c->cnt, nch * 12));
     TRY(ensure(c, c->child_idx, nch * 4));
     TRY(ensure(c, c->cursor, nch * 4));
@@ -600,6 +607,7 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
     ch.alive = (uint8_t *)c->alive.p;
     ch.geo64 = (double *)c->geo64.p;
     ch.geo32 = (float *)c->geo32.p;
+    ch.geo32lo = (float *)c->geo32lo.p;
     ch.cnt = (uint32_t *)c->cnt.p;
     ch.child_idx = (int32_t *)c->child_idx.p;
     ch.cursor = (uint32_t *)c->cursor.p;
@@ -724,13 +732,19 @@ static vote_status expand_chunk(vote_ctx *c, int l, int64_t only = -1) {
                                        (double)new_slots * rec_bytes_at(c, l + 1);
     }
     CK(cudaGetLastError());
-    if (c->log >= 2)
+    if (c->log >= 2) {
+        // the running FP64 recheck and test counters (a synchronisation per step: logging only)
+        CK(cudaMemcpyAsync(&c->h_sc->tests, &dsc(c)->tests, 24, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(&c->h_sc->rechecks_df, &dsc(c)->rechecks_df, 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
         std::fprintf(stderr, "[vote] step %lld level %d: %lld cells, %lld tiles, count %.0f B, emit %.0f B, "
-                     "%lld child cells\n", (long long)c->stats.chunks - 1, l, (long long)nc, (long long)nt,
+                     "%lld child cells, %llu tests, %llu FP64 and %llu double-float rechecks so far\n",
+                     (long long)c->stats.chunks - 1, l, (long long)nc, (long long)nt,
                      (double)nt * 32 * rb + (double)nt * ns * 4,
                      new_slots > 0 ? (double)nt * 32 * rb + (double)nt * ns * 4 +
                                          (double)new_slots * rec_bytes_at(c, l + 1) : 0.0,
-                     (long long)new_cells);
+                     (long long)new_cells, c->h_sc->tests, c->h_sc->rechecks, c->h_sc->rechecks_df);
+    }
     c->ls[l + 1].ncells = new_cells;
     c->ls[l + 1].nrecs = new_slots;
     if (new_slots > c->stats.peak_records) c->stats.peak_records = new_slots;
@@ -1386,7 +1400,7 @@ void vote_destroy(vote_ctx *c) {
         release(c, s.rec); release(c, s.mult); release(c, s.tile_cell);
         release(c, s.key); release(c, s.rbeg); release(c, s.rcnt); release(c, s.ub);
     }
-    DevBuf *bufs[] = {&c->levs_dev, &c->path, &c->scal, &c->alive, &c->geo64, &c->geo32, &c->cnt, &c->tinfo,
+    DevBuf *bufs[] = {&c->levs_dev, &c->path, &c->scal, &c->alive, &c->geo64, &c->geo32, &c->geo32lo, &c->cnt, &c->tinfo,
                       &c->ballot, &c->tdst,
                       &c->child_idx, &c->cursor, &c->keepflag, &c->recn, &c->bsums, &c->tr_level, &c->tr_key,
                       &c->tr_ub, &c->tr_lb, &c->surf_tmp, &c->mask_tmp, &c->ss_partial,

@@ -129,8 +129,12 @@ __device__ __forceinline__ void parent_psi(const Problem &P, const Level &lev, u
 // One thread per (cell, free-coordinate child slot fs); the 2^k threads of a cell
 // are consecutive lanes.  Writes the FP64 basis changes (for the exact recheck) and
 // the screen's coefficients G[fs][j][m] = coef_jm(dpsi) * s_t,m / s_f,j rounded to
-// FP32, and per (j, m) the largest |G| over the child slots (rounded up), which
-// bounds the magnitudes the screen's band scales with.
+// FP32, their remainders (G64 - G, rounded to FP32: the double-float tier's low
+// parts; G64 is exact, coef only copies or negates and s_t / s_f is a power of two),
+// per (j, m) the largest |G| over the child slots (rounded up), which bounds the
+// magnitudes the screen's band scales with, and the cell's exactness exponent: the
+// least e with every G a multiple of 2^e (at most 0), or kNoExp when some G is not
+// exactly an FP32 value.
 template <int FAM>
 __global__ void k_cell_geo(Chunk c) {
     using F = Fam<FAM>;
@@ -145,6 +149,7 @@ __global__ void k_cell_geo(Chunk c) {
     float ga[F::ND * F::LE];
 #pragma unroll
     for (int x = 0; x < F::ND * F::LE; ++x) ga[x] = 0.0f;
+    int ge = 0;                                      // exactness exponent (<= 0) of this thread's G
     if (in) {
         if (fs == 0) {
             unsigned thr = prune_threshold(P, c.sc, c.prune);
@@ -166,17 +171,25 @@ __global__ void k_cell_geo(Chunk c) {
 #pragma unroll
         for (int x = 0; x < F::ND * F::LE; ++x) {
             const double gx = g[x] * lev.gscale[x / F::LE][x % F::LE];
-            c.geo32[(size_t)cell * GF + fs * F::ND * F::LE + x] = (float)gx;
+            const float gh = (float)gx;
+            c.geo32[(size_t)cell * GF + fs * F::ND * F::LE + x] = gh;
+            c.geo32lo[((size_t)cell * NF + fs) * F::ND * F::LE + x] = (float)(gx - (double)gh);
             ga[x] = __double2float_ru(fabs(gx));
+            if ((double)gh != gx) ge = kNoExp;
+            else if (gx != 0.0 && ge > kNoExp) ge = min(ge, lowbit_exp(gx));
         }
     }
 #pragma unroll
-    for (int o = 1; o < NF; o <<= 1)
+    for (int o = 1; o < NF; o <<= 1) {
 #pragma unroll
         for (int x = 0; x < F::ND * F::LE; ++x) ga[x] = fmaxf(ga[x], __shfl_xor_sync(kFull, ga[x], o));
-    if (in && fs == 0)
+        ge = min(ge, __shfl_xor_sync(kFull, ge, o));
+    }
+    if (in && fs == 0) {
 #pragma unroll
         for (int x = 0; x < F::ND * F::LE; ++x) c.geo32[(size_t)cell * GF + NF * F::ND * F::LE + x] = ga[x];
+        c.geo32[(size_t)cell * GF + GF - 1] = (float)ge;
+    }
 }
 
 // Block-wide exclusive scan of one 64-bit value per thread (blockDim = 256).

@@ -44,6 +44,7 @@ struct Scalars {
     unsigned int err;                // nonzero: input out of range
     unsigned int pad2;
     unsigned int qmax[GV_MAXD + GV_MAXT];  // lift: largest |q_f,j|, |q_t,m| of the root records
+    unsigned long long rechecks_df;  // snaps the double-float tier decided (FP32 screen undecided)
 };
 
 struct Trace {
@@ -67,7 +68,8 @@ struct Chunk {
     int64_t t0, t1;          // tile range of the chunk
     uint8_t *alive;          // [nc]   cell still above the pruning threshold
     double *geo64;           // [nc][2^k][NB]          basis change per free child slot
-    float *geo32;            // [nc][2^k * ND * LE + ND * LE] screen coefficients G, max |G|
+    float *geo32;            // [nc][2^k * ND * LE + ND * LE + 1] screen coefficients G, max |G|, exponent
+    float *geo32lo;          // [nc][2^k * ND * LE]   G64 - G rounded to FP32 (double-float tier)
     uint32_t *cnt;           // [nc][2^d][3]      UB, LB, records per child
     int2 *tinfo;             // [t1 - t0]         per tile: chunk-local cell (-1: pruned), valid lanes
     uint32_t *ballot;        // [t1 - t0][2^d]    per tile and child: UB-pass lanes
@@ -83,9 +85,11 @@ struct Chunk {
     unsigned spin;           // polls of a bounded wait for a bulk copy before giving up
 };
 
-// Size in floats of one cell's screen geometry: G[2^k][ND][LE] and, per (j, m), the
-// largest |G| over the free slots (rounded up).
-__host__ __device__ constexpr int geo32_floats(int nfs, int nd, int le) { return nfs * nd * le + nd * le; }
+// Size in floats of one cell's screen geometry: G[2^k][ND][LE], per (j, m) the
+// largest |G| over the free slots (rounded up), and the cell's exactness exponent e
+// (every G is FP32-exact and a multiple of 2^e; kNoExp when not).
+__host__ __device__ constexpr int geo32_floats(int nfs, int nd, int le) { return nfs * nd * le + nd * le + 1; }
+constexpr int kNoExp = -1000;
 
 // Path geometry for replaying surfaces along the root-to-cell path.
 struct PathStep {

@@ -324,6 +324,71 @@ __device__ __noinline__ int3 snap64_words(const Problem *P, const Level *lev, Re
 }
 
 // ---------------------------------------------------------------------------
+// Double-float tier.  An integer field as an unevaluated sum hi + lo of two FP32
+// values (exact for |q| < 2^31: |q - hi| <= 2^6), and Knuth's two-sum.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_int(int q, float &hi, float &lo) {
+    hi = __int2float_rn(q);
+    lo = __int2float_rn(q - __float2int_rz(hi));
+}
+
+__device__ __forceinline__ float two_sum(float a, float b, float &err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// The snap of one record's dependent coordinates at the centre of child s, from
+// the residual q_f,j + sum_m q_t,m G64[fs][j][m] -+ h1_j / s_f,j evaluated as a
+// double-float (G64 = Gh + Gl, the cell's coefficients and their remainders):
+// (x, y) the snapped values, z = 1 when both are decided (the value is more than
+// bd_j away from a rounding tie and below lim in magnitude), else 0 (the FP64
+// definition decides).  Out of line: the FP32 screen needs it rarely.
+template <int FAM, bool Q16>
+__device__ __noinline__ int3 snap_df_words(const Level *lev, RecWords rw, const float *Gh, const float *Gl, int s,
+                                           float bd0, float bd1, float lim) {
+    using F = Fam<FAM>;
+    static_assert(F::ND <= 2, "two dependent coordinates at most");
+    constexpr int NFS = 1 << F::K;
+    const int fs = s & (NFS - 1);
+    int qn[2] = {0, 0}, ok = 1;
+#pragma unroll
+    for (int j = 0; j < F::ND; ++j) {
+        float hi, lo;
+        split_int(field_i<Q16>(rw.w, j), hi, lo);
+#pragma unroll
+        for (int m = 0; m < F::LE; ++m) {
+            if (!F::uses(j, m)) continue;
+            float th, tl;
+            split_int(field_i<Q16>(rw.w, F::ND + m), th, tl);
+            const int x = (fs * F::ND + j) * F::LE + m;
+            const float gh = __ldg(Gh + x), gl = __ldg(Gl + x);
+            const float p = __fmul_rn(th, gh);
+            const float e = __fmaf_rn(th, gh, -p);                  // th gh = p + e exactly
+            float err;
+            hi = two_sum(hi, p, err);
+            lo = __fadd_rn(lo, __fadd_rn(err, __fmaf_rn(tl, gl, __fmaf_rn(th, gl, __fmaf_rn(tl, gh, e)))));
+        }
+        if ((lev->split_mask >> (F::K + j)) & 1) {
+            // the residual at the child centre: partial - h1 when the dependent bit is set
+            const bool up = (s >> (F::K + j)) & 1;
+            const float h = up ? -lev->Hs[j] : lev->Hs[j], hl = up ? -lev->Hs_lo[j] : lev->Hs_lo[j];
+            float err;
+            hi = two_sum(hi, h, err);
+            lo = __fadd_rn(lo, __fadd_rn(err, hl));
+        }
+        const float r = rintf(hi);                                  // hi - r is exact
+        const float w = __fadd_rn(__fsub_rn(hi, r), lo);
+        const float k = rintf(w);
+        const float fr = __fsub_rn(w, k);
+        ok &= (int)(fabsf(hi) < lim) & (int)(0.5f - fabsf(fr) > (j ? bd1 : bd0));
+        qn[j] = ok ? __float2int_rn(r) + __float2int_rn(k) : 0;
+    }
+    return make_int3(qn[0], qn[1], ok);
+}
+
+// ---------------------------------------------------------------------------
 // FP32 screen (in steps of s_f): residual before the dependent shift for free
 // slot fs, from the record's fields and the cell's coefficients G[fs][j][m].
 // ---------------------------------------------------------------------------

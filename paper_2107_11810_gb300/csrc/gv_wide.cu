@@ -24,6 +24,20 @@ __global__ void __launch_bounds__(256) k_count_wide(const __grid_constant__ Chun
     constexpr int NW = rec_words(F::NFP, Q16);
     constexpr int GF = geo32_floats(NFS, ND, LE);
     const int lane = threadIdx.x & 31;
+    // the current cell's screen coefficients, staged once per run of tiles of the
+    // cell in the warp's part of shared memory (the per-free-slot loads then wait
+    // on shared memory, not on the cache hierarchy); blocks of 8 warps
+    __shared__ float s_g[8][GF];
+    float *sg = s_g[threadIdx.x >> 5];
+    int gcell = -1;
+    auto stage = [&](int cell) {
+        if (cell == gcell) return;                                  // uniform
+        __syncwarp();                                               // the old cell's reads are done
+        const float *src = c.geo32 + (size_t)cell * GF;
+        for (int i = lane; i < GF; i += 32) sg[i] = src[i];
+        __syncwarp();
+        gcell = cell;
+    };
     const int64_t nt = c.t1 - c.t0;
     const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -77,7 +91,8 @@ __global__ void __launch_bounds__(256) k_count_wide(const __grid_constant__ Chun
         uint32_t w[NW];
         load_words<NW>(c.in.rec, r, w);                             // whole tiles are allocated
         const uint32_t mult = WEIGHTED ? (act ? c.in.mult[r] : 0u) : 1u;
-        const float *G = c.geo32 + (size_t)cell * GF;
+        if constexpr (PREC == 1) stage(cell);
+        const float *G = sg;
         const double *g64 = c.geo64 + (size_t)cell * NFS * F::NB;
         unsigned bw[SPL];                                           // ballots of slots lane + 32 h
 #pragma unroll
@@ -203,6 +218,20 @@ __global__ void __launch_bounds__(256) k_emit_wide(const __grid_constant__ Chunk
     constexpr int NWI = rec_words(NFP, QI16), NWO = rec_words(NFP, QO16);
     constexpr int GF = geo32_floats(NFS, ND, LE);
     const int lane = threadIdx.x & 31;
+    // the current cell's screen coefficients, staged once per run of tiles of the
+    // cell in the warp's part of shared memory (the per-free-slot loads then wait
+    // on shared memory, not on the cache hierarchy); blocks of 8 warps
+    __shared__ float s_g[8][GF];
+    float *sg = s_g[threadIdx.x >> 5];
+    int gcell = -1;
+    auto stage = [&](int cell) {
+        if (cell == gcell) return;                                  // uniform
+        __syncwarp();                                               // the old cell's reads are done
+        const float *src = c.geo32 + (size_t)cell * GF;
+        for (int i = lane; i < GF; i += 32) sg[i] = src[i];
+        __syncwarp();
+        gcell = cell;
+    };
     const unsigned below = (1u << lane) - 1u;
     const int64_t nt = c.t1 - c.t0;
     const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -213,7 +242,7 @@ __global__ void __launch_bounds__(256) k_emit_wide(const __grid_constant__ Chunk
     float hs[ND];
 #pragma unroll
     for (int j = 0; j < ND; ++j) hs[j] = ((smask >> (F::K + j)) & 1) ? lev.Hs[j] : 0.0f;
-    unsigned nrechk = 0, bad = 0;
+    unsigned nrechk = 0, ndf = 0, bad = 0;
 
 #pragma unroll 1
     for (int64_t tt = ta; tt < tb; ++tt) {
@@ -232,7 +261,8 @@ __global__ void __launch_bounds__(256) k_emit_wide(const __grid_constant__ Chunk
         const int64_t r = (c.t0 + tt) * 32 + lane;
         uint32_t w[NWI];
         load_words<NWI>(c.in.rec, r, w);
-        const float *G = c.geo32 + (size_t)cell * GF;
+        if (PREC == 1) stage(cell);
+        const float *G = sg;
         const double *g64 = c.geo64 + (size_t)cell * NFS * F::NB;
         // the child's essential parameters (re-snapped when the step doubles)
         uint32_t fb[NFP];
@@ -254,12 +284,21 @@ __global__ void __launch_bounds__(256) k_emit_wide(const __grid_constant__ Chunk
             }
         }
         const uint32_t mult = c.out.mult ? c.in.mult[r] : 1u;
-        float es[ND];                                               // the snap's band (steps)
+        float es[ND], bd[ND];                                       // the snaps' bands (steps)
+            bool xs[ND];                                                // FP32 residual exact
         if (PREC == 1) {
             float M[ND];
+            // every term a multiple of 2^ex and M below 2^(24 + ex): the FP32 residual, and
+            // the definition's FP64 one, are exact, so a tie rounds to even in both
+            const int ex = min(__float2int_rn(G[GF - 1]), lev.hs_exp);
+            const float tq = ex > -100 ? __int_as_float((127 + 24 + ex) << 23) : 0.0f;
             magnitudes<FAM>(qf, qt, G + NFS * ND * LE, hs, M);
 #pragma unroll
-            for (int j = 0; j < ND; ++j) es[j] = 0.5f - kBandSnap * M[j];
+            for (int j = 0; j < ND; ++j) {
+                es[j] = 0.5f - kBandSnap * M[j];
+                bd[j] = __fmaf_ru(kBandDF, M[j], kBandDFAbs);
+                xs[j] = M[j] < tq;
+            }
         }
 #pragma unroll 1
         for (int fs = 0; fs < NFS; ++fs) {
@@ -289,19 +328,28 @@ __global__ void __launch_bounds__(256) k_emit_wide(const __grid_constant__ Chunk
                         const float y = ((ds >> j) & 1) ? u[j] - hs[j] : u[j] + hs[j];
                         if constexpr (QO16) {
                             const float t = y + kMagic16;
-                            done &= fabsf(y - (t - kMagic16)) < es[j] && fabsf(y) < 32767.0f;
+                            done &= (fabsf(y - (t - kMagic16)) < es[j] || xs[j]) && fabsf(y) < 32767.0f;
                             fb[j] = __float_as_uint(t);
                         } else {
                             const float t = y + kMagic;
-                            done &= fabsf(y - (t - kMagic)) < es[j] && fabsf(y) < 4.0e6f;
+                            done &= (fabsf(y - (t - kMagic)) < es[j] || xs[j]) && fabsf(y) < 4.0e6f;
                             fb[j] = (uint32_t)(__float_as_int(t) - 0x4B400000);
                         }
                     }
-                    nrechk += !done;
                 }
                 if (!done) {
-                    const int3 q = snap64_words<FAM, QI16>(&c.P, &c.lev, rec_words_of<NWI>(w), g64, s);
-                    bad |= (unsigned)(q.z != 0);
+                    int3 q = make_int3(0, 0, 0);
+                    if constexpr (PREC == 1) {                              // the double-float tier
+                        q = snap_df_words<FAM, QI16>(&c.lev, rec_words_of<NWI>(w), c.geo32 + (size_t)cell * GF,
+                                                     c.geo32lo + (size_t)cell * (NFS * ND * LE), s, bd[0],
+                                                     bd[ND - 1], QO16 ? 32767.0f : 1.0e9f);
+                        ++ndf;
+                    }
+                    if (!q.z) {                                             // the FP64 definition
+                        q = snap64_words<FAM, QI16>(&c.P, &c.lev, rec_words_of<NWI>(w), g64, s);
+                        bad |= (unsigned)(q.z != 0);
+                        nrechk += PREC == 1;
+                    }
                     const int qn[2] = {q.x, q.y};
 #pragma unroll
                     for (int j = 0; j < ND; ++j) {
@@ -321,9 +369,11 @@ __global__ void __launch_bounds__(256) k_emit_wide(const __grid_constant__ Chunk
         }
     }
     nrechk = __reduce_add_sync(kFull, nrechk);
+    ndf = __reduce_add_sync(kFull, ndf);
     bad = __reduce_or_sync(kFull, bad);
     if (lane == 0) {
         if (nrechk) atomicAdd(&c.sc->rechecks, (unsigned long long)nrechk);
+        if (ndf) atomicAdd(&c.sc->rechecks_df, (unsigned long long)ndf);
         if (bad) atomicOr(&c.sc->err, bad << 1);
     }
 }
