@@ -72,7 +72,7 @@ CASES = {
                                                noise_deg=0.05, seed=s),
     inputs.POSE6DOF: lambda s: inputs.pose6dof(n=80, inlier_frac=0.3, levels=3, seed=s),
     inputs.RAYS3D: lambda s: inputs.rays3d(n=300, inlier_frac=0.3, eps=0.03, noise=0.002, seed=s),
-    inputs.POINTSET2D: lambda s: inputs.pointset2d(m=14, eps=0.08, noise=0.002, seed=s),
+    inputs.POINTSET2D: lambda s: inputs.pointset2d(m=14, eps=0.16, noise=0.002, seed=s),
     inputs.AFFINE4D: lambda s: inputs.affine4d(n=150, inlier_frac=0.3, eps=0.15, noise=0.005, seed=s),
 }
 

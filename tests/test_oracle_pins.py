@@ -43,7 +43,7 @@ def small_rays(n, seed, frac=0.3, eps=0.03):
     return inputs.rays3d(n=n, inlier_frac=frac, eps=eps, noise=0.002, seed=seed)
 
 
-def small_points(m, seed, eps=0.08):
+def small_points(m, seed, eps=0.16):
     return inputs.pointset2d(m=m, eps=eps, noise=0.002, seed=seed)
 
 
