@@ -45,10 +45,10 @@ _LIB = os.path.join(_BUILD, "libgvoracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D = 1, 2, 3, 4, 5, 6, 7
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF = 1, 2, 3, 4, 5, 6, 7, 8
 NO_MERGE, NO_PRUNE, REVERSE = 1, 2, 4
 FAMILY_SHAPE = {LINE2D: (2, 1, 1, 2), PLANE3D_SPH: (3, 2, 3, 3), POSE3DOF: (3, 1, 2, 4), POSE6DOF: (6, 4, 11, 5),
-                RAYS3D: (3, 1, 2, 4), POINTSET2D: (4, 2, 2, 4), AFFINE4D: (4, 3, 3, 4)}
+                RAYS3D: (3, 1, 2, 4), POINTSET2D: (4, 2, 2, 4), AFFINE4D: (4, 3, 3, 4), RADIAL5DOF: (5, 4, 7, 5)}
 """family -> (d, k, number of essential params, number of input params)"""
 
 _CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11", "-fopenmp"]

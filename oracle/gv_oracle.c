@@ -68,7 +68,7 @@
 #define GVO_MAXL 40
 
 enum { GVO_LINE2D = 1, GVO_PLANE3D_SPH = 2, GVO_POSE3DOF = 3, GVO_POSE6DOF = 4, GVO_RAYS3D = 5,
-       GVO_POINTSET2D = 6, GVO_AFFINE4D = 7 };
+       GVO_POINTSET2D = 6, GVO_AFFINE4D = 7, GVO_RADIAL5DOF = 8 };
 enum { GVO_NO_MERGE = 1, GVO_NO_PRUNE = 2, GVO_REVERSE = 4 };
 
 /* ------------------------------------------------------------------------- */
@@ -193,6 +193,7 @@ static int family_shape(int fam, int d, int k, int *le, int *np)
     case GVO_RAYS3D:      if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
     case GVO_POINTSET2D:  if (d != 4 || k != 2) return 1; *le = 2; *np = 4; return 0;
     case GVO_AFFINE4D:    if (d != 4 || k != 3) return 1; *le = 3; *np = 4; return 0;
+    case GVO_RADIAL5DOF:  if (d != 5 || k != 4) return 1; *le = 7; *np = 5; return 0;
     default: return 1;
     }
 }
@@ -238,13 +239,21 @@ static void family_sigma(const gvo_problem *p, const double *h, double *sigma)
         sigma[10] = h[3];
         break;
     }
+    case GVO_RADIAL5DOF: {  /* entries of the rows r1, r2 of R(phi) (as for 6DoF), and y */
+        double hphi = (h[0] + h[1]) + h[2];
+        for (int m = 0; m < 6; ++m) sigma[m] = hphi;
+        sigma[6] = h[3];
+        break;
+    }
     }
 }
 
 /* number of basis values psi of a family */
 static int family_nb(int fam, int le)
 {
-    return fam == GVO_POSE6DOF ? 10 : (fam == GVO_RAYS3D ? 1 : le);   /* point sets: (c, d), le = 2 */
+    /* 6DoF and radial 5DoF: the nine entries of R(phi) and the last free coordinate;
+     * rays: x; point sets: (c, d), le = 2 */
+    return (fam == GVO_POSE6DOF || fam == GVO_RADIAL5DOF) ? 10 : (fam == GVO_RAYS3D ? 1 : le);
 }
 
 static double pow2_floor(double x)  /* 2^floor(log2 x), exact */
@@ -376,7 +385,8 @@ static void family_basis(const gvo_problem *p, int l, const int64_t *i, double *
         psi[1] = gvo_vsin(yaw);
         break;
     }
-    case GVO_POSE6DOF: {                                      /* rows of R(phi), then z */
+    case GVO_POSE6DOF:                                        /* rows of R(phi), then z */
+    case GVO_RADIAL5DOF: {                                    /* rows of R(phi), then y */
         double ph[3];
         for (int j = 0; j < 3; ++j) ph[j] = cell_center(p, l, j, i[j]);
         rodrigues(p->inv_fact, ph, psi);
@@ -467,6 +477,25 @@ static void family_lift(const gvo_problem *p, const double *params, int64_t n, i
         r->f[1] = ((sy3 + t[10] * psi[9]) - sy2) - c[5];
         break;
     }
+    case GVO_RADIAL5DOF: {
+        /* match (w, xi, eta) under the radial camera with rows p1 = (r1, -y), p2 = (r2, x)
+         * (Sec. 4.2.4): eta (r1 . w - y) = xi (r2 . w + x), so with rho = eta / xi
+         * x = rho (r1 . w) - r2 . w - rho y, affine in the basis (rows of R, y) with
+         * coefficients t = (rho w, w, rho). */
+        double w[3], xi = params[3 * n + i], eta = params[4 * n + i];
+        for (int j = 0; j < 3; ++j) w[j] = params[j * n + i];
+        double rho = eta / xi;
+        for (int j = 0; j < 3; ++j) {
+            r->t[j] = rho * w[j];
+            r->t[3 + j] = w[j];
+        }
+        r->t[6] = rho;
+        const double *t = r->t;
+        double s1 = (t[0] * psi[0] + t[1] * psi[1]) + t[2] * psi[2];
+        double s2 = (t[3] * psi[3] + t[4] * psi[4]) + t[5] * psi[5];
+        r->f[0] = ((s1 - s2) - t[6] * psi[9]) - c[4];
+        break;
+    }
     }
     r->mult = 1;
     r->orig = i;
@@ -506,7 +535,8 @@ static void child_geometry(const gvo_problem *p, int l, const int64_t *i, const 
         double psi_child[GVO_MAXT];
         family_basis(p, l + 1, g->ci, psi_child);
         for (int m = 0; m < p->nb; ++m) g->dpsi[m] = psi_child[m] - psi_parent[m];
-        if (p->fam == GVO_POSE6DOF) g->dpsi[9] = g->shift[3];   /* z is linear: exact shift */
+        /* z (6DoF) and y (radial 5DoF) are linear: exact shifts */
+        if (p->fam == GVO_POSE6DOF || p->fam == GVO_RADIAL5DOF) g->dpsi[9] = g->shift[3];
     }
 }
 
@@ -544,6 +574,13 @@ static void family_residual(const gvo_problem *p, const double *f, const double 
         double sy2 = (t[0] * d[3] + t[1] * d[4]) + t[2] * d[5];
         fo[0] = (f[0] + ((sx3 + t[9] * d[9]) - sx1)) - g->shift[4];
         fo[1] = (f[1] + ((sy3 + t[10] * d[9]) - sy2)) - g->shift[5];
+        break;
+    }
+    case GVO_RADIAL5DOF: {
+        const double *d = g->dpsi;
+        double s1 = (t[0] * d[0] + t[1] * d[1]) + t[2] * d[2];
+        double s2 = (t[3] * d[3] + t[4] * d[4]) + t[5] * d[5];
+        fo[0] = (f[0] + ((s1 - s2) - t[6] * d[9])) - g->shift[4];
         break;
     }
     }
@@ -590,6 +627,14 @@ static void family_lipschitz(const gvo_problem *p, const double *t, double *lam)
         double lx = nxw + nw, ly = nyw + nw;
         lam[0] = lx; lam[1] = lx; lam[2] = lx; lam[3] = fabs(t[9]);
         lam[4] = ly; lam[5] = ly; lam[6] = ly; lam[7] = fabs(t[10]);
+        break;
+    }
+    case GVO_RADIAL5DOF: {
+        /* |dx/dphi_a| <= |rho w| + |w| (rows r1, r2; the same bound as for 6DoF); dx/dy = -rho */
+        double nrw = sqrt((t[0] * t[0] + t[1] * t[1]) + t[2] * t[2]);
+        double nw = sqrt((t[3] * t[3] + t[4] * t[4]) + t[5] * t[5]);
+        double lx = nrw + nw;
+        lam[0] = lx; lam[1] = lx; lam[2] = lx; lam[3] = fabs(t[6]);
         break;
     }
     }

@@ -30,6 +30,11 @@ Surface parameters are FP64, structure-of-arrays ``params[P, n]``:
 * ``AFFINE4D``    (hyperplane fitting in the affine form, Sec. 4.1, d = 4): P = 4, rows
   (x1, x2, x3, x4) of points; voting space (a1, a2, a3, b) with the dual hyperplane
   b = x4 - (a1 x1 + a2 x2 + a3 x3).
+* ``RADIAL5DOF``  (radial camera, unknown focal length, Sec. 4.2.4): P = 5, rows
+  (w1, w2, w3, xi, eta) of a match between world point w and image point (xi, eta);
+  voting space (phi1, phi2, phi3, y, x) of the radial camera with rows
+  (r1, -y) and (r2, x), where eta (r1 . w - y) = xi (r2 . w + x), i.e.
+  x = eta (r1 . w - y) / xi - r2 . w.
 """
 from __future__ import annotations
 
@@ -38,11 +43,11 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D = 1, 2, 3, 4, 5, 6, 7
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF = 1, 2, 3, 4, 5, 6, 7, 8
 FAMILY_NAMES = {LINE2D: "LINE2D", PLANE3D_SPH: "PLANE3D_SPH", POSE3DOF: "POSE3DOF", POSE6DOF: "POSE6DOF",
-                RAYS3D: "RAYS3D", POINTSET2D: "POINTSET2D", AFFINE4D: "AFFINE4D"}
+                RAYS3D: "RAYS3D", POINTSET2D: "POINTSET2D", AFFINE4D: "AFFINE4D", RADIAL5DOF: "RADIAL5DOF"}
 FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1), POSE6DOF: (6, 4), RAYS3D: (3, 1),
-             POINTSET2D: (4, 2), AFFINE4D: (4, 3)}
+             POINTSET2D: (4, 2), AFFINE4D: (4, 3), RADIAL5DOF: (5, 4)}
 SEED_BASE = 2107118100
 
 
@@ -307,6 +312,75 @@ def pose6dof(n: int = 5000, inlier_frac: float = 0.05, prior_deg: float = 30.0, 
     truth = np.concatenate([phi, [t[2], t[0], t[1]]])
     return Problem(POSE6DOF, eps, bounds, np.ascontiguousarray(out), truth, inliers, "pose6dof",
                    dict(inlier_frac=inlier_frac, prior=prior, prior_deg=prior_deg, levels=levels))
+
+
+def radial5dof(n: int = 5000, inlier_frac: float = 0.05, prior_deg: float = 30.0, box: float = 10.0,
+               levels: int = 7, noise_deg: float = 0.1, points=(20.0, 20.0, 5.0), fov: float = 1.0,
+               xi_min: float = 0.2, focal=(0.8, 1.2), seed: int = SEED_BASE + 8,
+               rng: np.random.Generator | None = None) -> Problem:
+    """Radial-camera posing with unknown focal length (5DoF, Sec. 4.2.4).  World
+    points uniform in [0, points_0] x [0, points_1] x [0, points_2]; camera frame
+    X = R(phi) w + (-y, x, z), the radial camera's rows being (r1, -y) and (r2, x)
+    (z and the focal length f ~ U[focal] are what the radial model leaves out).
+    Truth: phi as for the calibrated camera (prior uniform in the unit ball, the
+    rotation within +- prior per axis of it), -y, x, z ~ U[0, box] (redrawn until a
+    quarter of the points are visible).  Inliers: points with X_3 > 1 m inside the
+    field of view |X_1|, |X_2| <= fov X_3 and |X_1| >= xi_min X_3 (the surface
+    divides by xi), seen at f (tan a, tan b) with a, b the bearing angles perturbed
+    by N(0, noise); outliers: a random point with a random image point of the field
+    of view, |xi| >= xi_min f.  Voting domain phi_prior +- prior per axis,
+    y in [-box, 0], x in [0, box]; every coordinate splits ``levels`` times, and the
+    tolerance of x is its leaf width (a constant distance)."""
+    if rng is None:
+        rng = np.random.default_rng(seed)
+    pr = math.radians(prior_deg)
+
+    def visible(X):
+        return ((X[:, 2] > 1.0) & (np.abs(X[:, 0]) <= fov * X[:, 2]) & (np.abs(X[:, 1]) <= fov * X[:, 2])
+                & (np.abs(X[:, 0]) >= xi_min * X[:, 2]))
+
+    def world(m):
+        return np.stack([rng.uniform(0, points[0], m), rng.uniform(0, points[1], m),
+                         rng.uniform(0, points[2], m)], axis=1)
+
+    while True:
+        v = rng.normal(size=3)
+        prior = v / np.linalg.norm(v) * rng.uniform(0.0, 1.0) ** (1.0 / 3.0)
+        phi = prior + rng.uniform(-pr, pr, 3)
+        t = rng.uniform(0.0, box, 3)                    # (-y, x, z)
+        R = rotvec_matrix(phi)
+        if visible(world(4096) @ R.T + t).mean() >= 0.25:
+            break
+    f = rng.uniform(*focal)
+    n_in = int(round(n * inlier_frac))
+    sig = math.radians(noise_deg)
+    out = np.empty((5, n))
+    got = 0
+    while got < n_in:
+        w = world(8 * (n_in - got) + 16)
+        X = w @ R.T + t
+        ok = visible(X)
+        w, X = w[ok][: n_in - got], X[ok][: n_in - got]
+        a = np.arctan2(X[:, 0], X[:, 2]) + rng.normal(0, sig, len(w))
+        b = np.arctan2(X[:, 1], X[:, 2]) + rng.normal(0, sig, len(w))
+        sl = slice(got, got + len(w))
+        out[0:3, sl] = w.T
+        out[3, sl], out[4, sl] = f * np.tan(a), f * np.tan(b)
+        got += len(w)
+    m = n - n_in
+    out[0:3, n_in:] = world(m).T
+    out[3, n_in:] = f * rng.choice([-1.0, 1.0], m) * rng.uniform(xi_min, fov, m)
+    out[4, n_in:] = f * rng.uniform(-fov, fov, m)
+    perm = rng.permutation(n)
+    out = out[:, perm]
+    inliers = np.nonzero(perm < n_in)[0]
+    lo = np.concatenate([prior - pr, [-box, 0.0]])
+    hi = np.concatenate([prior + pr, [0.0, box]])
+    bounds = np.stack([lo, hi], axis=1).reshape(-1)
+    eps = (hi - lo) / 2.0 ** levels
+    truth = np.concatenate([phi, [-t[0], t[1]]])
+    return Problem(RADIAL5DOF, eps, bounds, np.ascontiguousarray(out), truth, inliers, "radial5dof",
+                   dict(inlier_frac=inlier_frac, prior=prior, prior_deg=prior_deg, levels=levels, focal=f))
 
 
 def rays3d(n: int = 100_000, inlier_frac: float = 0.02, eps: float = 0.002, noise: float = 0.0005,

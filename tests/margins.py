@@ -28,7 +28,7 @@ import numpy as np
 import brute
 import oracle
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D = 1, 2, 3, 4, 5, 6, 7
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF = 1, 2, 3, 4, 5, 6, 7, 8
 
 
 def _rot(x):
@@ -63,6 +63,9 @@ def basis(family: int, x: np.ndarray) -> np.ndarray:
         fx = np.concatenate([-Rm[..., 0, :], Rm[..., 2, :], zero3, z, zero1], axis=-1)
         fy = np.concatenate([-Rm[..., 1, :], zero3, Rm[..., 2, :], zero1, z], axis=-1)
         return np.concatenate([fx, fy], axis=-1)
+    if family == RADIAL5DOF:        # t = (rho w, w, rho): x = rho w . r1 - w . r2 - rho y
+        Rm = _rot(x[..., 0:3])
+        return np.concatenate([Rm[..., 0, :], -Rm[..., 1, :], -x[..., 3:4]], axis=-1)
     raise ValueError(family)
 
 
@@ -88,6 +91,8 @@ def t_part(family: int, t: np.ndarray, x: np.ndarray) -> np.ndarray:
     if family == POSE6DOF:
         t = np.asarray(t, float)
         return np.stack([psi[..., :11] @ t, psi[..., 11:] @ t], axis=-1)
+    if family == RADIAL5DOF:
+        return (psi @ np.asarray(t, float))[..., None]
     raise ValueError(family)
 
 

@@ -6,7 +6,8 @@ surface happens to sit inside that margin.  Here each margin is checked on its
 own, against the surface equations (tests/margins.py), on the level structures
 of the benchmark workloads (2D line eps 0.01, 3D plane eps 0.005, 3DoF camera
 0.25 m / 0.5 deg, 6DoF camera with a +-30 deg rotation prior in a 10 m box, 7
-levels, rays in the unit cube eps 0.002, point sets eps 0.01, affine hyperplanes in 4-space eps 0.01):
+levels, rays in the unit cube eps 0.002, point sets eps 0.01, affine hyperplanes in 4-space eps 0.01, the radial
+camera with a +-30 deg rotation prior in a 10 m box, 7 levels):
 
 * sigma_m bounds the change of every basis function across every level's cells
   (Sec. 3.2: the essential parameters are rounded to a step scaled by how much
@@ -34,6 +35,7 @@ WORKLOADS = {
     "rays": lambda: inputs.rays3d(n=400, seed=inputs.SEED_BASE + 5),
     "points": lambda: inputs.pointset2d(m=20, seed=inputs.SEED_BASE + 6),
     "affine": lambda: inputs.affine4d(n=400, seed=inputs.SEED_BASE + 7),
+    "radial": lambda: inputs.radial5dof(n=400, seed=inputs.SEED_BASE + 8),
 }
 
 
@@ -68,6 +70,13 @@ def essential_samples(p, rng):
             px, py = p.params[0, i], p.params[1, i]
             ts.append(np.array([px, py]) / (px * px + py * py))
         ts += [np.array(v, float) for v in ([4, 0], [0, -4], [2.5, 2.5])]
+    elif p.family == inputs.RADIAL5DOF:         # t = (rho w, w, rho), rho = eta / xi
+        ts = []
+        for i in rng.choice(p.n, 20, replace=False):
+            w, rho = p.params[0:3, i], p.params[4, i] / p.params[3, i]
+            ts.append(np.concatenate([rho * w, w, [rho]]))
+        ts += [rng.normal(0.0, 10.0, 7) for _ in range(4)]
+        ts += [np.array([100, -60, 20, 20, -12, 4, 5], float)]
     else:                      # t = (w, xi w, eta w, xi, eta), plus arbitrary coefficient vectors
         ts = []
         for i in rng.choice(p.n, 20, replace=False):

@@ -59,6 +59,11 @@ MUTANTS = {
     "pose6_rotation_sign": ("R[1] = b0 * ph[1] - a2;", "R[1] = b0 * ph[1] + a2;"),
     "pose6_lipschitz_without_w": ("double lx = nxw + nw, ly = nyw + nw;", "double lx = nxw, ly = nyw;"),
     "pose6_sigma_one_axis": ("double hr = (h[0] + h[1]) + h[2];", "double hr = h[0];"),
+    "radial_residual_row": ("double s2 = (t[3] * d[3] + t[4] * d[4]) + t[5] * d[5];",
+                            "double s2 = (t[3] * d[0] + t[4] * d[1]) + t[5] * d[2];"),
+    "radial_lift_rho": ("double rho = eta / xi;", "double rho = xi / eta;"),
+    "radial_lipschitz_without_w": ("double lx = nrw + nw;", "double lx = nrw;"),
+    "radial_sigma_one_axis": ("double hphi = (h[0] + h[1]) + h[2];", "double hphi = h[2];"),
     "pose_sigma_halved": ("(a, b) */\n        sigma[0] = h[0];\n        sigma[1] = h[0];",
                           "(a, b) */\n        sigma[0] = 0.5 * h[0];\n        sigma[1] = 0.5 * h[0];"),
     "error_step_missing_essential_term": ("delta = delta + (p->s_t[l][m] * 0.5) * sigma[m];",
@@ -74,6 +79,7 @@ CASES = {
     inputs.RAYS3D: lambda s: inputs.rays3d(n=300, inlier_frac=0.3, eps=0.03, noise=0.002, seed=s),
     inputs.POINTSET2D: lambda s: inputs.pointset2d(m=14, eps=0.16, noise=0.002, seed=s),
     inputs.AFFINE4D: lambda s: inputs.affine4d(n=150, inlier_frac=0.3, eps=0.15, noise=0.005, seed=s),
+    inputs.RADIAL5DOF: lambda s: inputs.radial5dof(n=80, inlier_frac=0.3, levels=3, seed=s),
 }
 
 
@@ -110,6 +116,10 @@ def pins_hold(lib, fam, seed):
         free = ((1.0 / np.hypot(p.params[0], p.params[1])).max() + st) * hL[: p.k].sum()
     elif p.family == inputs.AFFINE4D:
         free = (np.abs(p.params[0:3]).max() + st) * hL[: p.k].sum()
+    elif p.family == inputs.RADIAL5DOF:
+        rho = np.abs(p.params[4] / p.params[3])
+        free = ((((1.0 + rho) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st) * hL[0:3].sum()
+                + (rho.max() + st) * hL[3])
     else:
         c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
         free = ((((1.0 + c) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st) * hL[0:3].sum()
@@ -132,6 +142,7 @@ MARGIN_CASES = {
     inputs.RAYS3D: lambda: inputs.rays3d(n=200, seed=inputs.SEED_BASE + 5),
     inputs.POINTSET2D: lambda: inputs.pointset2d(m=15, seed=inputs.SEED_BASE + 6),
     inputs.AFFINE4D: lambda: inputs.affine4d(n=200, seed=inputs.SEED_BASE + 7),
+    inputs.RADIAL5DOF: lambda: inputs.radial5dof(n=200, seed=inputs.SEED_BASE + 8),
 }
 MARGIN_T = {
     inputs.LINE2D: [np.array([1.0]), np.array([0.3])],
@@ -142,6 +153,8 @@ MARGIN_T = {
     inputs.RAYS3D: [np.array(v, float) for v in ([2, -2], [0.3, 1.7])],
     inputs.POINTSET2D: [np.array(v, float) for v in ([4, 0], [1.5, -2.5])],
     inputs.AFFINE4D: [np.array(v, float) for v in ([1, 1, 1], [0.2, -0.9, 0.5])],
+    inputs.RADIAL5DOF: [np.array(v, float) for v in ([100, -60, 20, 20, -12, 4, 5],
+                                                     [-3, 1.5, 0.6, 10, -5, 2, -0.3])],
 }
 
 
@@ -181,6 +194,7 @@ def test_planted_mistake_is_caught(name):
                                                                                "pose_lipschitz", "pose_sigma",
                                                                                "pose6_lipschitz", "pose6_sigma",
                                                                                "rays_lipschitz", "points_sigma", "affine_sigma",
+                                                                               "radial_lipschitz", "radial_sigma",
                                                                                "error_step"))])
 def test_margin_mistake_is_caught_by_the_margin_pins(name):
     old, new = MUTANTS[name]

@@ -17,8 +17,8 @@ import brute
 import oracle
 from paper_2107_11810_gb300 import inputs
 
-L2, PL, P3, P6, RY, PS, AF = (oracle.LINE2D, oracle.PLANE3D_SPH, oracle.POSE3DOF, oracle.POSE6DOF,
-                              oracle.RAYS3D, oracle.POINTSET2D, oracle.AFFINE4D)
+L2, PL, P3, P6, RY, PS, AF, RD = (oracle.LINE2D, oracle.PLANE3D_SPH, oracle.POSE3DOF, oracle.POSE6DOF,
+                                  oracle.RAYS3D, oracle.POINTSET2D, oracle.AFFINE4D, oracle.RADIAL5DOF)
 
 
 def small_plane(n, seed, eps=0.08, frac=0.3):
@@ -51,6 +51,10 @@ def small_affine(n, seed, eps=0.15, frac=0.3):
     return inputs.affine4d(n=n, inlier_frac=frac, eps=eps, noise=0.005, seed=seed)
 
 
+def small_radial(n, seed, frac=0.3, levels=3):
+    return inputs.radial5dof(n=n, inlier_frac=frac, levels=levels, seed=seed)
+
+
 CASES = [
     ("line", lambda s: small_line(300, s, eps=0.02)),
     ("plane", lambda s: small_plane(120, s)),
@@ -59,6 +63,7 @@ CASES = [
     ("rays", lambda s: small_rays(300, s)),
     ("points", lambda s: small_points(14, s)),
     ("affine", lambda s: small_affine(150, s)),
+    ("radial", lambda s: small_radial(80, s)),
 ]
 
 
@@ -168,6 +173,11 @@ def relaxed_eps(p, lv):
         lam = (1.0 / np.hypot(p.params[0], p.params[1])).max() + st
     elif p.family == AF:       # |db/da_i| = |x_i| <= 1
         lam = np.abs(p.params[0:3]).max() + st
+    elif p.family == RD:       # |dx/dphi_a| <= (1 + |rho|) |w|, |dx/dy| = |rho|, rho = eta / xi
+        rho = np.abs(p.params[4] / p.params[3])
+        lam_phi = ((1.0 + rho) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st
+        lam_y = rho.max() + st
+        return dep_eps(p) + hL[p.k:] + lam_phi * hL[0:3].sum() + lam_y * hL[3] + 2 * lv["A"][L] + 1e-9
     else:          # |dF/dphi_a| <= (1 + max(|xi|, |eta|)) |w|, |dF/dz| <= max(|xi|, |eta|)
         c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
         lam_phi = ((1.0 + c) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st
@@ -257,7 +267,7 @@ def test_trace_counts_equal_replay_and_monotone(name, mk):
 def test_empty_input():
     for mk in (lambda: small_line(10, 1), lambda: small_plane(10, 1), lambda: small_pose(10, 1),
                lambda: small_pose6(10, 1), lambda: small_rays(10, 1), lambda: small_points(3, 1),
-               lambda: small_affine(10, 1)):
+               lambda: small_affine(10, 1), lambda: small_radial(10, 1)):
         p = mk()
         r = oracle.solve(p.family, p.eps, p.bounds, p.params[:, :0])
         assert r["depth"] == 0
