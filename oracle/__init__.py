@@ -45,10 +45,11 @@ _LIB = os.path.join(_BUILD, "libgvoracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF = 1, 2, 3, 4, 5, 6, 7, 8
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF, POSE7DOF = range(1, 10)
 NO_MERGE, NO_PRUNE, REVERSE = 1, 2, 4
 FAMILY_SHAPE = {LINE2D: (2, 1, 1, 2), PLANE3D_SPH: (3, 2, 3, 3), POSE3DOF: (3, 1, 2, 4), POSE6DOF: (6, 4, 11, 5),
-                RAYS3D: (3, 1, 2, 4), POINTSET2D: (4, 2, 2, 4), AFFINE4D: (4, 3, 3, 4), RADIAL5DOF: (5, 4, 7, 5)}
+                RAYS3D: (3, 1, 2, 4), POINTSET2D: (4, 2, 2, 4), AFFINE4D: (4, 3, 3, 4), RADIAL5DOF: (5, 4, 7, 5),
+                POSE7DOF: (7, 5, 11, 5)}
 """family -> (d, k, number of essential params, number of input params)"""
 
 _CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11", "-fopenmp"]
@@ -82,9 +83,9 @@ def _declare(lib):
     lib.gvo_solve_parallel.restype = i32
     lib.gvo_solve_parallel.argtypes = [i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P]
     lib.gvo_sigma.restype = i32
-    lib.gvo_sigma.argtypes = [i32, i32, i32, P, P]
+    lib.gvo_sigma.argtypes = [i32, i32, i32, P, P, P]
     lib.gvo_lipschitz.restype = i32
-    lib.gvo_lipschitz.argtypes = [i32, i32, i32, P, P]
+    lib.gvo_lipschitz.argtypes = [i32, i32, i32, P, P, P]
     lib.gvo_path_records.restype = i32
     lib.gvo_path_records.argtypes = [i32, i32, i32, P, P, P, i64, i64, i32, P, P, P]
     lib.gvo_rotation.restype = None
@@ -250,26 +251,32 @@ def mask_to_indices(mask: np.ndarray, n: int) -> np.ndarray:
     return np.nonzero(bits)[0]
 
 
-def sigma(family, h, lib=None):
+def _bounds_arg(bounds, d):
+    return None if bounds is None else np.ascontiguousarray(bounds, dtype=np.float64).reshape(2 * d)
+
+
+def sigma(family, h, bounds=None, lib=None):
     """sigma_m: the oracle's bound on the change of basis function m across a cell
     of half-widths h[d] (it sets the essential-parameter snap steps and the
-    canonization error bound, Sec. 3.2)."""
+    canonization error bound, Sec. 3.2).  ``bounds`` (the domain, lo/hi per
+    coordinate) is needed where the bound depends on it (7DoF)."""
     d, k, le, _ = FAMILY_SHAPE[family]
     h = np.ascontiguousarray(h, dtype=np.float64).reshape(d)
     out = np.zeros(le)
-    if (lib or _load()).gvo_sigma(family, d, k, _ptr(h), _ptr(out)):
-        raise ValueError("invalid family")
+    if (lib or _load()).gvo_sigma(family, d, k, _ptr(_bounds_arg(bounds, d)), _ptr(h), _ptr(out)):
+        raise ValueError("invalid family or domain")
     return out
 
 
-def lipschitz(family, t, lib=None):
+def lipschitz(family, t, bounds=None, lib=None):
     """Lambda[j, i]: the oracle's bound on |dF_j/dx_i| for essential parameters t
-    (the free-coordinate term of the surface-box test, Sec. 3.2)."""
+    (the free-coordinate term of the surface-box test, Sec. 3.2); ``bounds`` as for
+    :func:`sigma`."""
     d, k, le, _ = FAMILY_SHAPE[family]
     t = np.ascontiguousarray(t, dtype=np.float64).reshape(le)
     out = np.zeros((d - k) * k)
-    if (lib or _load()).gvo_lipschitz(family, d, k, _ptr(t), _ptr(out)):
-        raise ValueError("invalid family")
+    if (lib or _load()).gvo_lipschitz(family, d, k, _ptr(_bounds_arg(bounds, d)), _ptr(t), _ptr(out)):
+        raise ValueError("invalid family or domain")
     return out.reshape(d - k, k)
 
 

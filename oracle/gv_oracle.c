@@ -63,12 +63,12 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define GVO_MAXD 6
+#define GVO_MAXD 7
 #define GVO_MAXT 11
 #define GVO_MAXL 40
 
 enum { GVO_LINE2D = 1, GVO_PLANE3D_SPH = 2, GVO_POSE3DOF = 3, GVO_POSE6DOF = 4, GVO_RAYS3D = 5,
-       GVO_POINTSET2D = 6, GVO_AFFINE4D = 7, GVO_RADIAL5DOF = 8 };
+       GVO_POINTSET2D = 6, GVO_AFFINE4D = 7, GVO_RADIAL5DOF = 8, GVO_POSE7DOF = 9 };
 enum { GVO_NO_MERGE = 1, GVO_NO_PRUNE = 2, GVO_REVERSE = 4 };
 
 /* ------------------------------------------------------------------------- */
@@ -194,6 +194,7 @@ static int family_shape(int fam, int d, int k, int *le, int *np)
     case GVO_POINTSET2D:  if (d != 4 || k != 2) return 1; *le = 2; *np = 4; return 0;
     case GVO_AFFINE4D:    if (d != 4 || k != 3) return 1; *le = 3; *np = 4; return 0;
     case GVO_RADIAL5DOF:  if (d != 5 || k != 4) return 1; *le = 7; *np = 5; return 0;
+    case GVO_POSE7DOF:    if (d != 7 || k != 5) return 1; *le = 11; *np = 5; return 0;
     default: return 1;
     }
 }
@@ -245,6 +246,22 @@ static void family_sigma(const gvo_problem *p, const double *h, double *sigma)
         sigma[6] = h[3];
         break;
     }
+    case GVO_POSE7DOF: {
+        /* basis (r1, r2, r3 / f, z / f) with f >= f_lo > 0 on the domain: an entry of R
+         * moves by at most hr (as for 6DoF), |1/f(x) - 1/f(c)| <= h_f / f_lo^2, so
+         * r3_i / f moves by at most hr / f_lo + h_f / f_lo^2 and z / f by at most
+         * h_z / f_lo + z_max h_f / f_lo^2 (|r3_i| <= 1, |z| <= z_max) */
+        double hr7 = (h[0] + h[1]) + h[2];
+        double flo = p->lo[4], zmax = fmax(fabs(p->lo[3]), fabs(p->lo[3] + p->W[3]));
+        double inv2 = 1.0 / (flo * flo);
+        double s3 = hr7 / flo + h[4] * inv2;
+        double sz = h[3] / flo + (zmax * h[4]) * inv2;
+        for (int m = 0; m < 3; ++m) sigma[m] = hr7;
+        for (int m = 3; m < 9; ++m) sigma[m] = s3;
+        sigma[9] = sz;
+        sigma[10] = sz;
+        break;
+    }
     }
 }
 
@@ -253,7 +270,8 @@ static int family_nb(int fam, int le)
 {
     /* 6DoF and radial 5DoF: the nine entries of R(phi) and the last free coordinate;
      * rays: x; point sets: (c, d), le = 2 */
-    return (fam == GVO_POSE6DOF || fam == GVO_RADIAL5DOF) ? 10 : (fam == GVO_RAYS3D ? 1 : le);
+    return (fam == GVO_POSE6DOF || fam == GVO_RADIAL5DOF || fam == GVO_POSE7DOF) ? 10
+                                                                                : (fam == GVO_RAYS3D ? 1 : le);
 }
 
 static double pow2_floor(double x)  /* 2^floor(log2 x), exact */
@@ -292,6 +310,7 @@ static int problem_init(gvo_problem *p, int fam, int d, int k, const double *eps
             int e = l < p->Lj[j] ? l : p->Lj[j];
             p->h[l][j] = ldexp(p->W[j], -(e + 1));
         }
+    if (fam == GVO_POSE7DOF && !(p->lo[4] > 0.0)) return 1;   /* the focal length must stay positive */
     if (p->L == 0) return 0;
     /* eps' = eps / L per dependent coordinate */
     double epsp_min = INFINITY;
@@ -324,7 +343,8 @@ static double cell_center(const gvo_problem *p, int l, int j, int64_t i)
 /* ------------------------------------------------------------------------- */
 /* Families (Sec. 3 Eq. 2 line duality; Sec. 4.1 plane fitting; 3DoF posing;   */
 /* Sec. 4.2.3 calibrated 6DoF posing; Sec. 4.3 rays in 3-space; Sec. 4.4      */
-/* point-set similarity alignment; Sec. 4.1 affine hyperplanes in 4-space).   */
+/* point-set similarity alignment; Sec. 4.1 affine hyperplanes in 4-space;    */
+/* Sec. 4.2.4 radial camera; Sec. 4.2.2 7DoF posing with unknown focal).      */
 /* ------------------------------------------------------------------------- */
 
 /* Rotation matrix (row-major) of the axis-angle vector ph, theta = |ph|, by
@@ -393,6 +413,17 @@ static void family_basis(const gvo_problem *p, int l, const int64_t *i, double *
         psi[9] = cell_center(p, l, 3, i[3]);
         break;
     }
+    case GVO_POSE7DOF: {                                      /* r1, r2, r3 / f, z / f */
+        double ph[3];
+        for (int j = 0; j < 3; ++j) ph[j] = cell_center(p, l, j, i[j]);
+        rodrigues(p->inv_fact, ph, psi);
+        double z = cell_center(p, l, 3, i[3]), f = cell_center(p, l, 4, i[4]);
+        psi[6] = psi[6] / f;
+        psi[7] = psi[7] / f;
+        psi[8] = psi[8] / f;
+        psi[9] = z / f;
+        break;
+    }
     }
 }
 
@@ -455,7 +486,8 @@ static void family_lift(const gvo_problem *p, const double *params, int64_t n, i
         r->f[1] = ((gb - v * psi[0]) + u * psi[1]) - c[3];
         break;
     }
-    case GVO_POSE6DOF: {
+    case GVO_POSE6DOF:
+    case GVO_POSE7DOF: {
         /* match (w, xi, eta): x = xi (r3 . w + z) - r1 . w, y = eta (r3 . w + z) - r2 . w
          * (Sec. 4.2.2 with f = 1, Sec. 4.2.3).  Affine in the basis (rows of R, z) with
          * coefficients t = (w, xi w, eta w, xi, eta). */
@@ -473,8 +505,11 @@ static void family_lift(const gvo_problem *p, const double *params, int64_t n, i
         double sx1 = (t[0] * psi[0] + t[1] * psi[1]) + t[2] * psi[2];
         double sy3 = (t[6] * psi[6] + t[7] * psi[7]) + t[8] * psi[8];
         double sy2 = (t[0] * psi[3] + t[1] * psi[4]) + t[2] * psi[5];
-        r->f[0] = ((sx3 + t[9] * psi[9]) - sx1) - c[4];
-        r->f[1] = ((sy3 + t[10] * psi[9]) - sy2) - c[5];
+        /* 7DoF (Sec. 4.2.2): the same with the basis (r1, r2, r3 / f, z / f), x and y
+         * being coordinates 5 and 6 */
+        const int jx = p->fam == GVO_POSE7DOF ? 5 : 4;
+        r->f[0] = ((sx3 + t[9] * psi[9]) - sx1) - c[jx];
+        r->f[1] = ((sy3 + t[10] * psi[9]) - sy2) - c[jx + 1];
         break;
     }
     case GVO_RADIAL5DOF: {
@@ -566,14 +601,16 @@ static void family_residual(const gvo_problem *p, const double *f, const double 
         fo[0] = (f[0] - (t[0] * g->dpsi[0] + t[1] * g->dpsi[1])) - g->shift[2];
         fo[1] = (f[1] - (t[1] * g->dpsi[0] - t[0] * g->dpsi[1])) - g->shift[3];
         break;
-    case GVO_POSE6DOF: {
+    case GVO_POSE6DOF:
+    case GVO_POSE7DOF: {
         const double *d = g->dpsi;
+        const int jx = p->fam == GVO_POSE7DOF ? 5 : 4;
         double sx3 = (t[3] * d[6] + t[4] * d[7]) + t[5] * d[8];
         double sx1 = (t[0] * d[0] + t[1] * d[1]) + t[2] * d[2];
         double sy3 = (t[6] * d[6] + t[7] * d[7]) + t[8] * d[8];
         double sy2 = (t[0] * d[3] + t[1] * d[4]) + t[2] * d[5];
-        fo[0] = (f[0] + ((sx3 + t[9] * d[9]) - sx1)) - g->shift[4];
-        fo[1] = (f[1] + ((sy3 + t[10] * d[9]) - sy2)) - g->shift[5];
+        fo[0] = (f[0] + ((sx3 + t[9] * d[9]) - sx1)) - g->shift[jx];
+        fo[1] = (f[1] + ((sy3 + t[10] * d[9]) - sy2)) - g->shift[jx + 1];
         break;
     }
     case GVO_RADIAL5DOF: {
@@ -627,6 +664,22 @@ static void family_lipschitz(const gvo_problem *p, const double *t, double *lam)
         double lx = nxw + nw, ly = nyw + nw;
         lam[0] = lx; lam[1] = lx; lam[2] = lx; lam[3] = fabs(t[9]);
         lam[4] = ly; lam[5] = ly; lam[6] = ly; lam[7] = fabs(t[10]);
+        break;
+    }
+    case GVO_POSE7DOF: {
+        /* x = xi (r3 . w + z) / f - r1 . w with f >= f_lo: |dx/dphi_a| <= |xi w| / f_lo + |w|,
+         * |dx/dz| <= |xi| / f_lo, |dx/df| = |xi (r3 . w + z)| / f^2 <= (|xi w| + |xi| z_max) / f_lo^2
+         * (and y with eta) */
+        double flo = p->lo[4], zmax = fmax(fabs(p->lo[3]), fabs(p->lo[3] + p->W[3]));
+        double nw = sqrt((t[0] * t[0] + t[1] * t[1]) + t[2] * t[2]);
+        double nxw = sqrt((t[3] * t[3] + t[4] * t[4]) + t[5] * t[5]);
+        double nyw = sqrt((t[6] * t[6] + t[7] * t[7]) + t[8] * t[8]);
+        double inv2 = 1.0 / (flo * flo);
+        double lx7 = nxw / flo + nw, ly7 = nyw / flo + nw;
+        lam[0] = lx7; lam[1] = lx7; lam[2] = lx7; lam[3] = fabs(t[9]) / flo;
+        lam[4] = (nxw + fabs(t[9]) * zmax) * inv2;
+        lam[5] = ly7; lam[6] = ly7; lam[7] = ly7; lam[8] = fabs(t[10]) / flo;
+        lam[9] = (nyw + fabs(t[10]) * zmax) * inv2;
         break;
     }
     case GVO_RADIAL5DOF: {
@@ -1037,24 +1090,37 @@ void gvo_rotation(const double *ph, double *R)
 }
 
 /* sigma[le]: the bound family_sigma gives for a cell of half-widths h[d]. */
-int gvo_sigma(int fam, int d, int k, const double *h, double *sigma)
+static int margin_problem(gvo_problem *p, int fam, int d, int k, const double *bounds)
+{
+    memset(p, 0, sizeof(*p));
+    if (family_shape(fam, d, k, &p->le, &p->np)) return 1;
+    p->fam = fam; p->d = d; p->k = k; p->nd = d - k; p->nb = family_nb(fam, p->le);
+    if (bounds)
+        for (int j = 0; j < d; ++j) {
+            p->lo[j] = bounds[2 * j];
+            p->W[j] = bounds[2 * j + 1] - bounds[2 * j];
+        }
+    /* the 7DoF margins depend on the domain (its smallest focal length) */
+    if (fam == GVO_POSE7DOF && !(bounds && p->lo[4] > 0.0)) return 1;
+    return 0;
+}
+
+/* sigma[le] for half-widths h[d]; bounds[2d] (lo, hi per coordinate) may be NULL
+ * for families whose bound does not depend on the domain. */
+int gvo_sigma(int fam, int d, int k, const double *bounds, const double *h, double *sigma)
 {
     gvo_problem p;
-    memset(&p, 0, sizeof(p));
-    if (family_shape(fam, d, k, &p.le, &p.np)) return 1;
-    p.fam = fam; p.d = d; p.k = k; p.nd = d - k; p.nb = family_nb(fam, p.le);
+    if (margin_problem(&p, fam, d, k, bounds)) return 1;
     family_sigma(&p, h, sigma);
     return 0;
 }
 
 /* lam[(d-k)*k]: the Lipschitz bounds family_lipschitz gives for the essential
  * parameters t[le] (dependent coordinate j, free coordinate i at j*k + i). */
-int gvo_lipschitz(int fam, int d, int k, const double *t, double *lam)
+int gvo_lipschitz(int fam, int d, int k, const double *bounds, const double *t, double *lam)
 {
     gvo_problem p;
-    memset(&p, 0, sizeof(p));
-    if (family_shape(fam, d, k, &p.le, &p.np)) return 1;
-    p.fam = fam; p.d = d; p.k = k; p.nd = d - k; p.nb = family_nb(fam, p.le);
+    if (margin_problem(&p, fam, d, k, bounds)) return 1;
     family_lipschitz(&p, t, lam);
     return 0;
 }

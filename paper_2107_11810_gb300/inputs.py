@@ -35,6 +35,9 @@ Surface parameters are FP64, structure-of-arrays ``params[P, n]``:
   voting space (phi1, phi2, phi3, y, x) of the radial camera with rows
   (r1, -y) and (r2, x), where eta (r1 . w - y) = xi (r2 . w + x), i.e.
   x = eta (r1 . w - y) / xi - r2 . w.
+* ``POSE7DOF``    (camera posing with unknown focal length, Sec. 4.2.2): P = 5, rows
+  (w1, w2, w3, xi, eta) as for 6DoF; voting space (phi1, phi2, phi3, z, f, x, y) with
+  x = xi (r3 . w + z) / f - r1 . w and y = eta (r3 . w + z) / f - r2 . w.
 """
 from __future__ import annotations
 
@@ -43,11 +46,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF = 1, 2, 3, 4, 5, 6, 7, 8
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF, POSE7DOF = range(1, 10)
 FAMILY_NAMES = {LINE2D: "LINE2D", PLANE3D_SPH: "PLANE3D_SPH", POSE3DOF: "POSE3DOF", POSE6DOF: "POSE6DOF",
-                RAYS3D: "RAYS3D", POINTSET2D: "POINTSET2D", AFFINE4D: "AFFINE4D", RADIAL5DOF: "RADIAL5DOF"}
+                RAYS3D: "RAYS3D", POINTSET2D: "POINTSET2D", AFFINE4D: "AFFINE4D", RADIAL5DOF: "RADIAL5DOF",
+                POSE7DOF: "POSE7DOF"}
 FAMILY_DK = {LINE2D: (2, 1), PLANE3D_SPH: (3, 2), POSE3DOF: (3, 1), POSE6DOF: (6, 4), RAYS3D: (3, 1),
-             POINTSET2D: (4, 2), AFFINE4D: (4, 3), RADIAL5DOF: (5, 4)}
+             POINTSET2D: (4, 2), AFFINE4D: (4, 3), RADIAL5DOF: (5, 4), POSE7DOF: (7, 5)}
 SEED_BASE = 2107118100
 
 
@@ -312,6 +316,35 @@ def pose6dof(n: int = 5000, inlier_frac: float = 0.05, prior_deg: float = 30.0, 
     truth = np.concatenate([phi, [t[2], t[0], t[1]]])
     return Problem(POSE6DOF, eps, bounds, np.ascontiguousarray(out), truth, inliers, "pose6dof",
                    dict(inlier_frac=inlier_frac, prior=prior, prior_deg=prior_deg, levels=levels))
+
+
+def pose7dof(n: int = 5000, inlier_frac: float = 0.05, prior_deg: float = 30.0, box: float = 10.0,
+             levels: int = 7, noise_deg: float = 0.1, points=(20.0, 20.0, 5.0), fov: float = 1.0,
+             focal=(0.8, 1.2), focal_range=(0.6, 1.3), seed: int = SEED_BASE + 9,
+             rng: np.random.Generator | None = None) -> Problem:
+    """Camera posing with unknown focal length (7DoF, Sec. 4.2.2).  As the
+    calibrated camera (points, prior, rotation, camera-frame translation
+    (x, y, z) ~ U[0, box]^3, inliers and outliers), with a focal length
+    f ~ U[focal]: inliers are seen at f (tan a, tan b), outliers at f times a
+    random image point of the field of view.  Voting domain phi_prior +- prior per
+    axis, z in [0, box], f in focal_range times the true f (the paper bounds f
+    within [0.6, 1.3] of the ground truth), (x, y) in [0, box]^2; every coordinate
+    splits ``levels`` times, and the tolerance of x and y is their leaf width."""
+    if rng is None:
+        rng = np.random.default_rng(seed)
+    p6 = pose6dof(n=n, inlier_frac=inlier_frac, prior_deg=prior_deg, box=box, levels=levels,
+                  noise_deg=noise_deg, points=points, fov=fov, rng=rng)
+    f = rng.uniform(*focal)
+    out = p6.params.copy()
+    out[3:5] *= f
+    lo6, hi6 = p6.bounds[0::2], p6.bounds[1::2]
+    lo = np.concatenate([lo6[:4], [focal_range[0] * f], lo6[4:]])
+    hi = np.concatenate([hi6[:4], [focal_range[1] * f], hi6[4:]])
+    bounds = np.stack([lo, hi], axis=1).reshape(-1)
+    eps = (hi - lo) / 2.0 ** levels
+    truth = np.concatenate([p6.truth[:4], [f], p6.truth[4:]])
+    meta = dict(p6.meta, focal=f)
+    return Problem(POSE7DOF, eps, bounds, np.ascontiguousarray(out), truth, p6.inliers, "pose7dof", meta)
 
 
 def radial5dof(n: int = 5000, inlier_frac: float = 0.05, prior_deg: float = 30.0, box: float = 10.0,

@@ -11,7 +11,7 @@ import itertools
 
 import numpy as np
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF = 1, 2, 3, 4, 5, 6, 7, 8
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF, POSE7DOF = range(1, 10)
 
 
 def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.ndarray:
@@ -56,6 +56,17 @@ def vertical_residuals(family: int, params: np.ndarray, pts: np.ndarray) -> np.n
         depth_ = Rw[:, 2, :] + z
         fx = xi[None, :] * depth_ - Rw[:, 0, :]
         fy = eta[None, :] * depth_ - Rw[:, 1, :]
+        return np.stack([x - fx, y - fy], axis=-1)
+    if family == POSE7DOF:               # unknown focal: f (X_1, X_2) / X_3 = (xi, eta) (Sec. 4.2.2)
+        from scipy.spatial.transform import Rotation
+        w = np.asarray(params[0:3], float)
+        xi, eta = params[3], params[4]
+        Rm = Rotation.from_rotvec(pts[:, 0:3]).as_matrix()
+        Rw = np.einsum("pij,jn->pin", Rm, w)
+        z, f, x, y = pts[:, 3:4], pts[:, 4:5], pts[:, 5:6], pts[:, 6:7]
+        depth_ = Rw[:, 2, :] + z
+        fx = xi[None, :] * depth_ / f - Rw[:, 0, :]
+        fy = eta[None, :] * depth_ / f - Rw[:, 1, :]
         return np.stack([x - fx, y - fy], axis=-1)
     if family == RADIAL5DOF:             # radial camera rows (r1, -y), (r2, x) (Sec. 4.2.4)
         from scipy.spatial.transform import Rotation

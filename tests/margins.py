@@ -28,7 +28,7 @@ import numpy as np
 import brute
 import oracle
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF = 1, 2, 3, 4, 5, 6, 7, 8
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF, POSE7DOF = range(1, 10)
 
 
 def _rot(x):
@@ -63,6 +63,14 @@ def basis(family: int, x: np.ndarray) -> np.ndarray:
         fx = np.concatenate([-Rm[..., 0, :], Rm[..., 2, :], zero3, z, zero1], axis=-1)
         fy = np.concatenate([-Rm[..., 1, :], zero3, Rm[..., 2, :], zero1, z], axis=-1)
         return np.concatenate([fx, fy], axis=-1)
+    if family == POSE7DOF:          # as POSE6DOF with r3 / f and z / f (free coords phi, z, f)
+        Rm = _rot(x[..., 0:3])
+        z, f = x[..., 3:4], x[..., 4:5]
+        zero3, zero1 = np.zeros(x.shape[:-1] + (3,)), np.zeros(x.shape[:-1] + (1,))
+        r3f = Rm[..., 2, :] / f
+        fx = np.concatenate([-Rm[..., 0, :], r3f, zero3, z / f, zero1], axis=-1)
+        fy = np.concatenate([-Rm[..., 1, :], zero3, r3f, zero1, z / f], axis=-1)
+        return np.concatenate([fx, fy], axis=-1)
     if family == RADIAL5DOF:        # t = (rho w, w, rho): x = rho w . r1 - w . r2 - rho y
         Rm = _rot(x[..., 0:3])
         return np.concatenate([Rm[..., 0, :], -Rm[..., 1, :], -x[..., 3:4]], axis=-1)
@@ -88,7 +96,7 @@ def t_part(family: int, t: np.ndarray, x: np.ndarray) -> np.ndarray:
         return np.stack([psi[..., :2] @ t, psi[..., 2:] @ t], axis=-1)
     if family == AFFINE4D:
         return (psi @ np.asarray(t, float))[..., None]
-    if family == POSE6DOF:
+    if family in (POSE6DOF, POSE7DOF):
         t = np.asarray(t, float)
         return np.stack([psi[..., :11] @ t, psi[..., 11:] @ t], axis=-1)
     if family == RADIAL5DOF:
@@ -119,8 +127,8 @@ def check_sigma(p, cells_per_level=4, points=100_000, seed=0, lib=None):
     lo, k = p.bounds[0::2], p.k
     worst = []
     for l in range(lv["L"]):
-        sig = oracle.sigma(p.family, lv["h"][l], lib=lib)
-        if p.family in (POSE6DOF, POINTSET2D):
+        sig = oracle.sigma(p.family, lv["h"][l], bounds=p.bounds, lib=lib)
+        if p.family in (POSE6DOF, POSE7DOF, POINTSET2D):
             sig = np.concatenate([sig, sig])          # the two dependent equations' functions
         w = 0.0
         for _ in range(cells_per_level):
@@ -137,7 +145,9 @@ def check_sigma(p, cells_per_level=4, points=100_000, seed=0, lib=None):
 
 def check_lipschitz(p, ts, cells_per_level=3, points=100_000, seed=0, lib=None):
     """max over sampled cells and essential parameters t of
-    |F(x; t) - F(c; t)| / (sum_i Lambda_ji(t) h_i), per level (must be <= 1)."""
+    |F(x; t) - F(c; t)| / (sum_i Lambda_ji(t) h_i), per level (must be <= 1), and of
+    the same along each free coordinate alone: |F(c + u h_i e_i) - F(c)| /
+    (Lambda_ji h_i) (so that a loose term cannot hide a missing one)."""
     rng = np.random.default_rng(seed)
     lv = oracle.levels(p.family, p.eps, p.bounds, lib=lib)
     lo, k = p.bounds[0::2], p.k
@@ -149,11 +159,20 @@ def check_lipschitz(p, ts, cells_per_level=3, points=100_000, seed=0, lib=None):
             ci = random_cell(lv["Lj"], l, rng)
             c = cell_center(lo, h, ci)[:k]
             x = cell_points(c, h[:k], points, rng)
+            u = np.concatenate([np.linspace(-1.0, 1.0, 65), rng.uniform(-1.0, 1.0, 64)])
             for t in ts:
-                lam = oracle.lipschitz(p.family, t, lib=lib)
-                dF = np.abs(t_part(p.family, t, x) - t_part(p.family, t, c[None])).max(axis=0)
+                lam = oracle.lipschitz(p.family, t, bounds=p.bounds, lib=lib)
+                F0 = t_part(p.family, t, c[None])
+                dF = np.abs(t_part(p.family, t, x) - F0).max(axis=0)
                 bound = lam @ h[:k]
                 w = max(w, float((dF / bound).max()))
+                for i in range(k):                  # one free coordinate at a time
+                    xi = np.repeat(c[None], len(u), axis=0)
+                    xi[:, i] += u * h[i]
+                    dFi = np.abs(t_part(p.family, t, xi) - F0).max(axis=0)
+                    # a term that is linear in x_i meets its bound exactly: allow rounding
+                    bi = lam[:, i] * h[i] * (1.0 + 1e-9) + 1e-12 * (1.0 + np.abs(F0[0]))
+                    w = max(w, float((dFi / bi).max()))
         worst.append(w)
     return np.array(worst)
 

@@ -7,7 +7,8 @@ own, against the surface equations (tests/margins.py), on the level structures
 of the benchmark workloads (2D line eps 0.01, 3D plane eps 0.005, 3DoF camera
 0.25 m / 0.5 deg, 6DoF camera with a +-30 deg rotation prior in a 10 m box, 7
 levels, rays in the unit cube eps 0.002, point sets eps 0.01, affine hyperplanes in 4-space eps 0.01, the radial
-camera with a +-30 deg rotation prior in a 10 m box, 7 levels):
+camera with a +-30 deg rotation prior in a 10 m box, 7 levels, and the same with an unknown focal length in
+[0.6, 1.3] of the true one):
 
 * sigma_m bounds the change of every basis function across every level's cells
   (Sec. 3.2: the essential parameters are rounded to a step scaled by how much
@@ -36,6 +37,7 @@ WORKLOADS = {
     "points": lambda: inputs.pointset2d(m=20, seed=inputs.SEED_BASE + 6),
     "affine": lambda: inputs.affine4d(n=400, seed=inputs.SEED_BASE + 7),
     "radial": lambda: inputs.radial5dof(n=400, seed=inputs.SEED_BASE + 8),
+    "pose7": lambda: inputs.pose7dof(n=400, seed=inputs.SEED_BASE + 9),
 }
 
 
@@ -77,7 +79,7 @@ def essential_samples(p, rng):
             ts.append(np.concatenate([rho * w, w, [rho]]))
         ts += [rng.normal(0.0, 10.0, 7) for _ in range(4)]
         ts += [np.array([100, -60, 20, 20, -12, 4, 5], float)]
-    else:                      # t = (w, xi w, eta w, xi, eta), plus arbitrary coefficient vectors
+    else:                      # 6DoF, 7DoF: t = (w, xi w, eta w, xi, eta), plus arbitrary coefficient vectors
         ts = []
         for i in rng.choice(p.n, 20, replace=False):
             w, xi, eta = p.params[0:3, i], p.params[3, i], p.params[4, i]

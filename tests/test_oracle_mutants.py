@@ -64,6 +64,11 @@ MUTANTS = {
     "radial_lift_rho": ("double rho = eta / xi;", "double rho = xi / eta;"),
     "radial_lipschitz_without_w": ("double lx = nrw + nw;", "double lx = nrw;"),
     "radial_sigma_one_axis": ("double hphi = (h[0] + h[1]) + h[2];", "double hphi = h[2];"),
+    "pose7_sigma_z_without_focal": ("double sz = h[3] / flo + (zmax * h[4]) * inv2;", "double sz = h[3] / flo;"),
+    "pose7_lipschitz_focal_without_square": ("lam[4] = (nxw + fabs(t[9]) * zmax) * inv2;",
+                                             "lam[4] = nxw + fabs(t[9]) * zmax;"),
+    "pose7_lipschitz_z_without_focal": ("lam[3] = fabs(t[9]) / flo;", "lam[3] = fabs(t[9]);"),
+    "pose7_basis_z_not_divided": ("psi[9] = z / f;", "psi[9] = z;"),
     "pose_sigma_halved": ("(a, b) */\n        sigma[0] = h[0];\n        sigma[1] = h[0];",
                           "(a, b) */\n        sigma[0] = 0.5 * h[0];\n        sigma[1] = 0.5 * h[0];"),
     "error_step_missing_essential_term": ("delta = delta + (p->s_t[l][m] * 0.5) * sigma[m];",
@@ -80,6 +85,7 @@ CASES = {
     inputs.POINTSET2D: lambda s: inputs.pointset2d(m=14, eps=0.16, noise=0.002, seed=s),
     inputs.AFFINE4D: lambda s: inputs.affine4d(n=150, inlier_frac=0.3, eps=0.15, noise=0.005, seed=s),
     inputs.RADIAL5DOF: lambda s: inputs.radial5dof(n=80, inlier_frac=0.3, levels=3, seed=s),
+    inputs.POSE7DOF: lambda s: inputs.pose7dof(n=60, inlier_frac=0.3, levels=3, seed=s),
 }
 
 
@@ -116,6 +122,12 @@ def pins_hold(lib, fam, seed):
         free = ((1.0 / np.hypot(p.params[0], p.params[1])).max() + st) * hL[: p.k].sum()
     elif p.family == inputs.AFFINE4D:
         free = (np.abs(p.params[0:3]).max() + st) * hL[: p.k].sum()
+    elif p.family == inputs.POSE7DOF:
+        flo, zmax = p.bounds[8], max(abs(p.bounds[6]), abs(p.bounds[7]))
+        c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
+        nw = np.linalg.norm(p.params[0:3], axis=0)
+        free = ((((1.0 + c / flo) * nw).max() + 4 * st * (1.0 + 1.0 / flo)) * hL[0:3].sum()
+                + (c.max() + st) / flo * hL[3] + ((c * (nw + zmax)).max() + 4 * st * (1.0 + zmax)) / flo ** 2 * hL[4])
     elif p.family == inputs.RADIAL5DOF:
         rho = np.abs(p.params[4] / p.params[3])
         free = ((((1.0 + rho) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st) * hL[0:3].sum()
@@ -143,6 +155,7 @@ MARGIN_CASES = {
     inputs.POINTSET2D: lambda: inputs.pointset2d(m=15, seed=inputs.SEED_BASE + 6),
     inputs.AFFINE4D: lambda: inputs.affine4d(n=200, seed=inputs.SEED_BASE + 7),
     inputs.RADIAL5DOF: lambda: inputs.radial5dof(n=200, seed=inputs.SEED_BASE + 8),
+    inputs.POSE7DOF: lambda: inputs.pose7dof(n=200, seed=inputs.SEED_BASE + 9),
 }
 MARGIN_T = {
     inputs.LINE2D: [np.array([1.0]), np.array([0.3])],
@@ -155,6 +168,8 @@ MARGIN_T = {
     inputs.AFFINE4D: [np.array(v, float) for v in ([1, 1, 1], [0.2, -0.9, 0.5])],
     inputs.RADIAL5DOF: [np.array(v, float) for v in ([100, -60, 20, 20, -12, 4, 5],
                                                      [-3, 1.5, 0.6, 10, -5, 2, -0.3])],
+    inputs.POSE7DOF: [np.array(v, float) for v in ([20, 20, 5, 20, 20, 5, -20, -20, -5, 1, -1],
+                                                   [3, -14, 2, 1, -5, 0.5, 2, -9, 1, 0.4, 0.6])],
 }
 
 
@@ -195,6 +210,7 @@ def test_planted_mistake_is_caught(name):
                                                                                "pose6_lipschitz", "pose6_sigma",
                                                                                "rays_lipschitz", "points_sigma", "affine_sigma",
                                                                                "radial_lipschitz", "radial_sigma",
+                                                                               "pose7_sigma", "pose7_lipschitz",
                                                                                "error_step"))])
 def test_margin_mistake_is_caught_by_the_margin_pins(name):
     old, new = MUTANTS[name]

@@ -17,8 +17,9 @@ import brute
 import oracle
 from paper_2107_11810_gb300 import inputs
 
-L2, PL, P3, P6, RY, PS, AF, RD = (oracle.LINE2D, oracle.PLANE3D_SPH, oracle.POSE3DOF, oracle.POSE6DOF,
-                                  oracle.RAYS3D, oracle.POINTSET2D, oracle.AFFINE4D, oracle.RADIAL5DOF)
+L2, PL, P3, P6, RY, PS, AF, RD, P7 = (oracle.LINE2D, oracle.PLANE3D_SPH, oracle.POSE3DOF, oracle.POSE6DOF,
+                                      oracle.RAYS3D, oracle.POINTSET2D, oracle.AFFINE4D, oracle.RADIAL5DOF,
+                                      oracle.POSE7DOF)
 
 
 def small_plane(n, seed, eps=0.08, frac=0.3):
@@ -55,6 +56,10 @@ def small_radial(n, seed, frac=0.3, levels=3):
     return inputs.radial5dof(n=n, inlier_frac=frac, levels=levels, seed=seed)
 
 
+def small_pose7(n, seed, frac=0.3, levels=3):
+    return inputs.pose7dof(n=n, inlier_frac=frac, levels=levels, seed=seed)
+
+
 CASES = [
     ("line", lambda s: small_line(300, s, eps=0.02)),
     ("plane", lambda s: small_plane(120, s)),
@@ -64,6 +69,7 @@ CASES = [
     ("points", lambda s: small_points(14, s)),
     ("affine", lambda s: small_affine(150, s)),
     ("radial", lambda s: small_radial(80, s)),
+    ("pose7", lambda s: small_pose7(60, s)),
 ]
 
 
@@ -173,6 +179,17 @@ def relaxed_eps(p, lv):
         lam = (1.0 / np.hypot(p.params[0], p.params[1])).max() + st
     elif p.family == AF:       # |db/da_i| = |x_i| <= 1
         lam = np.abs(p.params[0:3]).max() + st
+    elif p.family == P7:       # as 6DoF with 1/f: |dF/dphi_a| <= (1 + c/f_lo) |w|, |dF/dz| <= c/f_lo,
+        # |dF/df| <= c (|w| + z_max)/f_lo^2, c = max(|xi|, |eta|)
+        flo = p.bounds[8]
+        zmax = max(abs(p.bounds[6]), abs(p.bounds[7]))
+        c = np.maximum(np.abs(p.params[3]), np.abs(p.params[4]))
+        nw = np.linalg.norm(p.params[0:3], axis=0)
+        lam_phi = ((1.0 + c / flo) * nw).max() + 4 * st * (1.0 + 1.0 / flo)
+        lam_z = (c.max() + st) / flo
+        lam_f = ((c * (nw + zmax)).max() + 4 * st * (1.0 + zmax)) / flo ** 2
+        return (dep_eps(p) + hL[p.k:] + lam_phi * hL[0:3].sum() + lam_z * hL[3] + lam_f * hL[4]
+                + 2 * lv["A"][L] + 1e-9)
     elif p.family == RD:       # |dx/dphi_a| <= (1 + |rho|) |w|, |dx/dy| = |rho|, rho = eta / xi
         rho = np.abs(p.params[4] / p.params[3])
         lam_phi = ((1.0 + rho) * np.linalg.norm(p.params[0:3], axis=0)).max() + 4 * st
@@ -267,7 +284,7 @@ def test_trace_counts_equal_replay_and_monotone(name, mk):
 def test_empty_input():
     for mk in (lambda: small_line(10, 1), lambda: small_plane(10, 1), lambda: small_pose(10, 1),
                lambda: small_pose6(10, 1), lambda: small_rays(10, 1), lambda: small_points(3, 1),
-               lambda: small_affine(10, 1), lambda: small_radial(10, 1)):
+               lambda: small_affine(10, 1), lambda: small_radial(10, 1), lambda: small_pose7(10, 1)):
         p = mk()
         r = oracle.solve(p.family, p.eps, p.bounds, p.params[:, :0])
         assert r["depth"] == 0
