@@ -83,7 +83,12 @@ typedef enum {
  *   VOTE_AFFINE4D    d=4 k=3: coords (a1, a2, a3, b); input rows (x1, x2, x3, x4)
  *                    of points of 4-space; surface b = x4 - (a1 x1 + a2 x2 + a3 x3)
  *                    (hyperplane fitting in the affine form, Sec. 4.1);
- *                    16 children. */
+ *                    16 children.
+ *   VOTE_RADIAL5DOF  d=5 k=4: coords (phi1, phi2, phi3, y, x) of the radial camera
+ *                    with rows (r1, -y) and (r2, x) (unknown focal length,
+ *                    Sec. 4.2.4); input rows (w1, w2, w3, xi, eta) as for 6DoF
+ *                    (xi != 0); surface x = eta (r1 . w - y) / xi - r2 . w; the
+ *                    tolerance of x is a constant distance; 32 children. */
 typedef enum {
     VOTE_LINE2D = 1,
     VOTE_PLANE3D_SPH = 2,
@@ -91,7 +96,8 @@ typedef enum {
     VOTE_POSE6DOF = 4,
     VOTE_RAYS3D = 5,
     VOTE_POINTSET2D = 6,
-    VOTE_AFFINE4D = 7
+    VOTE_AFFINE4D = 7,
+    VOTE_RADIAL5DOF = 8
 } vote_family;
 
 /* Options for vote_set_option. */

@@ -169,7 +169,7 @@ __device__ __forceinline__ uint64_t child_key(const Problem &P, uint64_t key, in
 // basis value is the last free coordinate (its change is the exact child shift).
 // ---------------------------------------------------------------------------
 enum { FAM_LINE2D = 1, FAM_PLANE3D_SPH = 2, FAM_POSE3DOF = 3, FAM_POSE6DOF = 4, FAM_RAYS3D = 5, FAM_POINTSET2D = 6,
-       FAM_AFFINE4D = 7 };
+       FAM_AFFINE4D = 7, FAM_RADIAL5DOF = 8 };
 
 template <int FAM> struct Fam;
 
@@ -532,6 +532,70 @@ template <> struct Fam<FAM_POSE6DOF> {
         const float nyw = sqrtf(__fmaf_rn(qt[8], qt[8], __fmaf_rn(qt[7], qt[7], qt[6] * qt[6])));
         R[0] = __fmaf_rn(lev.lam_c[0], nxw + nw, __fmaf_rn(lev.lam_c[1], fabsf(qt[9]), lev.rc0[0]));
         R[1] = __fmaf_rn(lev.lam_c[2], nyw + nw, __fmaf_rn(lev.lam_c[3], fabsf(qt[10]), lev.rc0[1]));
+    }
+};
+
+// RADIAL5DOF: radial camera with unknown focal length (Sec. 4.2.4); coords (phi1, phi2,
+// phi3, y, x), the camera's rows (r1, -y) and (r2, x).  A match (w, xi, eta) gives
+// eta (r1 . w - y) = xi (r2 . w + x): with rho = eta / xi, x = rho (r1 . w) - r2 . w -
+// rho y, affine in the basis psi = (rows of R(phi), y) (r3 unused) with coefficients
+// t = (rho w, w, rho).
+template <> struct Fam<FAM_RADIAL5DOF> {
+    static constexpr int D = 5, K = 4, ND = 1, LE = 7, NP = 5, NB = 10, NFP = 8;
+    static constexpr bool LINEAR_BASIS = false, LINEAR_TAIL = true;
+    __host__ __device__ static constexpr bool uses(int, int) { return true; }
+    __device__ static void basis(const Problem &P, const double *c, double *psi) {
+        Fam<FAM_POSE6DOF>::rotation(P, c, psi);
+        psi[9] = c[3];
+    }
+    // the t-dependent part of x for basis values (or their changes) p
+    __device__ static double tpart(const double *t, const double *p) {
+        const double s1 = dadd(dadd(dmul(t[0], p[0]), dmul(t[1], p[1])), dmul(t[2], p[2]));
+        const double s2 = dadd(dadd(dmul(t[3], p[3]), dmul(t[4], p[4])), dmul(t[5], p[5]));
+        return dsub(dsub(s1, s2), dmul(t[6], p[9]));
+    }
+    __device__ static void lift(const double *prm, int64_t n, int64_t i, const double *c, const double *psi,
+                                double *f, double *t) {
+        const double xi = prm[3 * n + i], eta = prm[4 * n + i];
+        const double rho = ddiv(eta, xi);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double w = prm[j * n + i];
+            t[j] = dmul(rho, w);
+            t[3 + j] = w;
+        }
+        t[6] = rho;
+        f[0] = dsub(tpart(t, psi), c[4]);
+    }
+    __device__ static void residual64(const double *f, const double *t, const double *dpsi, const double *sh,
+                                      double *fo) {
+        fo[0] = dsub(dadd(f[0], tpart(t, dpsi)), sh[4]);
+    }
+    __device__ static void partial64(const double *f, const double *t, const double *dpsi, double *p) {
+        p[0] = dadd(f[0], tpart(t, dpsi));
+    }
+    // |dx/dphi_a| <= |rho w| + |w| (as for 6DoF), dx/dy = -rho
+    __device__ static void lipschitz64(const double *t, double *lam) {
+        const double nrw = dsqrt(dadd(dadd(dmul(t[0], t[0]), dmul(t[1], t[1])), dmul(t[2], t[2])));
+        const double nw = dsqrt(dadd(dadd(dmul(t[3], t[3]), dmul(t[4], t[4])), dmul(t[5], t[5])));
+        const double lx = dadd(nrw, nw);
+        lam[0] = lx; lam[1] = lx; lam[2] = lx; lam[3] = fabs(t[6]);
+    }
+    // g[m]: coefficient of t_m in x for basis changes dpsi
+    __device__ static void coef(const double *dpsi, double *g) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            g[i] = dpsi[i];                  // rho w . r1
+            g[3 + i] = -dpsi[3 + i];         // -w . r2
+        }
+        g[6] = -dpsi[9];                     // -rho y
+    }
+    // s_t equal for the six rotation coefficients: |rho w| + |w| = s_t (|q_rw| + |q_w|);
+    // lam_c: [rotation, y]
+    __device__ static void radius32(const Level &lev, const float *qt, float *R) {
+        const float nrw = sqrtf(__fmaf_rn(qt[2], qt[2], __fmaf_rn(qt[1], qt[1], qt[0] * qt[0])));
+        const float nw = sqrtf(__fmaf_rn(qt[5], qt[5], __fmaf_rn(qt[4], qt[4], qt[3] * qt[3])));
+        R[0] = __fmaf_rn(lev.lam_c[0], nrw + nw, __fmaf_rn(lev.lam_c[1], fabsf(qt[6]), lev.rc0[0]));
     }
 };
 

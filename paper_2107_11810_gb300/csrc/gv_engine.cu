@@ -124,6 +124,7 @@ static int family_shape(int fam, int d, int k, int *le, int *np) {
     case VOTE_RAYS3D: if (d != 3 || k != 1) return 1; *le = 2; *np = 4; return 0;
     case VOTE_POINTSET2D: if (d != 4 || k != 2) return 1; *le = 2; *np = 4; return 0;
     case VOTE_AFFINE4D: if (d != 4 || k != 3) return 1; *le = 3; *np = 4; return 0;
+    case VOTE_RADIAL5DOF: if (d != 5 || k != 4) return 1; *le = 7; *np = 5; return 0;
     default: return 1;
     }
 }
@@ -161,6 +162,13 @@ static void family_sigma(int fam, const double *h, double *sigma) {
         for (int m = 0; m < 9; ++m) sigma[m] = hr;
         sigma[9] = h[3];
         sigma[10] = h[3];
+        break;
+    }
+    case VOTE_RADIAL5DOF: {
+        // the six entries of rows r1, r2 (as for 6DoF); y is linear
+        const double hr = (h[0] + h[1]) + h[2];
+        for (int m = 0; m < 6; ++m) sigma[m] = hr;
+        sigma[6] = h[3];
         break;
     }
     }
@@ -319,11 +327,19 @@ static vote_status problem_init(vote_ctx *c, int fam, int d, int k, const double
             v.lam_c[3] = (float)(h[l + 1][3] * s_t[l][10] / P.s_f[1]);
             break;
         }
+        case VOTE_RADIAL5DOF: {  // (|rho w| + |w|) sum h1_phi + |rho| h1_y
+            const double hphi = (h[l + 1][0] + h[l + 1][1]) + h[l + 1][2];
+            v.lam_c[0] = (float)(hphi * s_t[l][0] / P.s_f[0]);
+            v.lam_c[1] = (float)(h[l + 1][3] * s_t[l][6] / P.s_f[0]);
+            break;
+        }
         }
         bool equal = true;
         if (fam == VOTE_PLANE3D_SPH || fam == VOTE_POSE3DOF) equal = s_t[l][0] == s_t[l][1];
         if (fam == VOTE_POSE6DOF)
             for (int m = 1; m < 9; ++m) equal &= s_t[l][m] == s_t[l][0];
+        if (fam == VOTE_RADIAL5DOF)
+            for (int m = 1; m < 6; ++m) equal &= s_t[l][m] == s_t[l][0];
         if (!equal) {
             set_err("internal: unequal essential steps at level %d", l);
             return VOTE_EINTERNAL;
@@ -352,6 +368,13 @@ static void lambda_max(int fam, const double *T, double *lam) {
         lam[3] = T[9];
         lam[4] = lam[5] = lam[6] = nyw + nw;
         lam[7] = T[10];
+        break;
+    }
+    case VOTE_RADIAL5DOF: {
+        const double nrw = std::sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+        const double nw = std::sqrt(T[3] * T[3] + T[4] * T[4] + T[5] * T[5]);
+        lam[0] = lam[1] = lam[2] = nrw + nw;
+        lam[3] = T[6];
         break;
     }
     }
@@ -436,6 +459,7 @@ static int family_nfp(int fam) {
     case VOTE_RAYS3D: return Fam<FAM_RAYS3D>::NFP;
     case VOTE_POINTSET2D: return Fam<FAM_POINTSET2D>::NFP;
     case VOTE_AFFINE4D: return Fam<FAM_AFFINE4D>::NFP;
+    case VOTE_RADIAL5DOF: return Fam<FAM_RADIAL5DOF>::NFP;
     default: return Fam<FAM_POSE6DOF>::NFP;
     }
 }
@@ -447,13 +471,14 @@ static int family_nb(int fam) {
     case VOTE_RAYS3D: return Fam<FAM_RAYS3D>::NB;
     case VOTE_POINTSET2D: return Fam<FAM_POINTSET2D>::NB;
     case VOTE_AFFINE4D: return Fam<FAM_AFFINE4D>::NB;
+    case VOTE_RADIAL5DOF: return Fam<FAM_RADIAL5DOF>::NB;
     default: return Fam<FAM_POSE6DOF>::NB;
     }
 }
 static_assert((int)VOTE_LINE2D == FAM_LINE2D && (int)VOTE_PLANE3D_SPH == FAM_PLANE3D_SPH &&
                   (int)VOTE_POSE3DOF == FAM_POSE3DOF && (int)VOTE_POSE6DOF == FAM_POSE6DOF &&
                   (int)VOTE_RAYS3D == FAM_RAYS3D && (int)VOTE_POINTSET2D == FAM_POINTSET2D &&
-                  (int)VOTE_AFFINE4D == FAM_AFFINE4D,
+                  (int)VOTE_AFFINE4D == FAM_AFFINE4D && (int)VOTE_RADIAL5DOF == FAM_RADIAL5DOF,
               "family numbers");
 
 // bytes of one record of level l (its format is fixed per solve by finalize_levels)

@@ -606,6 +606,7 @@ static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs
     case FAM_POSE6DOF: { constexpr int FAMV = FAM_POSE6DOF; CALL; } break;       \
     case FAM_POINTSET2D: { constexpr int FAMV = FAM_POINTSET2D; CALL; } break;   \
     case FAM_AFFINE4D: { constexpr int FAMV = FAM_AFFINE4D; CALL; } break;       \
+    case FAM_RADIAL5DOF: { constexpr int FAMV = FAM_RADIAL5DOF; CALL; } break;   \
     default: break;                                                 \
     }
 
@@ -668,6 +669,7 @@ void launch_tile_dst(const Chunk &c, cudaStream_t st) {
     if (ns == 4) k_tile_dst<4><<<blocks_for(nt, 32), 32 * 4, 0, st>>>(c);
     else if (ns == 8) k_tile_dst<8><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
     else if (ns == 16) k_tile_dst<16><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
+    else if (ns == 32) k_tile_dst<32><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
     else k_tile_dst<64><<<blocks_for(nt, 32), 32 * 8, 0, st>>>(c);
 }
 
@@ -678,6 +680,7 @@ void launch_child_lbmax(const Chunk &c, cudaStream_t st) {
     if (ns == 4) k_child_lbmax<4><<<blocks_for(n, 256), 256, 0, st>>>(c);
     else if (ns == 8) k_child_lbmax<8><<<blocks_for(n, 256), 256, 0, st>>>(c);
     else if (ns == 16) k_child_lbmax<16><<<blocks_for(n, 256), 256, 0, st>>>(c);
+    else if (ns == 32) k_child_lbmax<32><<<blocks_for(n, 256), 256, 0, st>>>(c);
     else k_child_lbmax<64><<<blocks_for(n, 256), 256, 0, st>>>(c);
 }
 
@@ -691,12 +694,14 @@ void launch_child_alloc(const Chunk &c, uint32_t *keepflag, uint32_t *recn, unsi
     if (ns == 4) k_child_mark<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else if (ns == 8) k_child_mark<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else if (ns == 16) k_child_mark<16><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else if (ns == 32) k_child_mark<32><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else k_child_mark<64><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     if (c.lev.leaf_children) return;
     k_scan_sums<<<1, 256, 0, st>>>(ba, bb, (int)nb, c.sc);
     if (ns == 4) k_child_write<4><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else if (ns == 8) k_child_write<8><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else if (ns == 16) k_child_write<16><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
+    else if (ns == 32) k_child_write<32><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
     else k_child_write<64><<<nb, 256, 0, st>>>(c, keepflag, recn, ba, bb);
 }
 

@@ -397,6 +397,7 @@ static unsigned wide_blocks(int64_t nt) {
     case FAM_POSE6DOF: { constexpr int FAMV = FAM_POSE6DOF; CALL; } break;     \
     case FAM_POINTSET2D: { constexpr int FAMV = FAM_POINTSET2D; CALL; } break; \
     case FAM_AFFINE4D: { constexpr int FAMV = FAM_AFFINE4D; CALL; } break;     \
+    case FAM_RADIAL5DOF: { constexpr int FAMV = FAM_RADIAL5DOF; CALL; } break; \
     default: break;                                                            \
     }
 

@@ -14,7 +14,7 @@ import threading
 
 import numpy as np
 
-from .inputs import LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, FAMILY_DK
+from .inputs import LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF, FAMILY_DK
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libvote.so")
@@ -28,7 +28,7 @@ VOTE_OPT_DIVE, VOTE_OPT_SPIN_LIMIT = 11, 12
 KERNEL_CLASSES = ["lift", "cell_geo", "test_count", "test_emit", "children", "replay", "group", "spare"]
 STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
           5: "VOTE_ETIMEOUT", 6: "VOTE_EUNSUPPORTED", 7: "VOTE_EINTERNAL"}
-NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4, POSE6DOF: 5, RAYS3D: 4, POINTSET2D: 4, AFFINE4D: 4}
+NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4, POSE6DOF: 5, RAYS3D: 4, POINTSET2D: 4, AFFINE4D: 4, RADIAL5DOF: 5}
 EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
            "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_get_kernel_times",
            "vote_get_level_stats", "vote_cell_counts_noalloc", "vote_softscore_fwd", "vote_softscore_bwd",
