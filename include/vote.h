@@ -301,8 +301,9 @@ vote_status vote_get_level_stats(vote_ctx *ctx, int64_t *cells, int64_t *records
  *   surfaces, n, level, coords, ub, lb, reach   as for vote_cell_counts.
  * Problems with more levels than the array holds (L > 31) return
  * VOTE_EUNSUPPORTED.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents (the counters
+ * address (cudaGetSymbolAddress).  Every call copies between host and device
+ * memory and synchronises the stream, so no call may be made while the stream is
+ * being captured into a CUDA graph.  All calls share the array and it keeps the last call's contents (the counters
  * are cleared at the start of each call): calls that may overlap on the GPU (on
  * different streams or host threads) race and must be serialised by the caller.
  * The call synchronises the stream before returning. */
