@@ -6,8 +6,13 @@
 // their step doubles).
 //
 // Positions: every tile's first output slot per child comes from k_tile_dst;
-// inside a tile a lane's position is the number of passing lanes below it.  The snap is taken in FP32 (in steps) when the value is at least
-// the screen's band away from a rounding tie, else in FP64 by the definition.
+// inside a tile a lane's position is the number of passing lanes below it.
+//
+// The snap is taken in FP32 (in steps) when the value is at least the screen's
+// band away from a rounding tie, or when the residual is exact in FP32 (every term
+// a multiple of 2^e and the magnitudes below 2^(24+e): a tie then rounds to even as
+// the definition's exact FP64 value does); else by a double-float recomputation
+// when that is far enough from a tie; else in FP64 by the definition.
 #include "gv_tile.cuh"
 
 namespace gv {

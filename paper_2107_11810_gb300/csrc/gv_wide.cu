@@ -4,8 +4,8 @@
 // of Sec. 3.2 with the FP32 screen and FP64 recheck, and the snap of the child
 // records for the next level), laid out for many child slots: lane s % 32 keeps the
 // counters and the ballot of child slot s, and the screen's coefficients of the
-// free child slots are read from the cell's geometry through the cache (they are
-// the same for every lane of a warp).
+// cell (the same for every lane of a warp) are staged in the warp's part of shared
+// memory once per run of tiles of one cell.
 //
 // Each warp takes a contiguous range of the chunk's tiles (so runs of tiles of one
 // cell stay together) and reads its records with plain loads; there are no
