@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import torch
 
-LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D = 1, 2, 3, 4, 5, 6, 7
+LINE2D, PLANE3D_SPH, POSE3DOF, POSE6DOF, RAYS3D, POINTSET2D, AFFINE4D, RADIAL5DOF, POSE7DOF = range(1, 10)
 
 
 def rotation(phi: torch.Tensor) -> torch.Tensor:
@@ -64,6 +64,15 @@ def residuals(family: int, params: torch.Tensor, p: torch.Tensor) -> torch.Tenso
         rx = p[4] - (params[3] * depth - X[0])
         ry = p[5] - (params[4] * depth - X[1])
         return torch.stack([rx, ry], dim=1)
+    if family == POSE7DOF:                     # x = xi (r3 . w + z) / f - r1 . w (and y with eta)
+        X = rotation(p[0:3]) @ params[0:3]
+        depth = (X[2] + p[3]) / p[4]
+        rx = p[5] - (params[3] * depth - X[0])
+        ry = p[6] - (params[4] * depth - X[1])
+        return torch.stack([rx, ry], dim=1)
+    if family == RADIAL5DOF:                   # x = eta (r1 . w - y) / xi - r2 . w
+        X = rotation(p[0:3]) @ params[0:3]
+        return (p[4] - (params[4] * (X[0] - p[3]) / params[3] - X[1]))[:, None]
     raise ValueError(family)
 
 

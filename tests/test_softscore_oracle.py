@@ -62,7 +62,9 @@ def test_oracle_gradients_match_central_differences():
                          (ss.POSE6DOF, lambda: inputs.pose6dof(n=200, seed=7), [0.5, 0.5]),
                          (ss.RAYS3D, lambda: inputs.rays3d(n=200, seed=9), [0.05, 0.05]),
                          (ss.POINTSET2D, lambda: inputs.pointset2d(m=15, seed=10), [0.05, 0.05]),
-                         (ss.AFFINE4D, lambda: inputs.affine4d(n=200, seed=11), [0.05])]:
+                         (ss.AFFINE4D, lambda: inputs.affine4d(n=200, seed=11), [0.05]),
+                         (ss.RADIAL5DOF, lambda: inputs.radial5dof(n=200, seed=12), [0.5]),
+                         (ss.POSE7DOF, lambda: inputs.pose7dof(n=200, seed=13), [0.5, 0.5])]:
         prob = mk()
         prm = torch.from_numpy(prob.params.copy()).requires_grad_(True)
         p = torch.tensor(prob.truth, dtype=torch.float64) + 0.003
@@ -106,3 +108,31 @@ def test_pose6_residuals_equal_the_textbook_projection():
     prm2[3] = prm2[3] + 0.01
     r2 = ss.residuals(ss.POSE6DOF, prm2, p)
     assert np.allclose(r2[:, 0].numpy(), -0.01 * X[:, 2], atol=1e-12)
+
+
+def test_radial_and_focal_residuals_equal_the_textbook_projections():
+    # radial camera rows (r1, -y), (r2, x): a noise-free match satisfies
+    # eta X_1 = xi X_2 with X_1 = r1 . w - y, X_2 = r2 . w + x, and the residual of a
+    # perturbed eta is the change of x; 7DoF: f (X_1, X_2) / X_3 = (xi, eta) with
+    # X = R w + (x, y, z) (scipy's rotation, independent of the oracle's)
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(9)
+    phi, t, f = np.array([0.3, -0.5, 0.6]), np.array([2.0, 3.0, 6.0]), 1.15
+    R = Rotation.from_rotvec(phi).as_matrix()
+    w = rng.uniform(0, 5, size=(20, 3))
+    Rw = w @ R.T
+    X = Rw + t
+    xi, eta = f * X[:, 0] / X[:, 2], f * X[:, 1] / X[:, 2]
+    prm = torch.from_numpy(np.stack([w[:, 0], w[:, 1], w[:, 2], xi, eta]))
+    # radial: (phi, y, x) with X_1 = r1 . w - y, X_2 = r2 . w + x
+    p5 = torch.tensor([*phi, -t[0], t[1]], dtype=torch.float64)
+    assert float(ss.residuals(ss.RADIAL5DOF, prm, p5).abs().max()) < 1e-12
+    prm2 = prm.clone()
+    prm2[4] = prm2[4] + 0.01
+    r2 = ss.residuals(ss.RADIAL5DOF, prm2, p5)[:, 0].numpy()
+    assert np.allclose(r2, -0.01 * X[:, 0] / xi, atol=1e-12)
+    # 7DoF: (phi, z, f, x, y)
+    p7 = torch.tensor([*phi, t[2], f, t[0], t[1]], dtype=torch.float64)
+    assert float(ss.residuals(ss.POSE7DOF, prm, p7).abs().max()) < 1e-12
+    s7 = ss.softscore(ss.POSE7DOF, prm, p7, torch.ones(20, dtype=torch.float64), [0.1, 0.1])
+    assert abs(float(s7) - 20.0) < 1e-9
