@@ -260,6 +260,19 @@ vote_status vote_leaf_box(vote_ctx *ctx, const int64_t *leaf, double *lo, double
 /* Number of levels L and per-coordinate split counts L_j (host [d]). */
 vote_status vote_levels(vote_ctx *ctx, int *L, int *Lj);
 
+/* The level structure of a problem, without a context or a device (host code only):
+ * the canonization's snap steps and accumulated error bound (Sec. 3.2,
+ * "Canonization" and the eps update).  family, d, k, eps[d], bounds[2d] as for
+ * vote_create.  Out (host; any of Lj, s_f, s_t, A may be NULL): *L levels; Lj [d]
+ * splits per coordinate; s_f [d-k] snap step of the dependent residuals; s_t
+ * [L * le] snap step of essential parameter m at level l (index l * le + m, le the
+ * family's essential-parameter count); A [L * (d-k)] accumulated canonization error
+ * bound after the snap at level l (A_{l+1}; index l * (d-k) + j).  L is at most 31,
+ * so arrays of 31 levels always suffice.  VOTE_EINVAL / VOTE_EUNSUPPORTED as for
+ * vote_create. */
+vote_status vote_level_constants(int family, int d, int k, const double *eps, const double *bounds, int *L,
+                                 int *Lj, double *s_f, double *s_t, double *A);
+
 /* Debug trace of the last solve (needs VOTE_OPT_TRACE_CAP > 0): host arrays of
  * capacity cap; level[i], coords[i*d + j], ub[i], lb[i]; *count = entries
  * written.  Returns VOTE_ECAPACITY if the trace overflowed. */

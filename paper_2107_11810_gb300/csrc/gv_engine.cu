@@ -1350,6 +1350,22 @@ vote_status vote_levels(vote_ctx *c, int *L, int *Lj) {
     return VOTE_OK;
 }
 
+vote_status vote_level_constants(int family, int d, int k, const double *eps, const double *bounds, int *L,
+                                 int *Lj, double *s_f, double *s_t, double *A) {
+    if (!eps || !bounds || !L) { set_err("invalid arguments"); return VOTE_EINVAL; }
+    vote_ctx tmp;                        // host-side constants only (no device memory)
+    TRY(problem_init(&tmp, family, d, k, eps, bounds));
+    const Problem &P = tmp.P;
+    *L = P.L;
+    if (Lj) for (int j = 0; j < P.d; ++j) Lj[j] = P.Lj[j];
+    if (s_f) for (int j = 0; j < P.nd; ++j) s_f[j] = P.s_f[j];
+    for (int l = 0; l < P.L; ++l) {
+        if (s_t) for (int m = 0; m < P.le; ++m) s_t[(size_t)l * P.le + m] = tmp.lev[l].s_t[m];
+        if (A) for (int j = 0; j < P.nd; ++j) A[(size_t)l * P.nd + j] = tmp.lev[l].A1[j];
+    }
+    return VOTE_OK;
+}
+
 vote_status vote_get_trace(vote_ctx *c, int64_t cap, int32_t *level, int64_t *coords, int64_t *ub, int64_t *lb,
                            int64_t *count) {
     if (!c || !count || cap < 0) { set_err("invalid arguments"); return VOTE_EINVAL; }

@@ -29,10 +29,13 @@ KERNEL_CLASSES = ["lift", "cell_geo", "test_count", "test_emit", "children", "re
 STATUS = {0: "VOTE_OK", 1: "VOTE_EINVAL", 2: "VOTE_ENOMEM", 3: "VOTE_ECUDA", 4: "VOTE_ECAPACITY",
           5: "VOTE_ETIMEOUT", 6: "VOTE_EUNSUPPORTED", 7: "VOTE_EINTERNAL"}
 NPARAM = {LINE2D: 2, PLANE3D_SPH: 3, POSE3DOF: 4, POSE6DOF: 5, RAYS3D: 4, POINTSET2D: 4, AFFINE4D: 4, RADIAL5DOF: 5}
+# essential parameters (record coefficients) per family
+NESSENTIAL = {LINE2D: 1, PLANE3D_SPH: 3, POSE3DOF: 2, POSE6DOF: 11, RAYS3D: 2, POINTSET2D: 2, AFFINE4D: 3,
+              RADIAL5DOF: 7}
 EXPORTS = ["vote_create", "vote_set_option", "vote_set_stream", "vote_solve", "vote_solve_host",
            "vote_cell_counts", "vote_levels", "vote_get_trace", "vote_get_stats", "vote_get_kernel_times",
            "vote_get_level_stats", "vote_cell_counts_noalloc", "vote_softscore_fwd", "vote_softscore_bwd",
-           "vote_refine", "vote_solve_batched", "vote_leaf_box",
+           "vote_refine", "vote_solve_batched", "vote_leaf_box", "vote_level_constants",
            "vote_last_error", "vote_destroy"]
 
 
@@ -70,6 +73,7 @@ def load(path: str | None = None):
             lib.vote_cell_counts.argtypes = [P, P, i64, i32, P, P, P, P]
             lib.vote_levels.argtypes = [P, P, P]
             lib.vote_leaf_box.argtypes = [P, P, P, P]
+            lib.vote_level_constants.argtypes = [i32, i32, i32, P, P, P, P, P, P, P]
             lib.vote_get_trace.argtypes = [P, i64, P, P, P, P, P]
             lib.vote_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
             lib.vote_get_kernel_times.argtypes = [P, P, P, P]
@@ -347,6 +351,26 @@ def cell_counts_noalloc(family: int, eps, bounds, surfaces, level: int, coords, 
     _check(lib.vote_cell_counts_noalloc(family, d, k, _ptr(e), _ptr(b), _ptr(surfaces), surfaces.shape[1],
                                         int(level), _ptr(c), _ptr(ub), _ptr(lb), _ptr(reach), handle))
     return int(ub[0]), int(lb[0])
+
+
+def level_constants(family: int, eps, bounds) -> dict:
+    """The level structure without a context or a device (vote_level_constants): L,
+    Lj [d], s_f [d-k], s_t [L, le] (essential-parameter snap steps per level) and
+    A [L, d-k] (accumulated canonization error bound after each level's snap)."""
+    lib = load()
+    d, k = FAMILY_DK[family]
+    le = NESSENTIAL[family]
+    e = np.ascontiguousarray(eps, dtype=np.float64).reshape(d)
+    b = np.ascontiguousarray(bounds, dtype=np.float64).reshape(2 * d)
+    L = ctypes.c_int()
+    Lj = np.zeros(d, np.int32)
+    s_f = np.zeros(d - k)
+    s_t = np.zeros(31 * le)
+    A = np.zeros(31 * (d - k))
+    _check(lib.vote_level_constants(family, d, k, _ptr(e), _ptr(b), ctypes.byref(L), _ptr(Lj), _ptr(s_f),
+                                    _ptr(s_t), _ptr(A)))
+    n = L.value
+    return dict(L=n, Lj=Lj, s_f=s_f, s_t=s_t[: n * le].reshape(n, le), A=A[: n * (d - k)].reshape(n, d - k))
 
 
 def mask_words_to_numpy(mask) -> np.ndarray:
