@@ -21,7 +21,7 @@ def rotation(phi: torch.Tensor) -> torch.Tensor:
     K = torch.stack([torch.stack([phi.new_zeros(()), -phi[2], phi[1]]),
                      torch.stack([phi[2], phi.new_zeros(()), -phi[0]]),
                      torch.stack([-phi[1], phi[0], phi.new_zeros(())])])
-    if float(th2) < 1e-8:
+    if float(th2.detach()) < 1e-8:
         a = 1.0 - th2 / 6.0
         b = 0.5 - th2 / 24.0
     else:
