@@ -4,7 +4,8 @@
   L = 12 levels) at 1e4 points;
 * pose6dof_n5000: the calibrated-camera configuration (5,000 matches, 250
   inliers, +-30 deg rotation prior, 10 m translation box, 7 levels, constant
-  vertical tolerance), and pose6dof_prior5_n5000, the same with a +-5 deg prior.
+  vertical tolerance), and pose6dof_prior5_n5000, the same with a +-5 deg prior;
+* radial5dof_n5000: the radial camera (Sec. 4.2.4) at the same sizes.
 
 Each is Algorithm 2 with canonization (Sec. 3.2) and pruning (Sec. 3.3), solved by
 the multi-core oracle (OpenMP over root subtrees; its results equal the
@@ -35,6 +36,7 @@ CASES = {
     "plane3d_eps005_n1e4": dict(generator="plane3d", kwargs=dict(n=10_000, inlier_frac=0.05)),
     "pose6dof_prior5_n5000": dict(generator="pose6dof", kwargs=dict(n=5000, prior_deg=5.0)),
     "pose6dof_n5000": dict(generator="pose6dof", kwargs=dict(n=5000, prior_deg=30.0)),
+    "radial5dof_n5000": dict(generator="radial5dof", kwargs=dict(n=5000)),
 }
 for _c in CASES.values():
     _c["make"] = (lambda c: lambda: getattr(inputs, c["generator"])(**c["kwargs"]))(_c)
