@@ -49,7 +49,12 @@
  *   - ties between leaves of equal depth go to the lexicographically smallest
  *     integer leaf coordinates;
  *   - the reported point is the centre of the best leaf, the inlier set is every
- *     original surface whose own record reaches that leaf.
+ *     original surface whose own record reaches that leaf;
+ *   - per family (stated where each family is defined below): its coordinates and
+ *     dependent/free split, the affine form used for canonization (6DoF, 7DoF and
+ *     the radial camera: more coefficients than the paper's essential parameters),
+ *     its margin bounds sigma and Lambda, and a constant tolerance on the dependent
+ *     coordinates of the camera families.
  *
  * Transcendentals: sin/cos come from gvo_vsin/gvo_vcos below (Cody-Waite argument
  * reduction by pi/2 with a three-part constant, then the Taylor series of sin and
