@@ -20,6 +20,8 @@ Functions and the passages they follow:
     error (Sec. 3.2, "Canonization" and the eps-update discussion).
   * :func:`vsin` / :func:`vcos` -- the sine/cosine used for cell-centre basis
     values (Taylor series with Cody-Waite reduction).
+  * :func:`oracle.naive.naive_voting` -- naive voting (Algorithm 1) on the leaf
+    grid, every family (the comparator's definition).
   * :func:`sigma`, :func:`lipschitz`, :func:`path_records` -- the margin functions
     behind the canonization error bound and the surface-box test (Sec. 3.2), and
     the canonical records of one surface along a root-to-cell path, exported so
