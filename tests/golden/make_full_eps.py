@@ -5,7 +5,9 @@
 * pose6dof_n5000: the calibrated-camera configuration (5,000 matches, 250
   inliers, +-30 deg rotation prior, 10 m translation box, 7 levels, constant
   vertical tolerance), and pose6dof_prior5_n5000, the same with a +-5 deg prior;
-* radial5dof_n5000: the radial camera (Sec. 4.2.4) at the same sizes.
+* radial5dof_n5000: the radial camera (Sec. 4.2.4) at the same sizes;
+* pointset2d_m300, affine4d_n1e4: the point-set (300 x 300 points) and affine
+  4-space (1e4 points) benchmark workloads.
 
 Each is Algorithm 2 with canonization (Sec. 3.2) and pruning (Sec. 3.3), solved by
 the multi-core oracle (OpenMP over root subtrees; its results equal the
@@ -37,6 +39,8 @@ CASES = {
     "pose6dof_prior5_n5000": dict(generator="pose6dof", kwargs=dict(n=5000, prior_deg=5.0)),
     "pose6dof_n5000": dict(generator="pose6dof", kwargs=dict(n=5000, prior_deg=30.0)),
     "radial5dof_n5000": dict(generator="radial5dof", kwargs=dict(n=5000)),
+    "pointset2d_m300": dict(generator="pointset2d", kwargs=dict(m=300)),
+    "affine4d_n1e4": dict(generator="affine4d", kwargs=dict()),
 }
 for _c in CASES.values():
     _c["make"] = (lambda c: lambda: getattr(inputs, c["generator"])(**c["kwargs"]))(_c)

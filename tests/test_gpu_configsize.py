@@ -1,0 +1,50 @@
+"""Bit-exact parity at the benchmark workloads' sizes for the 16-child families, through
+the C ABI: point-set similarity alignment (two sets of 300 points, 90,000 surfaces)
+and hyperplanes in 4-space (1e4 points).  Depth, best leaf, best point and inlier
+mask in both precision modes equal complete oracle solves stored by
+tests/golden/make_full_eps.py (or recomputed when the input bits differ).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2107_11810_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("name", ["pointset2d_m300", "affine4d_n1e4"])
+def test_benchmark_size_bit_exact_against_the_oracle(name):
+    from golden import make_full_eps
+    from paper_2107_11810_gb300 import vote
+    case = make_full_eps.CASES[name]
+    with open(os.path.join(os.path.dirname(__file__), "golden", name + ".json")) as f:
+        gold = json.load(f)
+    p = case["make"]()
+    if make_full_eps.params_sha256(p.params) == gold["params_sha256"]:
+        want = dict(depth=gold["depth"], best_leaf=np.array(gold["best_leaf"]),
+                    best_point=np.array([float.fromhex(x) for x in gold["best_point"]]),
+                    mask=np.array(gold["mask"], np.uint32))
+    else:                       # this platform generated other input bits: ask the oracle itself
+        want = oracle.solve_parallel(p.family, p.eps, p.bounds, p.params)
+    t = torch.from_numpy(p.params).cuda()
+    for precision in (1, 0):
+        s = vote.Solver(p.family, p.eps, p.bounds, precision=precision)
+        r = s.solve(t)
+        assert r["depth"] == want["depth"]
+        assert np.array_equal(r["best_leaf"], want["best_leaf"])
+        assert np.array_equal(r["best_point"], want["best_point"])
+        assert np.array_equal(vote.mask_words_to_numpy(r["mask"]), want["mask"])
+    assert r["depth"] >= 0.8 * len(p.inliers)
