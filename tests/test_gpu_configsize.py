@@ -1,8 +1,9 @@
-"""Bit-exact parity at the benchmark workloads' sizes for the 16-child families, through
-the C ABI: point-set similarity alignment (two sets of 300 points, 90,000 surfaces)
-and hyperplanes in 4-space (1e4 points).  Depth, best leaf, best point and inlier
-mask in both precision modes equal complete oracle solves stored by
-tests/golden/make_full_eps.py (or recomputed when the input bits differ).
+"""Bit-exact parity at the benchmark workloads' sizes, through the C ABI: point-set
+similarity alignment (two sets of 300 points, 90,000 surfaces) and hyperplanes in
+4-space (1e4 points) against complete oracle solves stored by
+tests/golden/make_full_eps.py (or recomputed when the input bits differ), and rays in
+3-space (1e5 rays) against the oracle run in the test.  Depth, best leaf, best point
+and inlier mask, in both precision modes.
 """
 import json
 import os
@@ -48,3 +49,18 @@ def test_benchmark_size_bit_exact_against_the_oracle(name):
         assert np.array_equal(r["best_point"], want["best_point"])
         assert np.array_equal(vote.mask_words_to_numpy(r["mask"]), want["mask"])
     assert r["depth"] >= 0.8 * len(p.inliers)
+
+
+def test_rays_benchmark_size_bit_exact_against_the_oracle():
+    # 1e5 rays (the rays3d_n1e5 workload): the oracle solves it in about a second
+    from paper_2107_11810_gb300 import inputs, vote
+    p = inputs.rays3d()
+    want = oracle.solve(p.family, p.eps, p.bounds, p.params)
+    t = torch.from_numpy(p.params).cuda()
+    for precision in (1, 0):
+        s = vote.Solver(p.family, p.eps, p.bounds, precision=precision)
+        r = s.solve(t)
+        assert r["depth"] == want["depth"]
+        assert np.array_equal(r["best_leaf"], want["best_leaf"])
+        assert np.array_equal(r["best_point"], want["best_point"])
+        assert np.array_equal(vote.mask_words_to_numpy(r["mask"]), want["mask"])
